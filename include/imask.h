@@ -1,0 +1,180 @@
+/*
+ * imask.h -- C ABI of libimask.so, the GB300 (sm_103a) hot path of ImaSk.
+ *
+ * ImaSk (A. Perelli, C.-B. Schoenlieb, M. J. Ehrhardt, "ImaSk: Stochastic
+ * Multiresolution Image Sketching for Inverse Imaging Problems") solves
+ *     min_x 1/2 |K x - b|^2 + R(x)                            (eq. min_obj)
+ * through the sketched problem min_x 1/2 |sum_i p_i K_i x - b|^2 + R(x)
+ * (eq. min_obj_new) with the SAGA-type primal-dual iteration of Alg. 1: at
+ * every iteration one resolution level is drawn at random and only that
+ * level's operator K_i and its adjoint are applied.
+ *
+ * Levels.  ell = 0..levels-1.  ell = 0 is the full-resolution compensated
+ * sketch K_0 = K S_r with S_r = p_0^{-1}(I - sum_{ell>=1} p_ell T_ell^* T_ell)
+ * (the paper's i = r, Sec. 4.1); ell >= 1 is K_ell = R_ell T_ell, the block
+ * mean over 2^ell x 2^ell blocks followed by the projector on the grid of side
+ * n / 2^ell (eq. CT_sketches).  ell = -1 selects the plain operator K.
+ *
+ * Layouts.  Images are row-major float[n][n]; pixel (i, c) is centred at
+ * (x_c, y_i) = (-W/2 + (c + 1/2) h, -W/2 + (i + 1/2) h) with h = W / n.
+ * Sinograms are row-major float[n_angles][n_det].  The projector is Joseph's
+ * method (linear interpolation along the major axis of every ray); the
+ * back-projector is its exact transpose, computed pixel by pixel.
+ *
+ * Conventions.
+ *  - Pointers named *_dev are device pointers owned by the caller; the library
+ *    never frees them.  Plans and states own their internal buffers.
+ *  - Every call is asynchronous and ordered on the stream it is given (a
+ *    cudaStream_t passed as void*; NULL is the legacy default stream), except
+ *    where a call says it synchronises.
+ *  - Functions never abort.  On error they return a status other than
+ *    IMASK_OK, record a message readable with imask_last_error() in the
+ *    calling thread, and leave their outputs unspecified.
+ *  - A plan is read-only after creation and may be shared between threads.
+ *    A state belongs to one caller at a time.
+ *  - n must be a multiple of 2^(levels-1) (IMASK_ERR_SHAPE otherwise); the
+ *    paper assumes power-of-two sides (Sec. 4.1), multiples suffice here.
+ */
+#ifndef IMASK_H
+#define IMASK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IMASK_OK = 0,
+  IMASK_ERR_INVALID = 1,   /* bad argument or descriptor field */
+  IMASK_ERR_SHAPE = 2,     /* n not a multiple of 2^(levels-1), sizes out of range */
+  IMASK_ERR_OOM = 3,       /* device or host allocation failed */
+  IMASK_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+  IMASK_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+  IMASK_ERR_NONFINITE = 6  /* a reduction met NaN or Inf */
+} imask_status;
+
+typedef struct imask_plan_s *imask_plan_t;   /* immutable geometry, levels, step size */
+typedef struct imask_state_s *imask_state_t; /* one solve: x, y, SAGA tables, counter */
+
+/* Problem description.  Geometry (Sec. 4.1-4.2): parallel beam, or fan beam
+ * with a flat detector.  View a is at angle angle_start + angle_span*a/n_angles.
+ * Bin j sits at offset (j - (n_det-1)/2) * det_spacing; det_spacing <= 0 picks
+ * h for parallel beam and h (src_dist + det_dist) / src_dist for fan beam.
+ * Parallel ray (a, j): {P : <P, (cos, sin)> = offset}.  Fan ray (a, j): from the
+ * source src_dist (cos, sin) to the bin centre -det_dist (cos, sin) +
+ * offset (-sin, cos).  probs[ell] (NULL: uniform) are the p_ell of Alg. 1.
+ * R(x) = mu/2 |x|^2 (reg 0) or mu/2 |x|^2 + tv_lambda sum sqrt(|grad x|^2 +
+ * tv_eps^2) with forward differences (reg 1, prox by tv_inner FISTA steps).
+ * mu <= 0 picks mu = |K|^2 / 2.46^2; sigma <= 0 picks the step of Thm. 3 from
+ * power-method estimates of L, Lbar, Lbar_p (Sec. 3.4-3.6). */
+typedef struct {
+  int32_t n, n_angles, n_det, geometry;  /* geometry: 0 parallel, 1 fan */
+  double fov, det_spacing, angle_start, angle_span, src_dist, det_dist;
+  int32_t levels;                        /* r, 1..8 */
+  const double *probs;                   /* host array of r entries, or NULL */
+  int32_t reg;                           /* 0 quadratic, 1 quadratic + smoothed TV */
+  double mu, tv_lambda, tv_eps;
+  int32_t tv_inner;
+  double sigma;
+  int32_t storage;                       /* 0: fp32 (the only storage implemented) */
+} imask_desc;
+
+/* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,
+ * Lbar_p; sigma and theta of Thm. 3 (theta = 0 when sigma was given). */
+typedef struct {
+  double mu, sigma, theta, L, Lbar, Lbar_p, norm_K;
+  int64_t n_meas, n_pix;
+  int32_t levels, n_xmajor_views_split; /* views whose rays change major axis */
+  int64_t n_xmajor_rays;
+} imask_plan_info;
+
+/* Creates a plan: validates the descriptor, builds the per-ray geometry tables
+ * in FP64 on the host, uploads them, and (when mu or sigma are <= 0) runs the
+ * FP64 power method on the device and the Thm. 3 solver on the host.
+ * Synchronises.  Errors: INVALID, SHAPE, OOM, CUDA. */
+imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out);
+imask_status imask_plan_destroy(imask_plan_t plan);
+imask_status imask_plan_get_info(imask_plan_t plan, imask_plan_info *info);
+
+/* Synchronises the device and reports IMASK_ERR_TIMEOUT if a projector
+ * launch of this plan gave up a bounded wait for its image strips since the
+ * last check (the flag is then cleared). */
+imask_status imask_plan_check(imask_plan_t plan);
+
+/* Host copy of the per-view major-axis split that the plan uses: for view a,
+ * rays j < split[a] are x-major iff first_x[a] != 0, the others the opposite
+ * (x-major: |dir_x| >= |dir_y| in FP64).  Arrays of n_angles entries. */
+imask_status imask_plan_axis_split(imask_plan_t plan, int32_t *split, int32_t *first_x);
+
+/* Same tables computed on the host alone, without a device (for testing the
+ * host geometry).  Errors: INVALID, SHAPE. */
+imask_status imask_geometry_axis_split(const imask_desc *desc, int32_t *split, int32_t *first_x);
+
+/* Thm. 3 step size from given constants (host FP64, grid x grid search over
+ * (c, rho) in (0, cbar) x (0, 1)): out = {sigma, theta, c, rho}. */
+imask_status imask_optimal_step(double L, double Lbar, double Lbar_p, double p_min,
+                                int32_t grid, double out[4]);
+
+/* sino_dev[n_angles*n_det] = K_level x_dev[n*n] (eq. CT_sketches; level -1:
+ * plain K).  Allocates its temporary images with cudaMallocAsync on stream. */
+imask_status imask_project(imask_plan_t plan, int32_t level, const float *x_dev,
+                           float *sino_dev, void *stream);
+
+/* img_dev[n*n] = K_level^T y_dev: level >= 1: 4^-level T^*(R_level^T y);
+ * level 0: S_r (K^T y); level -1: K^T y.  Pixel-driven gather (no atomics).
+ * Allocates its coarse temporary with cudaMallocAsync on stream. */
+imask_status imask_backproject(imask_plan_t plan, int32_t level, const float *y_dev,
+                               float *img_dev, void *stream);
+
+/* The level stream of Alg. 1 (sampling step): out_dev[t] = ell_{k0+t} drawn on
+ * the device from SplitMix64 output k0+t of `seed` against thresholds
+ * round(2^53 * cumsum(p)) * 2^11.  Bit-exact with any other implementation of
+ * that definition. */
+imask_status imask_levels(imask_plan_t plan, uint64_t seed, int64_t k0, int64_t n,
+                          int32_t *out_dev, void *stream);
+
+/* Creates the state of one solve (Alg. 1 defaults: x = y = 0, tables 0, k = 0)
+ * and copies b_dev[n_angles*n_det].  Allocates with cudaMallocAsync on stream. */
+imask_status imask_state_create(imask_plan_t plan, const float *b_dev, uint64_t seed,
+                                imask_state_t *state_out, void *stream);
+/* Advances the state by n_iters iterations of Alg. 1 on stream. */
+imask_status imask_step(imask_state_t state, int32_t n_iters, void *stream);
+/* Iteration counter k of the state (host value, no synchronisation). */
+int64_t imask_state_iteration(imask_state_t state);
+/* Copies a part of the state into dst_dev (float): what = 0 x[n*n], 1 y[m],
+ * 2 the running mean sum_l p_l phi_l [n*n], 3 the running mean sum_l p_l psi_l [m]. */
+imask_status imask_state_get(imask_state_t state, int32_t what, float *dst_dev, void *stream);
+imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
+/* Frees the state's buffers (stream-ordered on the stream last used). */
+imask_status imask_state_destroy(imask_state_t state);
+
+/* Whole solve: state_create, iters steps, copy x to x_dev, destroy. */
+imask_status imask_solve(imask_plan_t plan, const float *b_dev, uint64_t seed, int32_t iters,
+                         float *x_dev, void *stream);
+
+/* Metrics in FP64 on the device (synchronise; results on the host).
+ * Objective of eq. min_obj_new: 1/2 |sum_l p_l K_l x - b|^2 + R(x). */
+imask_status imask_objective(imask_plan_t plan, const float *x_dev, const float *b_dev,
+                             double *out, void *stream);
+/* |a - b|^2 / |b|^2 over n floats (IMASK_ERR_NONFINITE on NaN/Inf). */
+imask_status imask_rel_distance(int64_t n, const float *a_dev, const float *b_dev, double *out,
+                                void *stream);
+
+/* Kernel timing for roofline reports.  While enabled, every projector and
+ * back-projector launch made by this process is bracketed by CUDA events on
+ * its stream.  imask_profile_read synchronises those events and returns, per
+ * kind (0 forward projection, 1 back-projection, 2 primal update) and level
+ * (0..7), the total milliseconds and launch counts accumulated since the last
+ * reset: ms[kind*8 + level], count[kind*8 + level]. */
+imask_status imask_profile_enable(int32_t on);
+imask_status imask_profile_read(double ms[24], int64_t count[24], int32_t reset);
+/* Number of kernels this library has launched in the process so far. */
+int64_t imask_launch_count(void);
+
+const char *imask_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

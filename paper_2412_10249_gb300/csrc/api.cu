@@ -1,0 +1,1068 @@
+// api.cu -- host side of libimask.so: the C ABI declared in include/imask.h.
+//
+// Plan creation builds the acquisition geometry in FP64 on the host (ray list
+// with per-ray interpolation parameters, per-view major-axis split), uploads
+// it, and estimates the step-size constants of Sec. 3.4 with the power method
+// on the device (FP32 operators, FP64 reductions) before solving Thm. 3 on the
+// host.  States hold one solve of Alg. 1; imask_step launches the three
+// kernels of every iteration (see kernels.cu).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "imask_internal.h"
+
+// ===================================================================================
+// errors
+// ===================================================================================
+namespace {
+
+thread_local std::string t_err;
+
+imask_status fail(imask_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+imask_status cuda_fail(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(IMASK_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(IMASK_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+  } while (0)
+
+inline size_t align64(size_t n) { return (n + 63) & ~(size_t)63; }
+
+// ===================================================================================
+// profiling: CUDA events around projector / back-projector / update launches
+// ===================================================================================
+struct ProfRec {
+  int kind, level;
+  cudaEvent_t a, b;
+};
+
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<ProfRec> pending;
+  double ms[24] = {0};
+  int64_t count[24] = {0};
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+  }
+};
+
+Profiler g_prof;
+
+// Opens a timed region for (kind, level) on stream st; returns false when off.
+struct ProfScope {
+  bool active = false;
+  ProfRec rec{};
+  cudaStream_t st = nullptr;
+  ProfScope(int kind, int level, cudaStream_t s) : st(s) {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (!g_prof.on || level < 0 || level > 7) return;
+    rec.kind = kind;
+    rec.level = level;
+    rec.a = g_prof.get();
+    rec.b = g_prof.get();
+    if (!rec.a || !rec.b) return;
+    active = cudaEventRecord(rec.a, st) == cudaSuccess;
+  }
+  ~ProfScope() {
+    if (!active) return;
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    if (cudaEventRecord(rec.b, st) == cudaSuccess) g_prof.pending.push_back(rec);
+  }
+};
+
+}  // namespace
+
+// ===================================================================================
+// plan and state
+// ===================================================================================
+struct imask_plan_s {
+  imask_desc desc{};
+  std::vector<double> probs;
+  DevPlan dp{};
+  float4 *d_rays = nullptr;
+  ViewInfo *d_views = nullptr;
+  unsigned int *d_err = nullptr;
+  std::vector<int> split, first_x;
+  int n_cta_x = 0, n_cta_y = 0;
+  int n_split_views = 0;
+  double mu = 0, sigma = 0, theta = 0, L = 0, Lbar = 0, Lbar_p = 0, norm_K = 0;
+};
+
+struct imask_state_s {
+  imask_plan_t plan = nullptr;
+  unsigned long long seed = 0;
+  long long k = 0;
+  int cur = 0;
+  cudaStream_t stream = nullptr;
+  float *block = nullptr;
+  float *x = nullptr, *y[2] = {nullptr, nullptr}, *b = nullptr, *psi = nullptr,
+        *psi_mean = nullptr, *phi0 = nullptr, *phic = nullptr, *phi_mean = nullptr, *g = nullptr,
+        *tv = nullptr;
+  long long phic_off[IMASK_MAX_LEVELS] = {0};
+  PadSet pads{};
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// descriptor validation and host geometry (FP64)
+// ---------------------------------------------------------------------------------
+double pitch_of(const imask_desc &d) {
+  if (d.det_spacing > 0.0) return d.det_spacing;
+  double h = d.fov / (double)d.n;
+  if (d.geometry == 0) return h;
+  return h * (d.src_dist + d.det_dist) / d.src_dist;
+}
+
+imask_status validate(const imask_desc *d) {
+  if (!d) return fail(IMASK_ERR_INVALID, "descriptor is NULL");
+  if (d->n < 1 || d->n > 2048) return fail(IMASK_ERR_SHAPE, "n = %d outside [1, 2048]", d->n);
+  if (d->n_angles < 1 || d->n_det < 1)
+    return fail(IMASK_ERR_SHAPE, "n_angles and n_det must be positive");
+  if ((long long)d->n_angles * d->n_det >= (1LL << 30))
+    return fail(IMASK_ERR_SHAPE, "n_angles * n_det too large");
+  if (d->geometry != 0 && d->geometry != 1)
+    return fail(IMASK_ERR_INVALID, "geometry must be 0 (parallel) or 1 (fan)");
+  if (!(d->fov > 0.0) || !isfinite(d->fov)) return fail(IMASK_ERR_INVALID, "fov must be > 0");
+  if (d->levels < 1 || d->levels > IMASK_MAX_LEVELS)
+    return fail(IMASK_ERR_INVALID, "levels = %d outside [1, %d]", d->levels, IMASK_MAX_LEVELS);
+  if (d->n % (1 << (d->levels - 1)) != 0)
+    return fail(IMASK_ERR_SHAPE, "n = %d is not a multiple of 2^(levels-1) = %d", d->n,
+                1 << (d->levels - 1));
+  if (d->probs) {
+    double s = 0.0;
+    for (int l = 0; l < d->levels; ++l) {
+      if (!(d->probs[l] > 0.0 && d->probs[l] <= 1.0))
+        return fail(IMASK_ERR_INVALID, "probs[%d] = %g outside (0, 1]", l, d->probs[l]);
+      s += d->probs[l];
+    }
+    if (fabs(s - 1.0) > 1e-9) return fail(IMASK_ERR_INVALID, "probs sum to %.17g, not 1", s);
+  }
+  if (d->reg != 0 && d->reg != 1) return fail(IMASK_ERR_INVALID, "reg must be 0 or 1");
+  if (d->reg == 1 && (!(d->tv_eps > 0.0) || d->tv_lambda < 0.0 || d->tv_inner < 0))
+    return fail(IMASK_ERR_INVALID, "smoothed TV needs tv_eps > 0, tv_lambda >= 0, tv_inner >= 0");
+  if (d->storage != 0) return fail(IMASK_ERR_INVALID, "only fp32 storage (0) is implemented");
+  if (d->geometry == 1) {
+    if (!(d->src_dist > 0.5 * d->fov * 1.4142135623730951))
+      return fail(IMASK_ERR_INVALID, "fan source must lie outside the field of view");
+    if (d->det_dist < 0.0) return fail(IMASK_ERR_INVALID, "det_dist must be >= 0");
+  }
+  if (!(pitch_of(*d) > 0.0)) return fail(IMASK_ERR_INVALID, "detector pitch must be > 0");
+  return IMASK_OK;
+}
+
+// Ray (a, j) as a point and a direction, in the same operation order as the
+// definition in imask.h (the major-axis decision depends on the last bit).
+void ray_geom(const imask_desc &d, double pitch, int a, int j, double p0[2], double dir[2],
+              double *ca_out, double *sa_out) {
+  double ang = d.angle_start + d.angle_span * (double)a / (double)d.n_angles;
+  double s = ((double)j - 0.5 * (double)(d.n_det - 1)) * pitch;
+  double ca = cos(ang), sa = sin(ang);
+  if (d.geometry == 0) {
+    p0[0] = s * ca;
+    p0[1] = s * sa;
+    dir[0] = -sa;
+    dir[1] = ca;
+  } else {
+    double sx = d.src_dist * ca;
+    double sy = d.src_dist * sa;
+    double dx = -d.det_dist * ca - s * sa;
+    double dy = -d.det_dist * sa + s * ca;
+    p0[0] = sx;
+    p0[1] = sy;
+    dir[0] = dx - sx;
+    dir[1] = dy - sy;
+  }
+  if (ca_out) *ca_out = ca;
+  if (sa_out) *sa_out = sa;
+}
+
+// Per-view split: rays j < split[a] have major axis first_x[a] (1: x-major).
+imask_status axis_split(const imask_desc &d, std::vector<int> &split, std::vector<int> &first_x) {
+  const double pitch = pitch_of(d);
+  split.assign(d.n_angles, d.n_det);
+  first_x.assign(d.n_angles, 1);
+  for (int a = 0; a < d.n_angles; ++a) {
+    int first = -1, sp = d.n_det;
+    for (int j = 0; j < d.n_det; ++j) {
+      double p0[2], dir[2];
+      ray_geom(d, pitch, a, j, p0, dir, nullptr, nullptr);
+      int xm = fabs(dir[0]) >= fabs(dir[1]) ? 1 : 0;
+      if (j == 0) {
+        first = xm;
+      } else if (xm != first && sp == d.n_det) {
+        sp = j;
+      } else if (sp != d.n_det && xm == first) {
+        return fail(IMASK_ERR_INVALID,
+                    "view %d: rays change major axis more than once (fan wider than 90 degrees)",
+                    a);
+      }
+    }
+    split[a] = sp;
+    first_x[a] = first;
+  }
+  return IMASK_OK;
+}
+
+// thr[l] = round(2^53 * (p_0 + ... + p_l)) * 2^11, l = 0..r-2.
+void level_thresholds(const std::vector<double> &p, unsigned long long *thr) {
+  double cum = 0.0;
+  for (size_t l = 0; l + 1 < p.size(); ++l) {
+    cum += p[l];
+    long long v = llround(cum * 9007199254740992.0);
+    if (v >= 9007199254740992LL)
+      thr[l] = ~0ull;
+    else if (v <= 0)
+      thr[l] = 0ull;
+    else
+      thr[l] = ((unsigned long long)v) << 11;
+  }
+}
+
+LevelGeom level_geom(const imask_desc &d, int ell) {
+  LevelGeom g{};
+  const int sh = ell > 0 ? ell : 0;
+  g.nl = d.n >> sh;
+  g.ls = g.nl + 2 * IMASK_PAD;
+  int tc = (FP_STAGE_FLOATS / g.ls) & ~3;
+  tc = std::min(32, std::max(4, tc));
+  g.tc = tc;
+  g.lines = (g.nl + tc - 1) / tc * tc;
+  g.inv2l = (float)ldexp(1.0, -sh);
+  g.scale2l = (float)ldexp(1.0, sh);
+  g.hl = (float)(d.fov / (double)g.nl);
+  g.cmid = 0.5f * (float)(g.nl - 1);
+  g.bp_tile = ell <= 0 ? BP_TILE0 : std::max(1, BP_TILE0 >> ell);
+  g.bp_tiles = (g.nl + g.bp_tile - 1) / g.bp_tile;
+  return g;
+}
+
+int update_tile(int n, int levels) {
+  const int blk = 1 << (levels - 1);
+  const int cap = std::max(32, blk);
+  int best = blk;
+  for (int k = 1; blk * k <= cap; ++k)
+    if (n % (blk * k) == 0) best = blk * k;
+  return best;
+}
+
+size_t pad_floats(const LevelGeom &g) { return align64((size_t)g.lines * g.ls); }
+
+// Host copy of one state-or-scratch allocation plan.
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t n) {
+    size_t o = off;
+    off += align64(n);
+    return o;
+  }
+};
+
+// ---------------------------------------------------------------------------------
+// scratch for the bare operators (padded images of every level + coarse output)
+// ---------------------------------------------------------------------------------
+struct Scratch {
+  float *block = nullptr;
+  PadSet pads{};
+  float *g = nullptr;
+  cudaStream_t st = nullptr;
+};
+
+// levels_mask bit li (level li-1) selects which padded images to allocate.
+imask_status scratch_alloc(const imask_plan_s *p, unsigned levels_mask, bool with_g, cudaStream_t st,
+                           Scratch &s) {
+  Carve cv;
+  size_t offT[IMASK_MAX_LEVELS + 1] = {0}, offR[IMASK_MAX_LEVELS + 1] = {0};
+  for (int li = 0; li <= p->desc.levels; ++li) {
+    if (!(levels_mask & (1u << li))) continue;
+    const size_t f = pad_floats(p->dp.lg[li]);
+    offT[li] = cv.take(f);
+    offR[li] = cv.take(f);
+  }
+  size_t offg = with_g ? cv.take((size_t)p->dp.d) : 0;
+  const size_t total = std::max<size_t>(cv.off, 64);
+  void *mem = nullptr;
+  CK(cudaMallocAsync(&mem, total * sizeof(float), st), "cudaMallocAsync(scratch)");
+  s.block = (float *)mem;
+  s.st = st;
+  CK(cudaMemsetAsync(mem, 0, total * sizeof(float), st), "cudaMemsetAsync(scratch)");
+  for (int li = 0; li <= p->desc.levels; ++li) {
+    if (!(levels_mask & (1u << li))) continue;
+    s.pads.T[li] = s.block + offT[li];
+    s.pads.R[li] = s.block + offR[li];
+  }
+  s.g = with_g ? s.block + offg : nullptr;
+  return IMASK_OK;
+}
+
+void scratch_free(Scratch &s) {
+  if (s.block) cudaFreeAsync(s.block, s.st);
+  s.block = nullptr;
+}
+
+LevelSel fixed_level(int ell) {
+  LevelSel s{};
+  s.fixed = ell;
+  return s;
+}
+
+DualArgs no_dual() {
+  DualArgs d{};
+  d.on = 0;
+  return d;
+}
+
+// K_ell x -> sino using scratch pads (level index ell + 1 allocated).
+imask_status apply_K(const imask_plan_s *p, int ell, const float *x, float *sino, Scratch &s,
+                     cudaStream_t st) {
+  const LevelSel sel = fixed_level(ell);
+  CK(launch_sketch(p->dp, sel, x, s.pads, st), "sketch launch");
+  {
+    ProfScope ps(0, ell < 0 ? 0 : ell, st);
+    CK(launch_fp(p->dp, sel, s.pads, sino, no_dual(), p->n_cta_x, p->n_cta_y, p->d_err, st),
+       "projector launch");
+  }
+  return IMASK_OK;
+}
+
+imask_status apply_KT(const imask_plan_s *p, int ell, const float *y, float *img, Scratch &s,
+                      cudaStream_t st) {
+  const LevelSel sel = fixed_level(ell);
+  {
+    ProfScope ps(1, ell < 0 ? 0 : ell, st);
+    CK(launch_bp(p->dp, sel, y, s.g, st), "back-projector launch");
+  }
+  CK(launch_adjsketch(p->dp, ell, s.g, img, st), "adjoint sketch launch");
+  return IMASK_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 power method on the device (Sec. 3.6): largest eigenvalue of
+// sum_l w_l K_l^T K_l (image space), sum_l w_l K_l K_l^T (measurement space), or
+// (sum_l w_l K_l)^T (sum_l w_l K_l) (cross); level -1 alone when plain = true.
+// ---------------------------------------------------------------------------------
+struct PowerBuf {
+  float *v = nullptr, *u = nullptr, *ti = nullptr, *tm = nullptr, *acc = nullptr;
+  double *part = nullptr, *res = nullptr;
+};
+
+imask_status device_dot(const float *a, const float *b, long long n, PowerBuf &pb, cudaStream_t st,
+                        double *out) {
+  CK(launch_dot64(n, a, b, pb.part, pb.res, st), "dot launch");
+  CK(cudaMemcpyAsync(out, pb.res, sizeof(double), cudaMemcpyDeviceToHost, st), "copy dot");
+  CK(cudaStreamSynchronize(st), "sync dot");
+  return IMASK_OK;
+}
+
+imask_status power_method(const imask_plan_s *p, const double *w, bool cross, bool meas_space,
+                          bool plain, int iters, Scratch &s, PowerBuf &pb, cudaStream_t st,
+                          double *lam_out) {
+  const long long d = p->dp.d, m = p->dp.m;
+  const long long n = (cross || !meas_space) ? d : m;
+  const int r = plain ? 1 : p->desc.levels;
+  // start vector 1 + cos(0.7 i) / 2, normalised
+  std::vector<float> h(n);
+  double nrm = 0.0;
+  for (long long i = 0; i < n; ++i) {
+    double v = 1.0 + 0.5 * cos(0.7 * (double)i);
+    nrm += v * v;
+    h[i] = (float)v;
+  }
+  nrm = sqrt(nrm);
+  for (long long i = 0; i < n; ++i) h[i] = (float)((double)h[i] / nrm);
+  CK(cudaMemcpyAsync(pb.v, h.data(), n * sizeof(float), cudaMemcpyHostToDevice, st), "upload v");
+  double lam = 0.0;
+  imask_status rc;
+  for (int it = 0; it < iters; ++it) {
+    CK(launch_fill(n, 0.0f, pb.u, st), "fill");
+    if (cross) {
+      CK(launch_fill(m, 0.0f, pb.acc, st), "fill");
+      for (int l = 0; l < r; ++l) {
+        if ((rc = apply_K(p, plain ? -1 : l, pb.v, pb.tm, s, st)) != IMASK_OK) return rc;
+        CK(launch_axpy(m, (float)w[l], pb.tm, pb.acc, st), "axpy");
+      }
+      for (int l = 0; l < r; ++l) {
+        if ((rc = apply_KT(p, plain ? -1 : l, pb.acc, pb.ti, s, st)) != IMASK_OK) return rc;
+        CK(launch_axpy(d, (float)w[l], pb.ti, pb.u, st), "axpy");
+      }
+    } else if (!meas_space) {
+      for (int l = 0; l < r; ++l) {
+        if ((rc = apply_K(p, plain ? -1 : l, pb.v, pb.tm, s, st)) != IMASK_OK) return rc;
+        if ((rc = apply_KT(p, plain ? -1 : l, pb.tm, pb.ti, s, st)) != IMASK_OK) return rc;
+        CK(launch_axpy(d, (float)w[l], pb.ti, pb.u, st), "axpy");
+      }
+    } else {
+      for (int l = 0; l < r; ++l) {
+        if ((rc = apply_KT(p, plain ? -1 : l, pb.v, pb.ti, s, st)) != IMASK_OK) return rc;
+        if ((rc = apply_K(p, plain ? -1 : l, pb.ti, pb.tm, s, st)) != IMASK_OK) return rc;
+        CK(launch_axpy(m, (float)w[l], pb.tm, pb.u, st), "axpy");
+      }
+    }
+    double vu = 0.0, uu = 0.0;
+    if ((rc = device_dot(pb.v, pb.u, n, pb, st, &vu)) != IMASK_OK) return rc;
+    if ((rc = device_dot(pb.u, pb.u, n, pb, st, &uu)) != IMASK_OK) return rc;
+    if (!isfinite(vu) || !isfinite(uu))
+      return fail(IMASK_ERR_NONFINITE, "power method met a non-finite value");
+    lam = vu;
+    if (!(uu > 0.0)) break;
+    CK(launch_copy(n, pb.u, pb.v, st), "copy");
+    CK(launch_scale(n, (float)(1.0 / sqrt(uu)), pb.v, st), "scale");
+  }
+  *lam_out = lam;
+  return IMASK_OK;
+}
+
+imask_status plan_constants(imask_plan_s *p, cudaStream_t st) {
+  const bool need_mu = !(p->desc.mu > 0.0);
+  const bool need_sigma = !(p->desc.sigma > 0.0);
+  p->mu = p->desc.mu;
+  p->sigma = p->desc.sigma;
+  if (!need_mu && !need_sigma) return IMASK_OK;
+  const int iters = 100;
+  const long long d = p->dp.d, m = p->dp.m;
+  Scratch s;
+  unsigned mask = 0;
+  for (int li = 0; li <= p->desc.levels; ++li) mask |= 1u << li;
+  imask_status rc = scratch_alloc(p, mask, true, st, s);
+  if (rc != IMASK_OK) return rc;
+  PowerBuf pb;
+  void *mem = nullptr;
+  // v, u: max(d, m) each; ti: d; tm, acc: m
+  const size_t big = std::max(align64(d), align64(m));
+  const size_t fl = 2 * big + align64(d) + 2 * align64(m);
+  cudaError_t e = cudaMallocAsync(&mem, fl * sizeof(float) + 2048 * sizeof(double), st);
+  if (e != cudaSuccess) {
+    scratch_free(s);
+    return cuda_fail(e, "cudaMallocAsync(power)");
+  }
+  float *f = (float *)mem;
+  pb.v = f;
+  pb.u = pb.v + big;
+  pb.ti = pb.u + big;
+  pb.tm = pb.ti + align64(d);
+  pb.acc = pb.tm + align64(m);
+  pb.part = (double *)((char *)mem + fl * sizeof(float));
+  pb.res = pb.part + 1024;
+  do {
+    double one = 1.0, lam = 0.0;
+    if ((rc = power_method(p, &one, true, false, true, iters, s, pb, st, &lam)) != IMASK_OK) break;
+    p->norm_K = sqrt(lam);
+    if (need_mu) p->mu = p->norm_K * p->norm_K / (2.46 * 2.46);
+    if (!(p->mu > 0.0)) {
+      rc = fail(IMASK_ERR_INVALID, "derived mu is not positive");
+      break;
+    }
+    if (!need_sigma) break;
+    const int r = p->desc.levels;
+    double w1[IMASK_MAX_LEVELS], w2[IMASK_MAX_LEVELS];
+    for (int l = 0; l < r; ++l) {
+      w1[l] = p->probs[l];
+      w2[l] = p->probs[l] * p->probs[l];
+    }
+    double lc = 0, lbx = 0, lby = 0, lpx = 0, lpy = 0;
+    if ((rc = power_method(p, w1, true, false, false, iters, s, pb, st, &lc)) != IMASK_OK) break;
+    if ((rc = power_method(p, w2, false, false, false, iters, s, pb, st, &lbx)) != IMASK_OK) break;
+    if ((rc = power_method(p, w2, false, true, false, iters, s, pb, st, &lby)) != IMASK_OK) break;
+    if ((rc = power_method(p, w1, false, false, false, iters, s, pb, st, &lpx)) != IMASK_OK) break;
+    if ((rc = power_method(p, w1, false, true, false, iters, s, pb, st, &lpy)) != IMASK_OK) break;
+    p->L = sqrt(lc / p->mu);
+    p->Lbar = sqrt(std::max(lbx, lby) / p->mu);
+    p->Lbar_p = sqrt(std::max(lpx, lpy) / p->mu);
+    double pmin = 1.0;
+    for (int l = 0; l < r; ++l) pmin = std::min(pmin, p->probs[l]);
+    double out[4];
+    imask_optimal_step(p->L, p->Lbar, p->Lbar_p, pmin, 200, out);
+    p->sigma = out[0];
+    p->theta = out[1];
+  } while (false);
+  cudaFreeAsync(mem, st);
+  scratch_free(s);
+  if (rc == IMASK_OK) {
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    if (e2 != cudaSuccess) return cuda_fail(e2, "plan constants");
+  }
+  if (rc == IMASK_OK && !(p->sigma > 0.0)) rc = fail(IMASK_ERR_INVALID, "no admissible step size");
+  return rc;
+}
+
+}  // namespace
+
+// ===================================================================================
+// C ABI
+// ===================================================================================
+extern "C" {
+
+const char *imask_last_error(void) { return t_err.c_str(); }
+
+int64_t imask_launch_count(void) { return launch_counter(); }
+
+imask_status imask_geometry_axis_split(const imask_desc *desc, int32_t *split, int32_t *first_x) {
+  imask_status rc = validate(desc);
+  if (rc != IMASK_OK) return rc;
+  if (!split || !first_x) return fail(IMASK_ERR_INVALID, "NULL output");
+  std::vector<int> s, f;
+  if ((rc = axis_split(*desc, s, f)) != IMASK_OK) return rc;
+  for (int a = 0; a < desc->n_angles; ++a) {
+    split[a] = s[a];
+    first_x[a] = f[a];
+  }
+  return IMASK_OK;
+}
+
+// Thm. 3 on the grid c = cbar (i + 1/2)/G, rho = (j + 1/2)/G: eta* = c when
+// p_min > (Lbar^2/rho (1 - (1+L^2)c) / (1 - (1+L^2+Lbar_p^2)c) + 1 - rho) c,
+// else the crossing (sqrt(1 + D (p_min + rho c)) - 1) / D, D = 1/alpha - 1/c;
+// theta = max(phi(eta*), psi(eta*)); the best (c, rho) wins; sigma = eta/(1-eta).
+imask_status imask_optimal_step(double L, double Lbar, double Lbar_p, double p_min, int32_t grid,
+                                double out[4]) {
+  if (!out) return fail(IMASK_ERR_INVALID, "NULL output");
+  if (!(L > 0) || !(Lbar > 0) || !(Lbar_p > 0) || !(p_min > 0) || p_min > 1 || grid < 1)
+    return fail(IMASK_ERR_INVALID, "optimal_step: invalid constants");
+  const double L2 = L * L, Lb2 = Lbar * Lbar, Lp2 = Lbar_p * Lbar_p;
+  const double cbar = 1.0 / (1.0 + L2 + Lp2);
+  double best = INFINITY, best_eta = 0, best_c = 0, best_rho = 0;
+  for (int i = 0; i < grid; ++i) {
+    const double c = cbar * ((double)i + 0.5) / (double)grid;
+    for (int j = 0; j < grid; ++j) {
+      const double rho = ((double)j + 0.5) / (double)grid;
+      const double ratio = (1.0 - (1.0 + L2) * c) / (1.0 - (1.0 + L2 + Lp2) * c);
+      const double ainv = Lb2 / (rho * c) * ratio;
+      double eta;
+      if (p_min > (Lb2 / rho * ratio + 1.0 - rho) * c) {
+        eta = c;
+      } else {
+        const double D = ainv - 1.0 / c;
+        eta = (sqrt(1.0 + D * (p_min + rho * c)) - 1.0) / D;
+      }
+      const double phi = (eta - c) * (eta - c) / c + 1.0 - (1.0 - rho) * c;
+      const double psi = ainv * eta * eta + 1.0 - p_min;
+      const double th = phi > psi ? phi : psi;
+      if (th < best) {
+        best = th;
+        best_eta = eta;
+        best_c = c;
+        best_rho = rho;
+      }
+    }
+  }
+  out[0] = best_eta / (1.0 - best_eta);
+  out[1] = best;
+  out[2] = best_c;
+  out[3] = best_rho;
+  return IMASK_OK;
+}
+
+imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
+  if (!plan_out) return fail(IMASK_ERR_INVALID, "plan_out is NULL");
+  *plan_out = nullptr;
+  imask_status rc = validate(desc);
+  if (rc != IMASK_OK) return rc;
+  imask_plan_s *p = new (std::nothrow) imask_plan_s();
+  if (!p) return fail(IMASK_ERR_OOM, "host allocation");
+  p->desc = *desc;
+  const int r = desc->levels;
+  for (int l = -1; l < r; ++l) {
+    const LevelGeom g = level_geom(*desc, l);
+    if (g.tc * g.ls > FP_STAGE_FLOATS) {
+      delete p;
+      return fail(IMASK_ERR_SHAPE, "level %d is too wide for the projector's strip buffer", l);
+    }
+  }
+  p->probs.resize(r);
+  for (int l = 0; l < r; ++l) p->probs[l] = desc->probs ? desc->probs[l] : 1.0 / (double)r;
+  p->desc.probs = nullptr;  // never keep the caller's pointer
+
+  if ((rc = axis_split(*desc, p->split, p->first_x)) != IMASK_OK) {
+    delete p;
+    return rc;
+  }
+  // ray list: x-major rays in sinogram order, then y-major rays
+  const int na = desc->n_angles, nd = desc->n_det;
+  const double pitch = pitch_of(*desc);
+  const double W = desc->fov, h = W / (double)desc->n;
+  std::vector<float4> rays((size_t)na * nd);
+  std::vector<ViewInfo> views(na);
+  int m_x = 0;
+  for (int a = 0; a < na; ++a) {
+    const int sp = p->split[a];
+    const bool fx = p->first_x[a] != 0;
+    const int xs = fx ? 0 : sp, xe = fx ? sp : nd;
+    m_x += xe - xs;
+    if (sp > 0 && sp < nd) p->n_split_views++;
+  }
+  int xi = 0, yi = m_x;
+  for (int a = 0; a < na; ++a) {
+    const int sp = p->split[a];
+    const bool fx = p->first_x[a] != 0;
+    ViewInfo v{};
+    v.xj0 = fx ? 0 : sp;
+    v.xj1 = fx ? sp : nd;
+    v.yj0 = fx ? sp : 0;
+    v.yj1 = fx ? nd : sp;
+    v.xoff = xi;
+    v.yoff = yi;
+    double ca = 0, sa = 0;
+    for (int j = 0; j < nd; ++j) {
+      double p0[2], dir[2];
+      ray_geom(*desc, pitch, a, j, p0, dir, &ca, &sa);
+      const bool xm = (j < sp) == fx;
+      double t, c0;
+      if (xm) {
+        t = dir[1] / dir[0];
+        c0 = p0[1] + (0.0 - p0[0]) * t;   // ray height at x = 0
+      } else {
+        t = dir[0] / dir[1];
+        c0 = p0[0] + (0.0 - p0[1]) * t;   // ray abscissa at y = 0
+      }
+      float4 e;
+      e.x = (float)((c0 + 0.5 * W) / h);
+      e.y = (float)t;
+      e.z = (float)(h * sqrt(1.0 + t * t));
+      int sidx = a * nd + j;
+      memcpy(&e.w, &sidx, sizeof(int));
+      rays[xm ? xi++ : yi++] = e;
+    }
+    v.c = (float)ca;
+    v.s = (float)sa;
+    views[a] = v;
+  }
+
+  DevPlan &dp = p->dp;
+  dp.n = desc->n;
+  dp.n_angles = na;
+  dp.n_det = nd;
+  dp.geometry = desc->geometry;
+  dp.levels = r;
+  dp.m = na * nd;
+  dp.d = desc->n * desc->n;
+  dp.m_x = m_x;
+  dp.fov = (float)W;
+  dp.inv_pitch = (float)(1.0 / pitch);
+  dp.center = (float)(0.5 * (double)(nd - 1));
+  dp.src_dist = (float)desc->src_dist;
+  dp.sd_dist = (float)(desc->src_dist + desc->det_dist);
+  for (int l = 0; l < IMASK_MAX_LEVELS; ++l) dp.probs[l] = l < r ? (float)p->probs[l] : 0.0f;
+  level_thresholds(p->probs, dp.thr);
+  dp.lg[0] = level_geom(*desc, -1);
+  for (int l = 0; l < r; ++l) dp.lg[l + 1] = level_geom(*desc, l);
+  dp.upd_tile = update_tile(desc->n, r);
+  p->n_cta_x = (m_x + FP_CHUNK - 1) / FP_CHUNK;
+  p->n_cta_y = (dp.m - m_x + FP_CHUNK - 1) / FP_CHUNK;
+
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_rays, rays.size() * sizeof(float4))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_views, views.size() * sizeof(ViewInfo))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess) {
+    imask_plan_destroy(p);
+    return cuda_fail(e, "cudaMalloc(plan)");
+  }
+  if ((e = cudaMemcpy(p->d_rays, rays.data(), rays.size() * sizeof(float4),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_views, views.data(), views.size() * sizeof(ViewInfo),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(p->d_err, 0, sizeof(unsigned int))) != cudaSuccess) {
+    imask_plan_destroy(p);
+    return cuda_fail(e, "upload plan");
+  }
+  dp.rays = p->d_rays;
+  dp.views = p->d_views;
+
+  cudaStream_t st = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+    imask_plan_destroy(p);
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  rc = plan_constants(p, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  if (rc != IMASK_OK) {
+    imask_plan_destroy(p);
+    return rc;
+  }
+  *plan_out = p;
+  return IMASK_OK;
+}
+
+imask_status imask_plan_destroy(imask_plan_t p) {
+  if (!p) return IMASK_OK;
+  cudaDeviceSynchronize();
+  if (p->d_rays) cudaFree(p->d_rays);
+  if (p->d_views) cudaFree(p->d_views);
+  if (p->d_err) cudaFree(p->d_err);
+  delete p;
+  return IMASK_OK;
+}
+
+imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
+  if (!p || !info) return fail(IMASK_ERR_INVALID, "NULL argument");
+  memset(info, 0, sizeof *info);
+  info->mu = p->mu;
+  info->sigma = p->sigma;
+  info->theta = p->theta;
+  info->L = p->L;
+  info->Lbar = p->Lbar;
+  info->Lbar_p = p->Lbar_p;
+  info->norm_K = p->norm_K;
+  info->n_meas = p->dp.m;
+  info->n_pix = p->dp.d;
+  info->levels = p->desc.levels;
+  info->n_xmajor_views_split = p->n_split_views;
+  info->n_xmajor_rays = p->dp.m_x;
+  return IMASK_OK;
+}
+
+imask_status imask_plan_axis_split(imask_plan_t p, int32_t *split, int32_t *first_x) {
+  if (!p || !split || !first_x) return fail(IMASK_ERR_INVALID, "NULL argument");
+  for (int a = 0; a < p->desc.n_angles; ++a) {
+    split[a] = p->split[a];
+    first_x[a] = p->first_x[a];
+  }
+  return IMASK_OK;
+}
+
+imask_status imask_plan_check(imask_plan_t p) {
+  if (!p) return fail(IMASK_ERR_INVALID, "NULL plan");
+  CK(cudaDeviceSynchronize(), "synchronise");
+  unsigned int flag = 0;
+  CK(cudaMemcpy(&flag, p->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
+  if (flag) {
+    cudaMemset(p->d_err, 0, sizeof flag);
+    return fail(IMASK_ERR_TIMEOUT, "a projector launch gave up waiting for its image strips");
+  }
+  return IMASK_OK;
+}
+
+imask_status imask_project(imask_plan_t p, int32_t level, const float *x_dev, float *sino_dev,
+                           void *stream) {
+  if (!p || !x_dev || !sino_dev) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (level < -1 || level >= p->desc.levels)
+    return fail(IMASK_ERR_INVALID, "level %d outside [-1, %d]", level, p->desc.levels - 1);
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch s;
+  imask_status rc = scratch_alloc(p, 1u << (level + 1), false, st, s);
+  if (rc != IMASK_OK) return rc;
+  rc = apply_K(p, level, x_dev, sino_dev, s, st);
+  scratch_free(s);
+  return rc;
+}
+
+imask_status imask_backproject(imask_plan_t p, int32_t level, const float *y_dev, float *img_dev,
+                               void *stream) {
+  if (!p || !y_dev || !img_dev) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (level < -1 || level >= p->desc.levels)
+    return fail(IMASK_ERR_INVALID, "level %d outside [-1, %d]", level, p->desc.levels - 1);
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch s;
+  imask_status rc = scratch_alloc(p, 0u, true, st, s);
+  if (rc != IMASK_OK) return rc;
+  rc = apply_KT(p, level, y_dev, img_dev, s, st);
+  scratch_free(s);
+  return rc;
+}
+
+imask_status imask_levels(imask_plan_t p, uint64_t seed, int64_t k0, int64_t n, int32_t *out_dev,
+                          void *stream) {
+  if (!p || (!out_dev && n > 0)) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (n < 0 || k0 < 0) return fail(IMASK_ERR_INVALID, "negative range");
+  CK(launch_levels(p->dp, seed, k0, n, out_dev, (cudaStream_t)stream), "levels launch");
+  return IMASK_OK;
+}
+
+imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t seed,
+                                imask_state_t *state_out, void *stream) {
+  if (!p || !b_dev || !state_out) return fail(IMASK_ERR_INVALID, "NULL argument");
+  *state_out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  imask_state_s *s = new (std::nothrow) imask_state_s();
+  if (!s) return fail(IMASK_ERR_OOM, "host allocation");
+  s->plan = p;
+  s->seed = seed;
+  s->stream = st;
+  const int r = p->desc.levels;
+  const size_t d = p->dp.d, m = p->dp.m;
+  Carve cv;
+  size_t o_x = cv.take(d), o_y0 = cv.take(m), o_y1 = cv.take(m), o_b = cv.take(m);
+  size_t o_psi = cv.take(m * r), o_psim = cv.take(m), o_phi0 = cv.take(d), o_phim = cv.take(d);
+  size_t o_g = cv.take(d);
+  size_t o_phic[IMASK_MAX_LEVELS] = {0};
+  for (int l = 1; l < r; ++l) {
+    const size_t nl = (size_t)p->dp.lg[l + 1].nl;
+    o_phic[l] = cv.take(nl * nl);
+  }
+  size_t o_tv = p->desc.reg == 1 ? cv.take(5 * d) : 0;
+  size_t o_T[IMASK_MAX_LEVELS + 1] = {0}, o_R[IMASK_MAX_LEVELS + 1] = {0};
+  for (int li = 1; li <= r; ++li) {
+    o_T[li] = cv.take(pad_floats(p->dp.lg[li]));
+    o_R[li] = cv.take(pad_floats(p->dp.lg[li]));
+  }
+  void *mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, cv.off * sizeof(float), st);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_fail(e, "cudaMallocAsync(state)");
+  }
+  float *B = (float *)mem;
+  s->block = B;
+  s->x = B + o_x;
+  s->y[0] = B + o_y0;
+  s->y[1] = B + o_y1;
+  s->b = B + o_b;
+  s->psi = B + o_psi;
+  s->psi_mean = B + o_psim;
+  s->phi0 = B + o_phi0;
+  s->phi_mean = B + o_phim;
+  s->g = B + o_g;
+  s->phic = B;
+  for (int l = 1; l < r; ++l) s->phic_off[l] = (long long)o_phic[l];
+  s->tv = p->desc.reg == 1 ? B + o_tv : nullptr;
+  for (int li = 1; li <= r; ++li) {
+    s->pads.T[li] = B + o_T[li];
+    s->pads.R[li] = B + o_R[li];
+  }
+  if ((e = cudaMemsetAsync(mem, 0, cv.off * sizeof(float), st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(s->b, b_dev, m * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
+          cudaSuccess) {
+    cudaFreeAsync(mem, st);
+    delete s;
+    return cuda_fail(e, "state init");
+  }
+  *state_out = s;
+  return IMASK_OK;
+}
+
+imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
+  if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
+  if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  s->stream = st;
+  const imask_plan_s *p = s->plan;
+  const DevPlan &P = p->dp;
+  const float sigma = (float)p->sigma;
+  const float inv_1ps = (float)(1.0 / (1.0 + p->sigma));
+  const float tau = (float)(p->sigma / p->mu);
+  for (int it = 0; it < n_iters; ++it) {
+    LevelSel sel{};
+    sel.fixed = -2;
+    sel.seed = s->seed;
+    sel.k = s->k;
+    const int lvl = g_prof.on ? lvl_host_draw(P, s->seed, s->k) : 0;
+    DualArgs D{};
+    D.on = 1;
+    D.y_in = s->y[s->cur];
+    D.y_out = s->y[1 - s->cur];
+    D.b = s->b;
+    D.psi = s->psi;
+    D.psi_mean = s->psi_mean;
+    D.sigma = sigma;
+    D.inv_1ps = inv_1ps;
+    {
+      ProfScope ps(0, lvl, st);
+      CK(launch_fp(P, sel, s->pads, nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, st),
+         "projector launch");
+    }
+    {
+      ProfScope ps(1, lvl, st);
+      CK(launch_bp(P, sel, s->y[s->cur], s->g, st), "back-projector launch");
+    }
+    PrimalArgs A{};
+    A.g = s->g;
+    A.x = s->x;
+    A.phi0 = s->phi0;
+    A.phic = s->phic;
+    for (int l = 0; l < IMASK_MAX_LEVELS; ++l) A.phic_off[l] = s->phic_off[l];
+    A.phi_mean = s->phi_mean;
+    A.tau = tau;
+    A.inv_1ps = inv_1ps;
+    A.prox_in_place = p->desc.reg == 0 ? 1 : 0;
+    {
+      ProfScope ps(2, lvl, st);
+      CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
+    }
+    if (p->desc.reg == 1) {
+      CK(launch_tv_prox(P, tau, (float)p->mu, (float)p->desc.tv_lambda, (float)p->desc.tv_eps,
+                        p->desc.tv_inner, s->x, s->tv, st),
+         "TV prox launch");
+      LevelSel nxt = sel;
+      nxt.k = s->k + 1;
+      CK(launch_sketch(P, nxt, s->x, s->pads, st), "sketch launch");
+    }
+    s->cur = 1 - s->cur;
+    s->k += 1;
+  }
+  return IMASK_OK;
+}
+
+int64_t imask_state_iteration(imask_state_t s) { return s ? s->k : -1; }
+
+imask_status imask_state_get(imask_state_t s, int32_t what, float *dst, void *stream) {
+  if (!s || !dst) return fail(IMASK_ERR_INVALID, "NULL argument");
+  const imask_plan_s *p = s->plan;
+  const float *src = nullptr;
+  size_t n = 0;
+  switch (what) {
+    case 0: src = s->x; n = p->dp.d; break;
+    case 1: src = s->y[s->cur]; n = p->dp.m; break;
+    case 2: src = s->phi_mean; n = p->dp.d; break;
+    case 3: src = s->psi_mean; n = p->dp.m; break;
+    default: return fail(IMASK_ERR_INVALID, "unknown state part %d", what);
+  }
+  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+     "copy state");
+  return IMASK_OK;
+}
+
+imask_status imask_state_get_x(imask_state_t s, float *x_dev, void *stream) {
+  return imask_state_get(s, 0, x_dev, stream);
+}
+
+imask_status imask_state_destroy(imask_state_t s) {
+  if (!s) return IMASK_OK;
+  if (s->block) cudaFreeAsync(s->block, s->stream);
+  delete s;
+  return IMASK_OK;
+}
+
+imask_status imask_solve(imask_plan_t p, const float *b_dev, uint64_t seed, int32_t iters,
+                         float *x_dev, void *stream) {
+  if (!p || !b_dev || !x_dev) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (iters < 0) return fail(IMASK_ERR_INVALID, "iters < 0");
+  imask_state_t s = nullptr;
+  imask_status rc = imask_state_create(p, b_dev, seed, &s, stream);
+  if (rc != IMASK_OK) return rc;
+  rc = imask_step(s, iters, stream);
+  if (rc == IMASK_OK) rc = imask_state_get_x(s, x_dev, stream);
+  imask_state_destroy(s);
+  return rc;
+}
+
+imask_status imask_rel_distance(int64_t n, const float *a_dev, const float *b_dev, double *out,
+                                void *stream) {
+  if (!a_dev || !b_dev || !out || n < 0) return fail(IMASK_ERR_INVALID, "bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  void *mem = nullptr;
+  CK(cudaMallocAsync(&mem, (2 * reduce_blocks() + 2) * sizeof(double), st), "cudaMallocAsync");
+  double *part = (double *)mem, *res = part + 2 * reduce_blocks();
+  double h[2] = {0, 0};
+  cudaError_t e = launch_diff64(n, a_dev, b_dev, part, res, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, st);
+  cudaFreeAsync(mem, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "rel_distance");
+  if (!isfinite(h[0]) || !isfinite(h[1])) return fail(IMASK_ERR_NONFINITE, "non-finite input");
+  *out = h[1] > 0 ? h[0] / h[1] : h[0];
+  return IMASK_OK;
+}
+
+imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_dev, double *out,
+                             void *stream) {
+  if (!p || !x_dev || !b_dev || !out) return fail(IMASK_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long d = p->dp.d, m = p->dp.m;
+  Scratch s;
+  unsigned mask = 0;
+  for (int li = 1; li <= p->desc.levels; ++li) mask |= 1u << li;
+  imask_status rc = scratch_alloc(p, mask, false, st, s);
+  if (rc != IMASK_OK) return rc;
+  void *mem = nullptr;
+  cudaError_t e = cudaMallocAsync(
+      &mem, (2 * align64(m)) * sizeof(float) + (2 * reduce_blocks() + 8) * sizeof(double), st);
+  if (e != cudaSuccess) {
+    scratch_free(s);
+    return cuda_fail(e, "cudaMallocAsync(objective)");
+  }
+  float *kx = (float *)mem, *t = kx + align64(m);
+  double *part = (double *)(t + align64(m)), *res = part + 2 * reduce_blocks();
+  double h[4] = {0, 0, 0, 0};
+  do {
+    if ((e = launch_fill(m, 0.0f, kx, st)) != cudaSuccess) break;
+    for (int l = 0; l < p->desc.levels && rc == IMASK_OK; ++l) {
+      rc = apply_K(p, l, x_dev, t, s, st);
+      if (rc == IMASK_OK) e = launch_axpy(m, (float)p->probs[l], t, kx, st);
+      if (e != cudaSuccess) break;
+    }
+    if (rc != IMASK_OK || e != cudaSuccess) break;
+    if ((e = launch_diff64(m, kx, b_dev, part, res, st)) != cudaSuccess) break;
+    if ((e = launch_dot64(d, x_dev, x_dev, part, res + 2, st)) != cudaSuccess) break;
+    if (p->desc.reg == 1 &&
+        (e = launch_tv_value64(p->dp, x_dev, (float)p->desc.tv_eps, part, res + 3, st)) !=
+            cudaSuccess)
+      break;
+    e = cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, st);
+  } while (false);
+  cudaFreeAsync(mem, st);
+  scratch_free(s);
+  if (rc != IMASK_OK) return rc;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "objective");
+  double obj = 0.5 * h[0] + 0.5 * p->mu * h[2];
+  if (p->desc.reg == 1) obj += p->desc.tv_lambda * h[3];
+  if (!isfinite(obj)) return fail(IMASK_ERR_NONFINITE, "objective is not finite");
+  *out = obj;
+  return IMASK_OK;
+}
+
+imask_status imask_profile_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  g_prof.on = on != 0;
+  return IMASK_OK;
+}
+
+imask_status imask_profile_read(double ms[24], int64_t count[24], int32_t reset) {
+  std::lock_guard<std::mutex> lk(g_prof.mu);
+  for (auto &r : g_prof.pending) {
+    float t = 0.0f;
+    if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+      g_prof.ms[r.kind * 8 + r.level] += t;
+      g_prof.count[r.kind * 8 + r.level] += 1;
+    }
+    g_prof.pool.push_back(r.a);
+    g_prof.pool.push_back(r.b);
+  }
+  g_prof.pending.clear();
+  for (int i = 0; i < 24; ++i) {
+    if (ms) ms[i] = g_prof.ms[i];
+    if (count) count[i] = g_prof.count[i];
+  }
+  if (reset) {
+    for (int i = 0; i < 24; ++i) {
+      g_prof.ms[i] = 0;
+      g_prof.count[i] = 0;
+    }
+  }
+  return IMASK_OK;
+}
+
+}  // extern "C"

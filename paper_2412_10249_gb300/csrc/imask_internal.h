@@ -1,0 +1,129 @@
+// imask_internal.h -- structures shared by the kernels and the host side of
+// libimask.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/imask.h"
+
+#define IMASK_MAX_LEVELS 8
+#define IMASK_PAD 4            // zero entries before and after every padded image line
+#define FP_THREADS 512         // forward projector: threads per CTA
+#define FP_RAYS 4              // forward projector: rays per thread
+#define FP_CHUNK (FP_THREADS * FP_RAYS)
+#define FP_STAGES 3            // TMA strip pipeline depth
+#define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
+#define BP_THREADS 256         // back-projector: threads per CTA
+#define BP_TILE0 16            // back-projector tile side at level 0
+#define UPD_THREADS 256        // sketch / update kernels: threads per CTA
+
+// Per-view data for the pixel-driven back-projector (32 bytes).
+struct ViewInfo {
+  float c, s;       // cos / sin of the view angle
+  int xj0, xj1;     // x-major rays of the view: j in [xj0, xj1)
+  int xoff;         // ray-list index of ray (a, xj0)
+  int yj0, yj1;     // y-major rays: j in [yj0, yj1)
+  int yoff;         // ray-list index of ray (a, yj0)
+};
+
+// Geometry of one level grid.  Index 0 of the tables below is the plain
+// full-resolution grid (level -1), index ell + 1 is level ell.
+struct LevelGeom {
+  int nl;          // grid side
+  int ls;          // padded line stride, nl + 2 * IMASK_PAD
+  int lines;       // lines allocated (a multiple of tc)
+  int tc;          // lines per TMA strip
+  float inv2l;     // 2^-ell (1 for level -1)
+  float scale2l;   // 2^ell
+  float hl;        // pixel width fov / nl
+  float cmid;      // (nl - 1) / 2
+  int bp_tile;     // back-projector tile side
+  int bp_tiles;    // back-projector tiles per side
+};
+
+// Everything the kernels need about a plan (passed by value).
+struct DevPlan {
+  int n, n_angles, n_det, geometry, levels;
+  int m, d;          // measurement and pixel counts
+  int m_x;           // x-major rays (the first m_x entries of the ray list)
+  float fov, inv_pitch, center, src_dist, sd_dist;
+  float probs[IMASK_MAX_LEVELS];
+  unsigned long long thr[IMASK_MAX_LEVELS];   // level thresholds (r - 1 used)
+  LevelGeom lg[IMASK_MAX_LEVELS + 1];
+  int upd_tile;      // fine-pixel tile side of the sketch / update kernels
+  const float4 *rays;      // ray list: (a_mid, slope, g, sino index bits)
+  const ViewInfo *views;   // per view
+};
+
+// Padded level images: for every level index li (0: level -1, ell + 1: ell),
+// an x-major copy (lines = columns, "T") and a y-major copy (lines = rows, "R").
+struct PadSet {
+  float *T[IMASK_MAX_LEVELS + 1];
+  float *R[IMASK_MAX_LEVELS + 1];
+};
+
+// Level selection for a launch: fixed >= -1 uses that level, otherwise the
+// level is drawn from (seed, k) on the device.
+struct LevelSel {
+  int fixed;
+  unsigned long long seed;
+  long long k;
+};
+
+// Dual epilogue (Alg. 1, the zeta and y updates) fused into the projector.
+struct DualArgs {
+  int on;
+  const float *y_in;
+  float *y_out;
+  const float *b;
+  float *psi;        // table base, level ell at psi + ell * m
+  float *psi_mean;   // sum_l p_l psi_l
+  float sigma, inv_1ps;
+};
+
+// Primal epilogue (Alg. 1, the xi and x updates) in the update kernel.
+struct PrimalArgs {
+  const float *g;    // R_ell^T y on the level grid (back-projector output)
+  float *x;          // iterate, updated in place
+  float *phi0;       // table entry of level 0 (n*n)
+  float *phic;       // tables of levels >= 1, stored on their own grids
+  long long phic_off[IMASK_MAX_LEVELS];
+  float *phi_mean;   // sum_l p_l phi_l (n*n)
+  float tau;         // sigma / mu
+  float inv_1ps;     // 1 / (1 + sigma)
+  int prox_in_place; // 1: quadratic prox here; 0: store v, a TV prox follows
+};
+
+// ---- kernel launchers (kernels.cu) -------------------------------------------
+extern "C++" {
+int lvl_host_draw(const DevPlan &P, unsigned long long seed, long long k);
+cudaError_t launch_levels(const DevPlan &P, unsigned long long seed, long long k0, long long n,
+                          int *out, cudaStream_t st);
+cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet pads,
+                          cudaStream_t st);
+cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
+                      int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st);
+cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g, cudaStream_t st);
+cudaError_t launch_adjsketch(const DevPlan &P, int ell, const float *g, float *img,
+                             cudaStream_t st);
+cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int write_sketch,
+                          PadSet pads, cudaStream_t st);
+cudaError_t launch_tv_prox(const DevPlan &P, float tau, float mu, float lam, float eps, int inner,
+                           float *x, float *work, cudaStream_t st);
+cudaError_t launch_axpy(long long n, float alpha, const float *x, float *y, cudaStream_t st);
+cudaError_t launch_scale(long long n, float alpha, float *x, cudaStream_t st);
+cudaError_t launch_fill(long long n, float v, float *x, cudaStream_t st);
+cudaError_t launch_copy(long long n, const float *x, float *y, cudaStream_t st);
+// FP64 reductions: out[0] = sum a*b (b may equal a), or sum (a-b)^2 and sum b^2.
+cudaError_t launch_dot64(long long n, const float *a, const float *b, double *partial,
+                         double *out, cudaStream_t st);
+cudaError_t launch_diff64(long long n, const float *a, const float *b, double *partial,
+                          double *out, cudaStream_t st);
+cudaError_t launch_tv_value64(const DevPlan &P, const float *x, float eps, double *partial,
+                              double *out, cudaStream_t st);
+int reduce_blocks();
+long long fp_smem_bytes();
+int64_t launch_counter();
+void count_launch();
+}

@@ -1,0 +1,808 @@
+// kernels.cu -- device code of libimask.so (sm_103a).
+//
+// The hot path of one ImaSk iteration (Alg. 1) is three launches:
+//   k_fp      forward projection K_ell x (Joseph, one ray per thread and slot)
+//             over image strips staged in shared memory by TMA bulk copies,
+//             with the dual SAGA update and dual prox fused into its epilogue;
+//   k_bp      pixel-driven back-projection R_ell^T y on the level grid (gather,
+//             no atomics), the exact transpose of k_fp's weights;
+//   k_update  the image-side adjoint sketch (T_ell^T or S_r), the primal SAGA
+//             update and prox, and the image-side sketch T_ell' / S_r of the
+//             new iterate for the next drawn level (fused "sketch on load").
+// The level of every launch is drawn on the device from (seed, k).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "imask_internal.h"
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+
+constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: floor via round-down add
+constexpr int kMagicBits = 0x4B400000;
+constexpr float kBpEps = 0.01f;          // slack (in bins) of the back-projector's ray range
+constexpr int kWaitLimit = 1 << 20;      // bounded mbarrier polls before giving up
+
+// ---------------------------------------------------------------------------------
+// Level draw: SplitMix64 output k of `seed` against the integer thresholds of the
+// cumulative probabilities (Alg. 1, sampling step).
+// ---------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
+                                                                     unsigned long long k) {
+  unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ int draw_level(const DevPlan &P, unsigned long long seed,
+                                                   long long k) {
+  const unsigned long long u = splitmix64_at(seed, (unsigned long long)k);
+  int l = 0;
+  for (int t = 0; t + 1 < P.levels; ++t) l += (u >= P.thr[t]) ? 1 : 0;
+  return l;
+}
+
+__device__ __forceinline__ int sel_level(const DevPlan &P, const LevelSel &s) {
+  return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed, s.k);
+}
+
+// ---------------------------------------------------------------------------------
+// mbarrier / TMA bulk-copy helpers (inline PTX)
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// One 1-D bulk copy global -> shared that completes a transaction on `bar`.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Polls the barrier phase `parity` at most kWaitLimit times.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------------
+// Forward projector (Joseph) with the fused dual epilogue.
+//
+// Rays are listed x-major first, then y-major.  CTA b < n_cta_x takes x-major
+// rays [b*FP_CHUNK, ...), the others y-major rays.  An x-major ray marches over
+// the columns of the x-major padded image (one line per column, rows
+// contiguous); at column c its fractional row is q = a_mid 2^-ell - 1/2 +
+// (c - (nl-1)/2) * slope and the sample is the linear interpolation of the two
+// neighbouring rows.  Strips of tc lines are streamed through FP_STAGES
+// shared-memory buffers by cp.async.bulk; zero padding of IMASK_PAD entries
+// on both sides of every line, with q clamped to [-2, nl + 1/2], makes rows off
+// the grid read as zero without a branch.
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(FP_THREADS, 2)
+    k_fp(DevPlan P, LevelSel sel, PadSet pads, float *sino, DualArgs D, int n_cta_x,
+         unsigned int *err) {
+  extern __shared__ __align__(128) float fp_smem[];
+  __shared__ __align__(8) unsigned long long full_bar[FP_STAGES];
+
+  const int ell = sel_level(P, sel);
+  const LevelGeom G = P.lg[ell + 1];
+  const bool xaxis = (int)blockIdx.x < n_cta_x;
+  const int chunk = xaxis ? (int)blockIdx.x : (int)blockIdx.x - n_cta_x;
+  const int begin = xaxis ? chunk * FP_CHUNK : P.m_x + chunk * FP_CHUNK;
+  const int end = xaxis ? min(begin + FP_CHUNK, P.m_x) : min(begin + FP_CHUNK, P.m);
+  const float *img = xaxis ? pads.T[ell + 1] : pads.R[ell + 1];
+  const int tid = threadIdx.x;
+
+  float q0[FP_RAYS], sl[FP_RAYS], acc[FP_RAYS], gsc[FP_RAYS];
+  int sidx[FP_RAYS];
+#pragma unroll
+  for (int r = 0; r < FP_RAYS; ++r) {
+    const int idx = begin + r * FP_THREADS + tid;
+    acc[r] = 0.0f;
+    if (idx < end) {
+      const float4 p = P.rays[idx];
+      q0[r] = fmaf(p.x, G.inv2l, -0.5f);
+      sl[r] = p.y;
+      gsc[r] = p.z;
+      sidx[r] = __float_as_int(p.w);
+    } else {
+      q0[r] = -4.0f;  // clamped to -2: reads the zero padding
+      sl[r] = 0.0f;
+      gsc[r] = 0.0f;
+      sidx[r] = -1;
+    }
+  }
+
+  const int tc = G.tc, ls = G.ls;
+  const int nstrips = G.lines / tc;
+  const uint32_t strip_bytes = (uint32_t)(tc * ls) * 4u;
+  if (tid == 0) {
+    for (int s = 0; s < FP_STAGES; ++s) mbar_init(smem_u32(&full_bar[s]), 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < FP_STAGES && s < nstrips; ++s)
+      bulk_load(smem_u32(fp_smem + s * FP_STAGE_FLOATS), img + (size_t)s * tc * ls, strip_bytes,
+                smem_u32(&full_bar[s]));
+  }
+
+  const float qhi = (float)G.nl + 0.5f;
+  bool failed = false;
+  for (int s = 0; s < nstrips; ++s) {
+    const int st = s % FP_STAGES;
+    const uint32_t parity = (uint32_t)((s / FP_STAGES) & 1);
+    const bool ok = mbar_wait(smem_u32(&full_bar[st]), parity);
+    const float *buf = fp_smem + st * FP_STAGE_FLOATS + IMASK_PAD;
+    const float cf0 = (float)(s * tc) - G.cmid;
+    float part[FP_RAYS];
+#pragma unroll
+    for (int r = 0; r < FP_RAYS; ++r) part[r] = 0.0f;
+    for (int cc = 0; cc < tc; cc += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float cf = cf0 + (float)(cc + u);
+        const float *line = buf + (cc + u) * ls;
+#pragma unroll
+        for (int r = 0; r < FP_RAYS; ++r) {
+          float q = fmaf(cf, sl[r], q0[r]);
+          q = fminf(fmaxf(q, -2.0f), qhi);
+          const float tq = __fadd_rd(q, kMagic);
+          const int i0 = __float_as_int(tq) - kMagicBits;
+          const float f = q - (tq - kMagic);
+          const float v0 = line[i0];
+          const float v1 = line[i0 + 1];
+          part[r] = fmaf(f, v1 - v0, part[r] + v0);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < FP_RAYS; ++r) acc[r] += part[r];
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0 && s + FP_STAGES < nstrips) {
+      fence_proxy_async();
+      bulk_load(smem_u32(fp_smem + st * FP_STAGE_FLOATS), img + (size_t)(s + FP_STAGES) * tc * ls,
+                strip_bytes, smem_u32(&full_bar[st]));
+    }
+  }
+  if (failed) {
+    if (tid == 0) {
+      atomicOr(err, 1u);
+      // give the copies still in flight a bounded chance to land before exit
+      for (int s = 0; s < FP_STAGES; ++s) mbar_wait(smem_u32(&full_bar[s]), 0);
+    }
+    return;
+  }
+
+#pragma unroll
+  for (int r = 0; r < FP_RAYS; ++r) {
+    if (sidx[r] < 0) continue;
+    const float v = acc[r] * (gsc[r] * G.scale2l);
+    const int q = sidx[r];
+    if (!D.on) {
+      sino[q] = v;
+    } else {
+      // Alg. 1: zeta = psi_new - psi_l + sum p psi; y+ = (y + s zeta - s b)/(1+s);
+      // the running mean and the table entry take the refreshed value.
+      float *psil = D.psi + (size_t)ell * P.m;
+      const float po = psil[q];
+      const float pm = D.psi_mean[q];
+      const float zeta = v - po + pm;
+      D.y_out[q] = fmaf(D.sigma, zeta - D.b[q], D.y_in[q]) * D.inv_1ps;
+      D.psi_mean[q] = fmaf(P.probs[ell], v - po, pm);
+      psil[q] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Pixel-driven back-projector: g = R_ell^T y on the level grid.
+//
+// A CTA covers a t x t tile of level pixels and splits the views into
+// 256 / t^2 groups; each thread gathers, for its pixel and each of its views,
+// the rays whose interpolation weight at the pixel is non-zero.  For x-major
+// rays these are the bins j whose ray height at the pixel's column lies within
+// one pixel width of the pixel centre: the preimage of that interval under the
+// (affine or linear-fractional) bin map, widened by kBpEps bins.  The weight is
+// max(0, 1 - |q - i|) with q computed exactly as in k_fp, so the two kernels
+// use the same numbers.  View groups are summed in shared memory.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ float bin_of(const DevPlan &P, const ViewInfo &V, float x, float y) {
+  if (P.geometry == 0) return fmaf(fmaf(x, V.c, y * V.s), P.inv_pitch, P.center);
+  const float num = fmaf(-x, V.s, y * V.c);
+  const float den = P.src_dist - fmaf(x, V.c, y * V.s);
+  return fmaf(P.sd_dist * num / den, P.inv_pitch, P.center);
+}
+
+__global__ void __launch_bounds__(BP_THREADS)
+    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ g) {
+  __shared__ float red[BP_THREADS];
+  const int ell = sel_level(P, sel);
+  const LevelGeom G = P.lg[ell + 1];
+  const int t = G.bp_tile, tt = t * t, VG = BP_THREADS / tt;
+  const int nt = G.bp_tiles;
+  if ((int)blockIdx.x >= nt * nt) return;
+  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
+  const int lp = threadIdx.x % tt, vg = threadIdx.x / tt;
+  const int i = ti * t + lp / t, c = tj * t + lp % t;
+  const bool valid = (i < G.nl) && (c < G.nl);
+  float acc = 0.0f;
+  if (valid) {
+    const float hl = G.hl;
+    const float xc = -0.5f * P.fov + ((float)c + 0.5f) * hl;
+    const float yi = -0.5f * P.fov + ((float)i + 0.5f) * hl;
+    const float cm = (float)c - G.cmid, im = (float)i - G.cmid;
+    const float fi = (float)i, fc = (float)c;
+    for (int a = vg; a < P.n_angles; a += VG) {
+      const ViewInfo V = P.views[a];
+      const float *ya = y + (size_t)a * P.n_det;
+      if (V.xj1 > V.xj0) {
+        const float ja = bin_of(P, V, xc, yi - hl), jb = bin_of(P, V, xc, yi + hl);
+        const int lo = (int)fmaxf(ceilf(fminf(ja, jb) - kBpEps), (float)V.xj0);
+        const int hi = (int)fminf(floorf(fmaxf(ja, jb) + kBpEps), (float)(V.xj1 - 1));
+        const float4 *rp = P.rays + (V.xoff - V.xj0);
+        for (int j = lo; j <= hi; ++j) {
+          const float4 r = rp[j];
+          const float q = fmaf(cm, r.y, fmaf(r.x, G.inv2l, -0.5f));
+          const float w = fmaxf(0.0f, 1.0f - fabsf(q - fi));
+          acc = fmaf(w * r.z, __ldg(ya + j), acc);
+        }
+      }
+      if (V.yj1 > V.yj0) {
+        const float ja = bin_of(P, V, xc - hl, yi), jb = bin_of(P, V, xc + hl, yi);
+        const int lo = (int)fmaxf(ceilf(fminf(ja, jb) - kBpEps), (float)V.yj0);
+        const int hi = (int)fminf(floorf(fmaxf(ja, jb) + kBpEps), (float)(V.yj1 - 1));
+        const float4 *rp = P.rays + (V.yoff - V.yj0);
+        for (int j = lo; j <= hi; ++j) {
+          const float4 r = rp[j];
+          const float q = fmaf(im, r.y, fmaf(r.x, G.inv2l, -0.5f));
+          const float w = fmaxf(0.0f, 1.0f - fabsf(q - fc));
+          acc = fmaf(w * r.z, __ldg(ya + j), acc);
+        }
+      }
+    }
+    acc *= G.scale2l;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = VG >> 1; s > 0; s >>= 1) {
+    if (vg < s) red[threadIdx.x] += red[threadIdx.x + s * tt];
+    __syncthreads();
+  }
+  if (vg == 0 && valid) g[(size_t)i * G.nl + c] = red[threadIdx.x];
+}
+
+// ---------------------------------------------------------------------------------
+// Image-side sketches on fine-pixel tiles of side P.upd_tile (a multiple of
+// 2^(r-1) that divides n), so every block of every level lies inside one tile.
+// ---------------------------------------------------------------------------------
+
+// Block means of the tile `src` (side ts) at levels 1..r-1, level l at
+// pyr + pyr_off(l), side ts >> l.  Hierarchical 2x2 means.
+__device__ void tile_pyramid(const float *src, float *pyr, int ts, int r) {
+  const float *prev = src;
+  int ps = ts, off = 0;
+  for (int l = 1; l < r; ++l) {
+    const int s = ps >> 1;
+    float *cur = pyr + off;
+    for (int p = threadIdx.x; p < s * s; p += blockDim.x) {
+      const int I = p / s, J = p % s;
+      const float *q = prev + (2 * I) * ps + 2 * J;
+      cur[p] = 0.25f * ((q[0] + q[1]) + (q[ps] + q[ps + 1]));
+    }
+    __syncthreads();
+    prev = cur;
+    ps = s;
+    off += s * s;
+  }
+}
+
+__device__ __forceinline__ int pyr_off(int ts, int l) {
+  int off = 0;
+  for (int k = 1; k < l; ++k) off += (ts >> k) * (ts >> k);
+  return off;
+}
+
+// S_r v at tile pixel (li, lj): (v - sum_{l>=1} p_l mean_l) / p_0.
+__device__ __forceinline__ float compensate_px(const DevPlan &P, float v, const float *pyr, int ts,
+                                               int li, int lj) {
+  float s = v;
+  int off = 0;
+  for (int l = 1; l < P.levels; ++l) {
+    const int side = ts >> l;
+    s = fmaf(-P.probs[l], pyr[off + (li >> l) * side + (lj >> l)], s);
+    off += side * side;
+  }
+  return s / P.probs[0];
+}
+
+// Writes the tile's contribution to the padded images of level `ell`
+// (-1: plain grid).  `vals` holds the level values of the tile (side `side`).
+__device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, const float *vals,
+                             int side, int ti0, int tj0) {
+  const int li = ell + 1;
+  const LevelGeom G = P.lg[li];
+  const int sh = ell > 0 ? ell : 0;
+  const int I0 = ti0 >> sh, J0 = tj0 >> sh;
+  float *R = pads.R[li];
+  float *T = pads.T[li];
+  for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
+    const int I = p / side, J = p % side;
+    R[(size_t)(I0 + I) * G.ls + IMASK_PAD + J0 + J] = vals[I * side + J];
+  }
+  for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
+    const int J = p / side, I = p % side;
+    T[(size_t)(J0 + J) * G.ls + IMASK_PAD + I0 + I] = vals[I * side + J];
+  }
+}
+
+// Sketch of the tile held in xs (fine values) for level ell; uses aux and pyr.
+__device__ void sketch_tile(const DevPlan &P, const PadSet &pads, int ell, float *xs, float *aux,
+                            float *pyr, int ts, int ti0, int tj0) {
+  if (ell < 0) {
+    write_padded(P, pads, -1, xs, ts, ti0, tj0);
+    return;
+  }
+  if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
+  if (ell == 0) {
+    for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
+      aux[p] = compensate_px(P, xs[p], pyr, ts, p / ts, p % ts);
+    __syncthreads();
+    write_padded(P, pads, 0, aux, ts, ti0, tj0);
+  } else {
+    write_padded(P, pads, ell, pyr + pyr_off(ts, ell), ts >> ell, ti0, tj0);
+  }
+}
+
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_sketch(DevPlan P, LevelSel sel, const float *__restrict__ x, PadSet pads) {
+  extern __shared__ __align__(16) float upd_smem[];
+  const int ts = P.upd_tile, ntx = P.n / ts;
+  float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
+  const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
+  const int ell = sel_level(P, sel);
+  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
+    xs[p] = x[(size_t)(ti0 + p / ts) * P.n + tj0 + p % ts];
+  __syncthreads();
+  sketch_tile(P, pads, ell, xs, aux, pyr, ts, ti0, tj0);
+}
+
+// img = K_ell^T-side image map of g: ell >= 1: 4^-ell T^* g; ell = 0: S_r g;
+// ell = -1: g.
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_adjsketch(DevPlan P, int ell, const float *__restrict__ g, float *__restrict__ img) {
+  extern __shared__ __align__(16) float upd_smem[];
+  const int ts = P.upd_tile, ntx = P.n / ts;
+  float *xs = upd_smem, *pyr = xs + 2 * ts * ts;
+  const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
+  const int n = P.n;
+  if (ell < 0) {
+    for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
+      const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
+      img[gp] = g[gp];
+    }
+    return;
+  }
+  if (ell >= 1) {
+    const LevelGeom G = P.lg[ell + 1];
+    const float s = G.inv2l * G.inv2l;
+    for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
+      const int fi = ti0 + p / ts, fj = tj0 + p % ts;
+      img[(size_t)fi * n + fj] = g[(size_t)(fi >> ell) * G.nl + (fj >> ell)] * s;
+    }
+    return;
+  }
+  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
+    xs[p] = g[(size_t)(ti0 + p / ts) * n + tj0 + p % ts];
+  __syncthreads();
+  if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
+  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
+    img[(size_t)(ti0 + p / ts) * n + tj0 + p % ts] = compensate_px(P, xs[p], pyr, ts, p / ts, p % ts);
+}
+
+// Primal half of Alg. 1 on one tile, then the sketch of the new iterate for
+// the next level.  phi_new = 4^-ell T^*(g) (ell >= 1, block-constant, kept on
+// the level grid) or S_r g (ell = 0); xi = phi_new - phi_ell + sum p phi;
+// x+ = prox(x - (sigma/mu) xi); the running mean and the table take phi_new.
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_update(DevPlan P, LevelSel sel, PrimalArgs A, int write_sketch, PadSet pads) {
+  extern __shared__ __align__(16) float upd_smem[];
+  const int ts = P.upd_tile, ntx = P.n / ts;
+  float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
+  float *dc = pyr + ts * ts / 2 + 4;
+  const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
+  const int n = P.n;
+  const int ell = sel_level(P, sel);
+  const float pl = P.probs[ell];
+
+  int cs = 0;
+  if (ell >= 1) {
+    const LevelGeom G = P.lg[ell + 1];
+    cs = ts >> ell;
+    const int I0 = ti0 >> ell, J0 = tj0 >> ell;
+    float *phic = A.phic + A.phic_off[ell];
+    const float inv4l = G.inv2l * G.inv2l;
+    for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
+      const size_t gi = (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
+      const float cnew = A.g[gi] * inv4l;
+      dc[p] = cnew - phic[gi];
+      phic[gi] = cnew;
+    }
+    __syncthreads();
+  } else {
+    for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
+      aux[p] = A.g[(size_t)(ti0 + p / ts) * n + tj0 + p % ts];
+    __syncthreads();
+    if (P.levels > 1) tile_pyramid(aux, pyr, ts, P.levels);
+  }
+
+  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
+    const int li = p / ts, lj = p % ts;
+    const size_t gp = (size_t)(ti0 + li) * n + tj0 + lj;
+    float delta;
+    if (ell >= 1) {
+      delta = dc[(li >> ell) * cs + (lj >> ell)];
+    } else {
+      const float s0 = compensate_px(P, aux[p], pyr, ts, li, lj);
+      delta = s0 - A.phi0[gp];
+      A.phi0[gp] = s0;
+    }
+    const float pm = A.phi_mean[gp];
+    const float xi = delta + pm;
+    const float v = fmaf(-A.tau, xi, A.x[gp]);
+    A.phi_mean[gp] = fmaf(pl, delta, pm);
+    const float xn = A.prox_in_place ? v * A.inv_1ps : v;
+    A.x[gp] = xn;
+    xs[p] = xn;
+  }
+  if (!write_sketch) return;
+  __syncthreads();
+  const int elln = draw_level(P, sel.seed, sel.k + 1);
+  sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0);
+}
+
+// ---------------------------------------------------------------------------------
+// Smoothed-TV prox by FISTA (fixed step count), global-memory kernels.
+// F(x) = 1/2|x - v|^2 + tau mu/2 |x|^2 + tau lam sum sqrt(|grad x|^2 + eps^2)
+// ---------------------------------------------------------------------------------
+__global__ void k_tv_dual(int n, const float *__restrict__ z, float eps, float *__restrict__ w1,
+                          float *__restrict__ w2) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)n * n) return;
+  const int i = (int)(p / n), j = (int)(p % n);
+  const float zp = z[p];
+  const float g1 = (i + 1 < n) ? z[p + n] - zp : 0.0f;
+  const float g2 = (j + 1 < n) ? z[p + 1] - zp : 0.0f;
+  const float inv = rsqrtf(fmaf(g1, g1, fmaf(g2, g2, eps * eps)));
+  w1[p] = g1 * inv;
+  w2[p] = g2 * inv;
+}
+
+__global__ void k_tv_step(int n, const float *__restrict__ v, float *__restrict__ xk,
+                          float *__restrict__ z, const float *__restrict__ w1,
+                          const float *__restrict__ w2, float tau_mu, float tau_lam, float inv_L,
+                          float beta, float *__restrict__ out) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)n * n) return;
+  const int i = (int)(p / n), j = (int)(p % n);
+  // transpose of the forward differences applied to (w1, w2)
+  float div = 0.0f;
+  if (i + 1 < n) div -= w1[p];
+  if (i >= 1) div += w1[p - n];
+  if (j + 1 < n) div -= w2[p];
+  if (j >= 1) div += w2[p - 1];
+  const float zp = z[p];
+  const float grad = (zp - v[p]) + tau_mu * zp + tau_lam * div;
+  const float xn = zp - grad * inv_L;
+  const float xo = xk[p];
+  xk[p] = xn;
+  z[p] = fmaf(beta, xn - xo, xn);
+  if (out) out[p] = xn;
+}
+
+// ---------------------------------------------------------------------------------
+// Elementwise helpers and FP64 reductions
+// ---------------------------------------------------------------------------------
+__global__ void k_levels(DevPlan P, unsigned long long seed, long long k0, long long n, int *out) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = draw_level(P, seed, k0 + t);
+}
+
+__global__ void k_axpy(long long n, float a, const float *__restrict__ x, float *__restrict__ y) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = fmaf(a, x[t], y[t]);
+}
+
+__global__ void k_scale(long long n, float a, float *x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] *= a;
+}
+
+__global__ void k_fill(long long n, float v, float *x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] = v;
+}
+
+__global__ void k_copy(long long n, const float *__restrict__ x, float *__restrict__ y) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = x[t];
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 304;
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < kRedThreads / 32; ++w) s += sh[w];
+  __syncthreads();
+  return s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_dot64(long long n, const float *__restrict__ a, const float *__restrict__ b, double *part) {
+  double s = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    s = fma((double)a[t], (double)b[t], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_diff64(long long n, const float *__restrict__ a, const float *__restrict__ b, double *part) {
+  double s = 0.0, q = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double d = (double)a[t] - (double)b[t];
+    s = fma(d, d, s);
+    q = fma((double)b[t], (double)b[t], q);
+  }
+  s = block_sum(s);
+  q = block_sum(q);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s;
+    part[2 * blockIdx.x + 1] = q;
+  }
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_tv64(int n, const float *__restrict__ x, double eps, double *part) {
+  double s = 0.0;
+  const long long d = (long long)n * n;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < d;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(p / n), j = (int)(p % n);
+    const double g1 = (i + 1 < n) ? (double)x[p + n] - (double)x[p] : 0.0;
+    const double g2 = (j + 1 < n) ? (double)x[p + 1] - (double)x[p] : 0.0;
+    s += sqrt(g1 * g1 + g2 * g2 + eps * eps);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// Deterministic final sum of `nb` partials with stride `stride` (component `comp`).
+__global__ void k_final64(const double *part, int nb, int stride, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int c = 0; c < stride; ++c) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b * stride + c];
+    out[c] = s;
+  }
+}
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  if (b > 4096) b = 4096;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+inline int upd_smem_bytes(const DevPlan &P) {
+  const int ts = P.upd_tile;
+  return (int)sizeof(float) * (ts * ts * 2 + ts * ts / 2 + 4 + ts * ts / 4 + 4);
+}
+
+}  // namespace
+
+// ===================================================================================
+// launchers
+// ===================================================================================
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+int64_t launch_counter() { return g_launches.load(std::memory_order_relaxed); }
+int reduce_blocks() { return kRedBlocks; }
+long long fp_smem_bytes() { return (long long)FP_STAGES * FP_STAGE_FLOATS * (long long)sizeof(float); }
+
+int lvl_host_draw(const DevPlan &P, unsigned long long seed, long long k) {
+  return draw_level(P, seed, k);
+}
+
+cudaError_t launch_levels(const DevPlan &P, unsigned long long seed, long long k0, long long n,
+                          int *out, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_levels<<<grid_for(n, 256), 256, 0, st>>>(P, seed, k0, n, out);
+  return cudaGetLastError();
+}
+
+static cudaError_t set_smem(const void *fn, int bytes) {
+  static_assert(sizeof(int) == 4, "");
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet pads,
+                          cudaStream_t st) {
+  const int nt = P.n / P.upd_tile;
+  const int sm = upd_smem_bytes(P);
+  cudaError_t e = set_smem((const void *)k_sketch, sm);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_sketch<<<nt * nt, UPD_THREADS, sm, st>>>(P, sel, x, pads);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
+                      int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st) {
+  const int sm = (int)fp_smem_bytes();
+  cudaError_t e = set_smem((const void *)k_fp, sm);
+  if (e != cudaSuccess) return e;
+  if (n_cta_x + n_cta_y == 0) return cudaSuccess;
+  count_launch();
+  k_fp<<<n_cta_x + n_cta_y, FP_THREADS, sm, st>>>(P, sel, pads, sino, dual, n_cta_x, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g, cudaStream_t st) {
+  // the grid covers the level with the most tiles; extra CTAs return at once
+  int most = 0;
+  for (int li = 0; li <= P.levels; ++li) most = max(most, P.lg[li].bp_tiles * P.lg[li].bp_tiles);
+  if (sel.fixed >= -1) most = P.lg[sel.fixed + 1].bp_tiles * P.lg[sel.fixed + 1].bp_tiles;
+  count_launch();
+  k_bp<<<most, BP_THREADS, 0, st>>>(P, sel, y, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjsketch(const DevPlan &P, int ell, const float *g, float *img,
+                             cudaStream_t st) {
+  const int nt = P.n / P.upd_tile;
+  const int sm = upd_smem_bytes(P);
+  cudaError_t e = set_smem((const void *)k_adjsketch, sm);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_adjsketch<<<nt * nt, UPD_THREADS, sm, st>>>(P, ell, g, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int write_sketch,
+                          PadSet pads, cudaStream_t st) {
+  const int nt = P.n / P.upd_tile;
+  const int sm = upd_smem_bytes(P);
+  cudaError_t e = set_smem((const void *)k_update, sm);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_update<<<nt * nt, UPD_THREADS, sm, st>>>(P, sel, pa, write_sketch, pads);
+  return cudaGetLastError();
+}
+
+// work: 4 * n*n floats (v, x_k, z, w1 | w2 uses the 5th block: caller passes 5 n*n).
+cudaError_t launch_tv_prox(const DevPlan &P, float tau, float mu, float lam, float eps, int inner,
+                           float *x, float *work, cudaStream_t st) {
+  const long long d = (long long)P.n * P.n;
+  float *v = work, *xk = work + d, *z = work + 2 * d, *w1 = work + 3 * d, *w2 = work + 4 * d;
+  const int blocks = (int)((d + 255) / 256);
+  count_launch();
+  k_copy<<<grid_for(d, 256), 256, 0, st>>>(d, x, v);
+  count_launch();
+  k_copy<<<grid_for(d, 256), 256, 0, st>>>(d, x, xk);
+  count_launch();
+  k_copy<<<grid_for(d, 256), 256, 0, st>>>(d, x, z);
+  const float L = 1.0f + tau * mu + 8.0f * tau * lam / eps;
+  double t = 1.0;
+  for (int it = 0; it < inner; ++it) {
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const float beta = (float)((t - 1.0) / tn);
+    t = tn;
+    count_launch();
+    k_tv_dual<<<blocks, 256, 0, st>>>(P.n, z, eps, w1, w2);
+    count_launch();
+    k_tv_step<<<blocks, 256, 0, st>>>(P.n, v, xk, z, w1, w2, tau * mu, tau * lam, 1.0f / L, beta,
+                                      it + 1 == inner ? x : nullptr);
+  }
+  if (inner <= 0) {
+    count_launch();
+    k_copy<<<grid_for(d, 256), 256, 0, st>>>(d, v, x);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(long long n, float alpha, const float *x, float *y, cudaStream_t st) {
+  count_launch();
+  k_axpy<<<grid_for(n, 256), 256, 0, st>>>(n, alpha, x, y);
+  return cudaGetLastError();
+}
+cudaError_t launch_scale(long long n, float alpha, float *x, cudaStream_t st) {
+  count_launch();
+  k_scale<<<grid_for(n, 256), 256, 0, st>>>(n, alpha, x);
+  return cudaGetLastError();
+}
+cudaError_t launch_fill(long long n, float v, float *x, cudaStream_t st) {
+  count_launch();
+  k_fill<<<grid_for(n, 256), 256, 0, st>>>(n, v, x);
+  return cudaGetLastError();
+}
+cudaError_t launch_copy(long long n, const float *x, float *y, cudaStream_t st) {
+  count_launch();
+  k_copy<<<grid_for(n, 256), 256, 0, st>>>(n, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot64(long long n, const float *a, const float *b, double *partial, double *out,
+                         cudaStream_t st) {
+  count_launch();
+  k_dot64<<<kRedBlocks, kRedThreads, 0, st>>>(n, a, b, partial);
+  count_launch();
+  k_final64<<<1, 32, 0, st>>>(partial, kRedBlocks, 1, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diff64(long long n, const float *a, const float *b, double *partial,
+                          double *out, cudaStream_t st) {
+  count_launch();
+  k_diff64<<<kRedBlocks, kRedThreads, 0, st>>>(n, a, b, partial);
+  count_launch();
+  k_final64<<<1, 32, 0, st>>>(partial, kRedBlocks, 2, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tv_value64(const DevPlan &P, const float *x, float eps, double *partial,
+                              double *out, cudaStream_t st) {
+  count_launch();
+  k_tv64<<<kRedBlocks, kRedThreads, 0, st>>>(P.n, x, (double)eps, partial);
+  count_launch();
+  k_final64<<<1, 32, 0, st>>>(partial, kRedBlocks, 1, out);
+  return cudaGetLastError();
+}
