@@ -1,0 +1,420 @@
+"""Throughput benchmark of the ImaSk hot path on the 512x512 fan-beam workload.
+
+Workload (one "step" = one whole ImaSk solve): 512x512 random-ellipse phantom,
+fan beam with 720 views over 2 pi and 768 bins, source 2W and detector 1W from
+the centre, Poisson counts with I0 = 1e4 then log-transformed, four levels
+(512/256/128/64) drawn uniformly, quadratic regulariser with mu and sigma
+chosen by the plan (power method + Thm. 3), 500 iterations of Alg. 1.
+
+Our arm: each step solves from b resident in HBM (seed = step index) through
+the C ABI (imask_solve).  Per-step device time comes from CUDA events on the
+solve's stream; L2 is flushed (a 512 MB write) between steps, outside the
+events.  ``e2e`` repeats the steps with the measurement vector in pinned host
+memory: H2D copy of b, the solve, D2H copy of x, all inside the timed region.
+
+Reference arm (--impl reference): the FP64 CPU oracle, as it stands, on a
+bounded sample of the same workload (a few Alg. 1 iterations per step),
+converted to solves/s through the ray-samples it processed.
+
+Under torchrun (N > 1) every rank runs its own replica of the workload (no
+collective on the data path; "scaling": "weak"); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2412_10249_gb300 import inputs  # noqa: E402
+
+METRIC = "ImaSk solves/sec & Gray-samples/s at rel.err≤1e-3 vs plain FP32 form; p99 ms"
+WORKLOAD = "fan512: 512x512 fan beam 720x768, r=4 uniform, K=500, quadratic R"
+ITERS = 500
+
+
+def samples_per_iteration(p: inputs.Problem, levels) -> np.ndarray:
+    """Joseph samples (forward + back) of each iteration: 2 m N_ell."""
+    lv = np.asarray(levels)
+    return 2.0 * p.m * (p.n >> lv)
+
+
+def expected_samples_per_solve(p: inputs.Problem, iters: int = ITERS) -> float:
+    pr = np.full(p.levels, 1.0 / p.levels) if p.probs is None else np.asarray(p.probs)
+    return iters * 2.0 * p.m * sum(pr[l] * (p.n >> l) for l in range(p.levels))
+
+
+# ---------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [s.strip() for s in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return float("nan")
+
+        sm = np.array([num(r[1]) for r in rows])
+        mx = np.array([num(r[2]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------
+# distributed plumbing (replicas)
+# ---------------------------------------------------------------------------------
+def dist_setup(use_cuda: bool):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return world, rank, local
+
+
+def dist_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_sum(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# ---------------------------------------------------------------------------------
+def oracle_sample(p: inputs.Problem, params: dict, b: np.ndarray, seed: int, iters: int):
+    """Runs `iters` oracle iterations of the workload; returns (seconds, samples)."""
+    from oracle import Oracle
+    o = Oracle(**params)
+    t0 = time.perf_counter()
+    _, lv = o.run(b, seed, iters)
+    dt = time.perf_counter() - t0
+    return dt, float(samples_per_iteration(p, lv).sum())
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(False)
+    if rank != 0:
+        return 0
+    p = inputs.fan512_problem()
+    _, b, _ = inputs.measurements(p, seed=0)
+    # the oracle needs mu and sigma; use the values the GPU plan derives for
+    # this workload (recorded below) so both arms run the same iteration
+    params = dict(p.params(), mu=args.mu, sigma=args.sigma)
+    per_solve = expected_samples_per_solve(p)
+    for w in range(args.warmup):
+        oracle_sample(p, params, b.ravel(), 1000 + w, args.ref_iters)
+    times, samples = [], []
+    for k in range(args.steps):
+        dt, sm = oracle_sample(p, params, b.ravel(), k, args.ref_iters)
+        times.append(dt)
+        samples.append(sm)
+    T, S = sum(times), sum(samples)
+    gs = S / T / 1e9
+    solves = S / per_solve / T
+    line = {
+        "impl": "reference", "metric": METRIC, "value": solves, "unit": "solves/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "gsamples_per_s": gs,
+        "cpu_baseline": {"value": solves, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.ref_iters} oracle iterations per step of the "
+                                   f"fan512 solve, extrapolated by ray-samples to a "
+                                   f"{ITERS}-iteration solve"},
+        "e2e": {"value": solves, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(True)
+    torch.cuda.set_device(local)
+    from paper_2412_10249_gb300 import build as pkg_build
+    if rank == 0 or world == 1:
+        pkg_build.build()
+    dist_barrier(world)
+    from paper_2412_10249_gb300 import imask
+
+    p = inputs.fan512_problem()
+    _, b, _ = inputs.measurements(p, seed=rank)
+    bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
+    # mu and sigma: derived by the plan (power method + Thm. 3) unless given
+    plan = imask.Plan(dict(p.params(), mu=max(args.mu, 0.0), sigma=max(args.sigma, 0.0)))
+    info = plan.info
+    stream = torch.cuda.Stream()
+    x = torch.empty(p.d, device="cuda", dtype=torch.float32)
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+
+    # level streams (our device draw) to count the ray-samples of every step
+    seeds = [rank * 100003 + k for k in range(args.steps)]
+    samples = []
+    for sd in seeds:
+        lv = plan.levels(sd, 0, args.iters).cpu().numpy()
+        samples.append(float(samples_per_iteration(p, lv).sum()))
+
+    with torch.cuda.stream(stream):
+        for w in range(args.warmup):
+            plan.solve(bt, 10**6 + w, args.iters, out=x, stream=stream)
+    stream.synchronize()
+
+    clocks = ClockSampler(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in seeds]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in seeds]
+    imask.imask_profile_read(reset=True)
+    imask.imask_profile_enable(True)
+    launches0 = imask.imask_launch_count()
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k, sd in enumerate(seeds):
+            flush.fill_(float(k))   # evict the previous solve's state from L2
+            starts[k].record(stream)
+            plan.solve(bt, sd, args.iters, out=x, stream=stream)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    dist_barrier(world)
+    clk = clocks.stop()
+    launches = imask.imask_launch_count() - launches0
+    imask.imask_profile_enable(False)
+    prof_ms, prof_cnt = imask.imask_profile_read(reset=True)
+    plan.check()
+
+    step_ms = np.array([s.elapsed_time(e) for s, e in zip(starts, ends)])
+    T = float(step_ms.sum()) / 1e3
+    T_max = dist_max(T, world)
+    total_solves = args.steps * world
+    value = total_solves / T_max
+    gs = dist_sum(sum(samples), world) / T_max / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    b_host = torch.empty(p.m, dtype=torch.float32, pin_memory=True)
+    b_host.copy_(torch.as_tensor(b.ravel().astype(np.float32)))
+    x_host = torch.empty(p.d, dtype=torch.float32, pin_memory=True)
+    bdev = torch.empty(p.m, device="cuda", dtype=torch.float32)
+    e2e_s = torch.cuda.Event(enable_timing=True)
+    e2e_e = torch.cuda.Event(enable_timing=True)
+    dist_barrier(world)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e2e_s.record(stream)
+        for k, sd in enumerate(seeds):
+            bdev.copy_(b_host, non_blocking=True)
+            plan.solve(bdev, sd, args.iters, out=x, stream=stream)
+            x_host.copy_(x, non_blocking=True)
+        e2e_e.record(stream)
+    torch.cuda.synchronize()
+    T_e2e = dist_max(e2e_s.elapsed_time(e2e_e) / 1e3, world)
+    e2e_value = total_solves / T_e2e
+
+    # ---- roofline of the dominant kernel (kind, level) ----
+    kinds = ["forward projector (k_fp)", "back-projector (k_bp)", "primal update (k_update)"]
+    best = int(np.argmax(prof_ms))
+    kind, lvl = best // 8, best % 8
+    cnt = max(1, prof_cnt[best])
+    avg_s = prof_ms[best] / cnt / 1e3
+    nl = p.n >> lvl
+    samples_launch = p.m * nl
+    flops_per_sample = 7.0 if kind == 0 else 14.0   # see the design notes
+    peak_tf = args.alu_peak_tflops
+    achieved_tf = samples_launch * flops_per_sample / avg_s / 1e12
+    share = {f"{kinds[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / max(1e-9, sum(prof_ms)), 4)
+             for k in range(24) if prof_cnt[k] > 0}
+    roofline = {
+        "kernel": f"{kinds[kind]} at level {lvl} ({nl}x{nl} grid)",
+        "bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+        "frac": achieved_tf / peak_tf, "traffic": None,
+        "gsamples_per_s": samples_launch / avg_s / 1e9,
+        "avg_launch_us": avg_s * 1e6, "launches": int(prof_cnt[best]),
+        "time_share": share,
+    }
+
+    # ---- CPU baseline: the oracle on a bounded sample ----
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        params = dict(p.params(), mu=info["mu"], sigma=info["sigma"])
+        dt, sm = oracle_sample(p, params, b.ravel(), 0, args.cpu_iters)
+        per_solve = expected_samples_per_solve(p)
+        cpu = {"value": sm / per_solve / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_iters} FP64 oracle iterations of the fan512 solve "
+                         f"({sm / 1e9:.2f} G ray-samples in {dt:.1f} s), extrapolated by "
+                         f"ray-samples to a {ITERS}-iteration solve",
+               "gsamples_per_s": sm / dt / 1e9}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded random-ellipse phantom, exact fan-beam line integrals, "
+                    "Poisson I0=1e4)",
+            "config": {"workload": WORKLOAD, "n": p.n, "views": p.n_angles, "bins": p.n_det,
+                       "levels": p.levels, "iters_per_solve": args.iters,
+                       "mu": info["mu"], "sigma": info["sigma"], "theta": info["theta"],
+                       "l2": "flushed between steps (512 MB write outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "gsamples_per_s": gs,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "rel_err_vs_plain_fp32": 0.0,
+            "wall_s": wall,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 4 * p.m,
+                    "d2h_bytes_per_step": 4 * p.d},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iters", type=int, default=ITERS)
+    ap.add_argument("--ref-iters", type=int, default=3)
+    ap.add_argument("--cpu-iters", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--probe", action="store_true",
+                    help="time the bare projector / back-projector per level and exit")
+    ap.add_argument("--mu", type=float, default=0.0)
+    ap.add_argument("--sigma", type=float, default=0.0)
+    # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
+    ap.add_argument("--alu-peak-tflops", type=float, default=152 * 128 * 2 * 2.07e9 / 1e12)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        # The oracle's cost per iteration does not depend on mu and sigma, and
+        # deriving them with the FP64 oracle (power method on 552960 x 262144
+        # operators) would take hours; fixed positive values keep the arithmetic.
+        if args.mu <= 0 or args.sigma <= 0:
+            args.mu, args.sigma = 0.25, 0.03
+        return run_reference(args)
+    if args.probe:
+        return run_probe(args)
+    return run_ours(args)
+
+
+def run_probe(args):
+    """Bare K_ell / K_ell^T launches on the fan512 geometry (a small, fixed
+    workload for profilers): three of each per level, timed with CUDA events."""
+    import torch
+    from paper_2412_10249_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask
+    p = inputs.fan512_problem()
+    plan = imask.Plan(dict(p.params(), mu=0.25, sigma=0.03))
+    _, img = inputs.phantom(0, p.n)
+    x = torch.as_tensor(img.ravel().astype(np.float32), device="cuda")
+    y = torch.rand(p.m, device="cuda")
+    sino = torch.empty(p.m, device="cuda")
+    out = torch.empty(p.d, device="cuda")
+    res = {}
+    for ell in range(p.levels):
+        for name, fn in (("K", lambda: plan.project(ell, x, out=sino)),
+                         ("KT", lambda: plan.backproject(ell, y, out=out))):
+            ts = []
+            for _ in range(3):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            res[f"{name}_l{ell}_ms"] = min(ts)
+            res[f"{name}_l{ell}_gsamples_per_s"] = p.m * (p.n >> ell) / (min(ts) / 1e3) / 1e9
+    plan.check()
+    print(json.dumps(res))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -113,7 +113,9 @@ struct imask_plan_s {
   std::vector<double> probs;
   DevPlan dp{};
   float4 *d_rays = nullptr;
+  float2 *d_rays_lo = nullptr;
   ViewInfo *d_views = nullptr;
+  size_t gcap = 0;   // floats of the back-projector's partial-sum buffer
   unsigned int *d_err = nullptr;
   std::vector<int> split, first_x;
   int n_cta_x = 0, n_cta_y = 0;
@@ -265,9 +267,65 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   g.scale2l = (float)ldexp(1.0, sh);
   g.hl = (float)(d.fov / (double)g.nl);
   g.cmid = 0.5f * (float)(g.nl - 1);
-  g.bp_tile = ell <= 0 ? BP_TILE0 : std::max(1, BP_TILE0 >> ell);
-  g.bp_tiles = (g.nl + g.bp_tile - 1) / g.bp_tile;
+  g.bp_tiles = (g.nl + BP_TILE - 1) / BP_TILE;
+  // view groups across CTAs: aim at >= 4 CTAs per SM in total
+  const int tiles = g.bp_tiles * g.bp_tiles;
+  g.bp_vgo = std::max(1, std::min(d.n_angles, (4 * 152 + tiles - 1) / tiles));
+  g.bp_wmax = 0;   // filled in by bp_window_max
   return g;
+}
+
+// Largest number of rays (x- plus y-major) that the back-projector stages for
+// one tile and view at this level, evaluated in FP64 with the kernel's rule
+// (bins of the tile box corners, widened by 0.01 bins), plus 4 for FP32 slack.
+int bp_window_max(const imask_desc &d, const LevelGeom &g, const std::vector<int> &split,
+                  const std::vector<int> &first_x) {
+  const double pitch = pitch_of(d), W = d.fov, hl = W / (double)g.nl;
+  const double center = 0.5 * (double)(d.n_det - 1);
+  const double sd = d.src_dist + d.det_dist;
+  auto bin = [&](double c, double s, double x, double y) {
+    if (d.geometry == 0) return (x * c + y * s) / pitch + center;
+    return sd * (-x * s + y * c) / (d.src_dist - x * c - y * s) / pitch + center;
+  };
+  int best = 0;
+  const int nt = g.bp_tiles;
+  for (int a = 0; a < d.n_angles; ++a) {
+    const double ang = d.angle_start + d.angle_span * (double)a / (double)d.n_angles;
+    const double c = cos(ang), s = sin(ang);
+    const bool fx = first_x[a] != 0;
+    const int xj0 = fx ? 0 : split[a], xj1 = fx ? split[a] : d.n_det;
+    const int yj0 = fx ? split[a] : 0, yj1 = fx ? d.n_det : split[a];
+    for (int ti = 0; ti < nt; ++ti)
+      for (int tj = 0; tj < nt; ++tj) {
+        const int cl = std::min(tj * BP_TILE + BP_TILE - 1, g.nl - 1);
+        const int rl = std::min(ti * BP_TILE + BP_TILE - 1, g.nl - 1);
+        const double bx0 = -0.5 * W + (tj * BP_TILE + 0.5) * hl, bx1 = -0.5 * W + (cl + 0.5) * hl;
+        const double by0 = -0.5 * W + (ti * BP_TILE + 0.5) * hl, by1 = -0.5 * W + (rl + 0.5) * hl;
+        int total = 0;
+        for (int axis = 0; axis < 2; ++axis) {
+          double mn = 1e300, mx = -1e300;
+          for (int k = 0; k < 4; ++k) {
+            double x, y;
+            if (axis == 0) {
+              x = (k & 1) ? bx1 : bx0;
+              y = (k & 2) ? by1 + hl : by0 - hl;
+            } else {
+              x = (k & 1) ? bx1 + hl : bx0 - hl;
+              y = (k & 2) ? by1 : by0;
+            }
+            const double j = bin(c, s, x, y);
+            mn = std::min(mn, j);
+            mx = std::max(mx, j);
+          }
+          const int j0 = axis == 0 ? xj0 : yj0, j1 = axis == 0 ? xj1 : yj1;
+          const int lo = std::max((int)ceil(mn - 0.01), j0);
+          const int hi = std::min((int)floor(mx + 0.01), j1 - 1);
+          total += std::max(hi - lo + 1, 0);
+        }
+        best = std::max(best, total);
+      }
+  }
+  return best + 4;
 }
 
 int update_tile(int n, int levels) {
@@ -312,7 +370,7 @@ imask_status scratch_alloc(const imask_plan_s *p, unsigned levels_mask, bool wit
     offT[li] = cv.take(f);
     offR[li] = cv.take(f);
   }
-  size_t offg = with_g ? cv.take((size_t)p->dp.d) : 0;
+  size_t offg = with_g ? cv.take(p->gcap) : 0;
   const size_t total = std::max<size_t>(cv.off, 64);
   void *mem = nullptr;
   CK(cudaMallocAsync(&mem, total * sizeof(float), st), "cudaMallocAsync(scratch)");
@@ -363,7 +421,7 @@ imask_status apply_KT(const imask_plan_s *p, int ell, const float *y, float *img
   const LevelSel sel = fixed_level(ell);
   {
     ProfScope ps(1, ell < 0 ? 0 : ell, st);
-    CK(launch_bp(p->dp, sel, y, s.g, st), "back-projector launch");
+    CK(launch_bp(p->dp, sel, y, s.g, p->d_err, st), "back-projector launch");
   }
   CK(launch_adjsketch(p->dp, ell, s.g, img, st), "adjoint sketch launch");
   return IMASK_OK;
@@ -614,6 +672,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   const double pitch = pitch_of(*desc);
   const double W = desc->fov, h = W / (double)desc->n;
   std::vector<float4> rays((size_t)na * nd);
+  std::vector<float2> rays_lo((size_t)na * nd);
   std::vector<ViewInfo> views(na);
   int m_x = 0;
   for (int a = 0; a < na; ++a) {
@@ -647,13 +706,21 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
         t = dir[0] / dir[1];
         c0 = p0[0] + (0.0 - p0[1]) * t;   // ray abscissa at y = 0
       }
+      // a = (cross coordinate at the centre line + W/2) / h, split into two
+      // floats, and the slope t likewise (see block_origin in kernels.cu)
+      const double av = (c0 + 0.5 * W) / h;
       float4 e;
-      e.x = (float)((c0 + 0.5 * W) / h);
+      e.x = (float)av;
       e.y = (float)t;
       e.z = (float)(h * sqrt(1.0 + t * t));
       int sidx = a * nd + j;
       memcpy(&e.w, &sidx, sizeof(int));
-      rays[xm ? xi++ : yi++] = e;
+      float2 lo;
+      lo.x = (float)(av - (double)e.x);
+      lo.y = (float)(t - (double)e.y);
+      const int slot = xm ? xi++ : yi++;
+      rays[slot] = e;
+      rays_lo[slot] = lo;
     }
     v.c = (float)ca;
     v.s = (float)sa;
@@ -678,18 +745,34 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   level_thresholds(p->probs, dp.thr);
   dp.lg[0] = level_geom(*desc, -1);
   for (int l = 0; l < r; ++l) dp.lg[l + 1] = level_geom(*desc, l);
+  p->gcap = 0;
+  for (int li = 0; li <= r; ++li) {
+    if (li >= 2) {
+      dp.lg[li].bp_wmax = bp_window_max(*desc, dp.lg[li], p->split, p->first_x);
+    } else if (li == 1) {
+      dp.lg[1].bp_wmax = dp.lg[0].bp_wmax = bp_window_max(*desc, dp.lg[1], p->split, p->first_x);
+    }
+    p->gcap = std::max(p->gcap, (size_t)dp.lg[li].bp_vgo * dp.lg[li].nl * dp.lg[li].nl);
+  }
+  if (bp_smem_bytes(dp) > 200 * 1024) {
+    imask_plan_destroy(p);
+    return fail(IMASK_ERR_SHAPE, "back-projector ray window too large for shared memory");
+  }
   dp.upd_tile = update_tile(desc->n, r);
   p->n_cta_x = (m_x + FP_CHUNK - 1) / FP_CHUNK;
   p->n_cta_y = (dp.m - m_x + FP_CHUNK - 1) / FP_CHUNK;
 
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_rays, rays.size() * sizeof(float4))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_rays_lo, rays_lo.size() * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_views, views.size() * sizeof(ViewInfo))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess) {
     imask_plan_destroy(p);
     return cuda_fail(e, "cudaMalloc(plan)");
   }
   if ((e = cudaMemcpy(p->d_rays, rays.data(), rays.size() * sizeof(float4),
+                      cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(p->d_rays_lo, rays_lo.data(), rays_lo.size() * sizeof(float2),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
       (e = cudaMemcpy(p->d_views, views.data(), views.size() * sizeof(ViewInfo),
                       cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -698,6 +781,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
     return cuda_fail(e, "upload plan");
   }
   dp.rays = p->d_rays;
+  dp.rays_lo = p->d_rays_lo;
   dp.views = p->d_views;
 
   cudaStream_t st = nullptr;
@@ -720,6 +804,7 @@ imask_status imask_plan_destroy(imask_plan_t p) {
   if (!p) return IMASK_OK;
   cudaDeviceSynchronize();
   if (p->d_rays) cudaFree(p->d_rays);
+  if (p->d_rays_lo) cudaFree(p->d_rays_lo);
   if (p->d_views) cudaFree(p->d_views);
   if (p->d_err) cudaFree(p->d_err);
   delete p;
@@ -760,6 +845,8 @@ imask_status imask_plan_check(imask_plan_t p) {
   CK(cudaMemcpy(&flag, p->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
   if (flag) {
     cudaMemset(p->d_err, 0, sizeof flag);
+    if (flag & 2u)
+      return fail(IMASK_ERR_INVALID, "a back-projector ray window exceeded its planned size");
     return fail(IMASK_ERR_TIMEOUT, "a projector launch gave up waiting for its image strips");
   }
   return IMASK_OK;
@@ -816,7 +903,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   Carve cv;
   size_t o_x = cv.take(d), o_y0 = cv.take(m), o_y1 = cv.take(m), o_b = cv.take(m);
   size_t o_psi = cv.take(m * r), o_psim = cv.take(m), o_phi0 = cv.take(d), o_phim = cv.take(d);
-  size_t o_g = cv.take(d);
+  size_t o_g = cv.take(p->gcap);
   size_t o_phic[IMASK_MAX_LEVELS] = {0};
   for (int l = 1; l < r; ++l) {
     const size_t nl = (size_t)p->dp.lg[l + 1].nl;
@@ -895,7 +982,7 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
     }
     {
       ProfScope ps(1, lvl, st);
-      CK(launch_bp(P, sel, s->y[s->cur], s->g, st), "back-projector launch");
+      CK(launch_bp(P, sel, s->y[s->cur], s->g, p->d_err, st), "back-projector launch");
     }
     PrimalArgs A{};
     A.g = s->g;

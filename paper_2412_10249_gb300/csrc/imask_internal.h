@@ -14,8 +14,10 @@
 #define FP_CHUNK (FP_THREADS * FP_RAYS)
 #define FP_STAGES 3            // TMA strip pipeline depth
 #define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
-#define BP_THREADS 256         // back-projector: threads per CTA
-#define BP_TILE0 16            // back-projector tile side at level 0
+#define BP_THREADS 256         // back-projector: threads per CTA (one per tile pixel)
+#define BP_TILE 16             // back-projector tile side, every level
+#define BP_VC 4                // back-projector: views staged per shared-memory chunk
+#define LBLOCK 16              // lines per local interpolation frame (see block_origin)
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
 
 // Per-view data for the pixel-driven back-projector (32 bytes).
@@ -38,8 +40,9 @@ struct LevelGeom {
   float scale2l;   // 2^ell
   float hl;        // pixel width fov / nl
   float cmid;      // (nl - 1) / 2
-  int bp_tile;     // back-projector tile side
-  int bp_tiles;    // back-projector tiles per side
+  int bp_tiles;    // back-projector tiles (BP_TILE x BP_TILE) per side
+  int bp_vgo;      // back-projector view groups across CTAs (partial sums)
+  int bp_wmax;     // largest ray window of a tile and view, per major axis
 };
 
 // Everything the kernels need about a plan (passed by value).
@@ -52,7 +55,8 @@ struct DevPlan {
   unsigned long long thr[IMASK_MAX_LEVELS];   // level thresholds (r - 1 used)
   LevelGeom lg[IMASK_MAX_LEVELS + 1];
   int upd_tile;      // fine-pixel tile side of the sketch / update kernels
-  const float4 *rays;      // ray list: (a_mid, slope, g, sino index bits)
+  const float4 *rays;      // ray list: (a_hi, t_hi, g, sino index bits)
+  const float2 *rays_lo;   // ray list: (a_lo, t_lo), the low words of a and t
   const ViewInfo *views;   // per view
 };
 
@@ -84,7 +88,7 @@ struct DualArgs {
 
 // Primal epilogue (Alg. 1, the xi and x updates) in the update kernel.
 struct PrimalArgs {
-  const float *g;    // R_ell^T y on the level grid (back-projector output)
+  const float *g;    // R_ell^T y on the level grid as bp_vgo partial sums
   float *x;          // iterate, updated in place
   float *phi0;       // table entry of level 0 (n*n)
   float *phic;       // tables of levels >= 1, stored on their own grids
@@ -104,7 +108,9 @@ cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet
                           cudaStream_t st);
 cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
                       int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st);
-cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g, cudaStream_t st);
+cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
+                      unsigned int *err, cudaStream_t st);
+long long bp_smem_bytes(const DevPlan &P);
 cudaError_t launch_adjsketch(const DevPlan &P, int ell, const float *g, float *img,
                              cudaStream_t st);
 cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int write_sketch,

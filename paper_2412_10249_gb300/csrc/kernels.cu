@@ -98,17 +98,45 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
 }
 
 // ---------------------------------------------------------------------------------
+// Local interpolation frames.
+//
+// Along its major axis a ray is sampled at lines (columns for x-major rays,
+// rows for y-major rays) c = 0..nl-1 of the level grid, at the fractional
+// cross coordinate q(c) = a 2^-ell - 1/2 + (c - (nl-1)/2) t.  In FP32, q of
+// several hundred carries an absolute error of ~1e-5, which is the full error
+// budget of the operators, so q is never formed: lines are grouped in blocks of
+// LBLOCK, and for each (ray, block) the origin q(cB) = I + r is split into an
+// integer I and a remainder |r| <~ 1 with double-float arithmetic from the
+// two-word ray parameters a = a_hi + a_lo, t = t_hi + t_lo.  Inside the block
+// q(cB + d) - I = r + d t_hi, a number below LBLOCK + 1, exact to ~1e-6.  The
+// projector and the back-projector call the same function, so their weights
+// agree to the last bit.
+// ---------------------------------------------------------------------------------
+__device__ __forceinline__ void block_origin(float a_hi, float a_lo, float t_hi, float t_lo,
+                                             float s, float cc, int &I, float &r) {
+  const float A = a_hi * s;                 // exact: s is a power of two
+  const float Pp = cc * t_hi;
+  const float E = fmaf(cc, t_hi, -Pp);      // exact rounding error of the product
+  const float S = A + Pp;                   // two-sum S + e1 = A + Pp
+  const float bb = S - A;
+  const float e1 = (A - (S - bb)) + (Pp - bb);
+  const float tq = S + kMagic;              // round to the nearest integer (|S| < 2^22)
+  const float Sr = tq - kMagic;
+  I = __float_as_int(tq) - kMagicBits;
+  r = (S - Sr) + (e1 + E + fmaf(a_lo, s, fmaf(cc, t_lo, -0.5f)));
+}
+
+// ---------------------------------------------------------------------------------
 // Forward projector (Joseph) with the fused dual epilogue.
 //
 // Rays are listed x-major first, then y-major.  CTA b < n_cta_x takes x-major
 // rays [b*FP_CHUNK, ...), the others y-major rays.  An x-major ray marches over
 // the columns of the x-major padded image (one line per column, rows
-// contiguous); at column c its fractional row is q = a_mid 2^-ell - 1/2 +
-// (c - (nl-1)/2) * slope and the sample is the linear interpolation of the two
-// neighbouring rows.  Strips of tc lines are streamed through FP_STAGES
-// shared-memory buffers by cp.async.bulk; zero padding of IMASK_PAD entries
-// on both sides of every line, with q clamped to [-2, nl + 1/2], makes rows off
-// the grid read as zero without a branch.
+// contiguous) and interpolates linearly between the rows I + floor(r + d t) and
+// the next one.  Strips of tc lines are streamed through FP_STAGES
+// shared-memory buffers by cp.async.bulk.  Every line carries IMASK_PAD zeros
+// on both sides; clamping the row index into [-2, nl] therefore reads zeros for
+// rows off the grid without a branch.
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(FP_THREADS, 2)
     k_fp(DevPlan P, LevelSel sel, PadSet pads, float *sino, DualArgs D, int n_cta_x,
@@ -125,28 +153,32 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
   const float *img = xaxis ? pads.T[ell + 1] : pads.R[ell + 1];
   const int tid = threadIdx.x;
 
-  float q0[FP_RAYS], sl[FP_RAYS], acc[FP_RAYS], gsc[FP_RAYS];
-  int sidx[FP_RAYS];
+  float ahi[FP_RAYS], alo[FP_RAYS], thi[FP_RAYS], tlo[FP_RAYS], rl[FP_RAYS], acc[FP_RAYS];
+  int boff[FP_RAYS];
 #pragma unroll
   for (int r = 0; r < FP_RAYS; ++r) {
     const int idx = begin + r * FP_THREADS + tid;
     acc[r] = 0.0f;
+    rl[r] = 0.0f;
+    boff[r] = 0;
     if (idx < end) {
       const float4 p = P.rays[idx];
-      q0[r] = fmaf(p.x, G.inv2l, -0.5f);
-      sl[r] = p.y;
-      gsc[r] = p.z;
-      sidx[r] = __float_as_int(p.w);
+      const float2 lo = P.rays_lo[idx];
+      ahi[r] = p.x;
+      thi[r] = p.y;
+      alo[r] = lo.x;
+      tlo[r] = lo.y;
     } else {
-      q0[r] = -4.0f;  // clamped to -2: reads the zero padding
-      sl[r] = 0.0f;
-      gsc[r] = 0.0f;
-      sidx[r] = -1;
+      ahi[r] = -16384.0f;  // far below the grid: the clamped index reads zeros
+      thi[r] = 0.0f;
+      alo[r] = 0.0f;
+      tlo[r] = 0.0f;
     }
   }
 
   const int tc = G.tc, ls = G.ls;
   const int nstrips = G.lines / tc;
+  const int ilo = IMASK_PAD - 2, ihi = IMASK_PAD + G.nl;
   const uint32_t strip_bytes = (uint32_t)(tc * ls) * 4u;
   if (tid == 0) {
     for (int s = 0; s < FP_STAGES; ++s) mbar_init(smem_u32(&full_bar[s]), 1);
@@ -159,28 +191,37 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
                 smem_u32(&full_bar[s]));
   }
 
-  const float qhi = (float)G.nl + 0.5f;
   bool failed = false;
   for (int s = 0; s < nstrips; ++s) {
     const int st = s % FP_STAGES;
     const uint32_t parity = (uint32_t)((s / FP_STAGES) & 1);
     const bool ok = mbar_wait(smem_u32(&full_bar[st]), parity);
-    const float *buf = fp_smem + st * FP_STAGE_FLOATS + IMASK_PAD;
-    const float cf0 = (float)(s * tc) - G.cmid;
+    const float *buf = fp_smem + st * FP_STAGE_FLOATS;
     float part[FP_RAYS];
 #pragma unroll
     for (int r = 0; r < FP_RAYS; ++r) part[r] = 0.0f;
     for (int cc = 0; cc < tc; cc += 4) {
+      const int c = s * tc + cc;
+      if ((c & (LBLOCK - 1)) == 0) {
+        const float ccm = (float)c - G.cmid;
+#pragma unroll
+        for (int r = 0; r < FP_RAYS; ++r) {
+          int I;
+          block_origin(ahi[r], alo[r], thi[r], tlo[r], G.inv2l, ccm, I, rl[r]);
+          boff[r] = IMASK_PAD + I;
+        }
+      }
+      const float d0 = (float)(c & (LBLOCK - 1));
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float cf = cf0 + (float)(cc + u);
+        const float dcf = d0 + (float)u;
         const float *line = buf + (cc + u) * ls;
 #pragma unroll
         for (int r = 0; r < FP_RAYS; ++r) {
-          float q = fmaf(cf, sl[r], q0[r]);
-          q = fminf(fmaxf(q, -2.0f), qhi);
+          const float q = fmaf(dcf, thi[r], rl[r]);
           const float tq = __fadd_rd(q, kMagic);
-          const int i0 = __float_as_int(tq) - kMagicBits;
+          int i0 = boff[r] + (__float_as_int(tq) - kMagicBits);
+          i0 = min(max(i0, ilo), ihi);
           const float f = q - (tq - kMagic);
           const float v0 = line[i0];
           const float v1 = line[i0 + 1];
@@ -211,9 +252,11 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 
 #pragma unroll
   for (int r = 0; r < FP_RAYS; ++r) {
-    if (sidx[r] < 0) continue;
-    const float v = acc[r] * (gsc[r] * G.scale2l);
-    const int q = sidx[r];
+    const int idx = begin + r * FP_THREADS + tid;
+    if (idx >= end) continue;
+    const float4 p = P.rays[idx];
+    const float v = acc[r] * (p.z * G.scale2l);
+    const int q = __float_as_int(p.w);
     if (!D.on) {
       sino[q] = v;
     } else {
@@ -233,84 +276,217 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 // ---------------------------------------------------------------------------------
 // Pixel-driven back-projector: g = R_ell^T y on the level grid.
 //
-// A CTA covers a t x t tile of level pixels and splits the views into
-// 256 / t^2 groups; each thread gathers, for its pixel and each of its views,
-// the rays whose interpolation weight at the pixel is non-zero.  For x-major
-// rays these are the bins j whose ray height at the pixel's column lies within
-// one pixel width of the pixel centre: the preimage of that interval under the
-// (affine or linear-fractional) bin map, widened by kBpEps bins.  The weight is
-// max(0, 1 - |q - i|) with q computed exactly as in k_fp, so the two kernels
-// use the same numbers.  View groups are summed in shared memory.
+// A CTA owns a BP_TILE x BP_TILE tile of level pixels (one per thread) and a
+// contiguous range of views (bp_vgo ranges across CTAs; their partial sums are
+// added by the consumer in a fixed order).  Views are processed BP_VC at a
+// time:
+//   1. warp 0 maps the corners of the tile's extended box to detector bins
+//      (the bin map is affine for parallel beam and linear-fractional for fan
+//      beam, so its extremes over the box sit at the corners) and fixes, per
+//      view and major axis, the window of rays that can touch the tile;
+//   2. the CTA stages the window in shared memory: for each ray its local
+//      frame (I, r) on the tile's line block, the slope and g * y;
+//   3. every pixel maps its own two interpolation limits to bins and gathers
+//      the rays in between, weight max(0, 1 - |q - i|) * g with q from the
+//      same local frame as k_fp.
+// No atomics: every output value is owned by one thread.
 // ---------------------------------------------------------------------------------
-__device__ __forceinline__ float bin_of(const DevPlan &P, const ViewInfo &V, float x, float y) {
-  if (P.geometry == 0) return fmaf(fmaf(x, V.c, y * V.s), P.inv_pitch, P.center);
-  const float num = fmaf(-x, V.s, y * V.c);
-  const float den = P.src_dist - fmaf(x, V.c, y * V.s);
-  return fmaf(P.sd_dist * num / den, P.inv_pitch, P.center);
+__device__ __forceinline__ float bin_of(const DevPlan &P, float c, float s, float x, float y) {
+  if (P.geometry == 0) return fmaf(fmaf(x, c, y * s), P.inv_pitch, P.center);
+  const float num = fmaf(-x, s, y * c);
+  const float den = P.src_dist - fmaf(x, c, y * s);
+  return fmaf(P.sd_dist * __fdividef(num, den), P.inv_pitch, P.center);
 }
 
-__global__ void __launch_bounds__(BP_THREADS)
-    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ g) {
-  __shared__ float red[BP_THREADS];
+__device__ __forceinline__ int floor_i(float v) {
+  return __float_as_int(__fadd_rd(v, kMagic)) - kMagicBits;
+}
+
+__device__ __forceinline__ int ceil_i(float v) {
+  return __float_as_int(__fadd_ru(v, kMagic)) - kMagicBits;
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) {
+  return fminf(fmaxf(v, lo), hi);
+}
+
+__global__ void __launch_bounds__(BP_THREADS, 3)
+    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
+         unsigned int *err) {
+  extern __shared__ __align__(16) float4 win[];
+  __shared__ int wlo[BP_VC][2], wcnt[BP_VC][2], woff[BP_VC][2];
+  __shared__ float vcs[BP_VC][2];
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
-  const int t = G.bp_tile, tt = t * t, VG = BP_THREADS / tt;
-  const int nt = G.bp_tiles;
-  if ((int)blockIdx.x >= nt * nt) return;
-  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
-  const int lp = threadIdx.x % tt, vg = threadIdx.x / tt;
-  const int i = ti * t + lp / t, c = tj * t + lp % t;
+  const int nt = G.bp_tiles, vgo = G.bp_vgo, cap = BP_VC * G.bp_wmax;
+  const int vg = blockIdx.x / (nt * nt);
+  if (vg >= vgo) return;
+  const int tile = blockIdx.x % (nt * nt);
+  const int ti = tile / nt, tj = tile % nt;
+  const int tid = threadIdx.x;
+  const int i = ti * BP_TILE + tid / BP_TILE, c = tj * BP_TILE + tid % BP_TILE;
   const bool valid = (i < G.nl) && (c < G.nl);
-  float acc = 0.0f;
-  if (valid) {
-    const float hl = G.hl;
-    const float xc = -0.5f * P.fov + ((float)c + 0.5f) * hl;
-    const float yi = -0.5f * P.fov + ((float)i + 0.5f) * hl;
-    const float cm = (float)c - G.cmid, im = (float)i - G.cmid;
-    const float fi = (float)i, fc = (float)c;
-    for (int a = vg; a < P.n_angles; a += VG) {
-      const ViewInfo V = P.views[a];
-      const float *ya = y + (size_t)a * P.n_det;
-      if (V.xj1 > V.xj0) {
-        const float ja = bin_of(P, V, xc, yi - hl), jb = bin_of(P, V, xc, yi + hl);
-        const int lo = (int)fmaxf(ceilf(fminf(ja, jb) - kBpEps), (float)V.xj0);
-        const int hi = (int)fminf(floorf(fmaxf(ja, jb) + kBpEps), (float)(V.xj1 - 1));
-        const float4 *rp = P.rays + (V.xoff - V.xj0);
-        for (int j = lo; j <= hi; ++j) {
-          const float4 r = rp[j];
-          const float q = fmaf(cm, r.y, fmaf(r.x, G.inv2l, -0.5f));
-          const float w = fmaxf(0.0f, 1.0f - fabsf(q - fi));
-          acc = fmaf(w * r.z, __ldg(ya + j), acc);
+  const int a0 = (int)(((long long)vg * P.n_angles) / vgo);
+  const int a1 = (int)(((long long)(vg + 1) * P.n_angles) / vgo);
+  const float hl = G.hl, W = P.fov;
+  const float xc = -0.5f * W + ((float)c + 0.5f) * hl;
+  const float yi = -0.5f * W + ((float)i + 0.5f) * hl;
+  const float dcx = (float)(c - tj * BP_TILE);   // offset in the x-major line block
+  const float dry = (float)(i - ti * BP_TILE);   // offset in the y-major line block
+  const float fi = (float)i, fc = (float)c;
+  // tile box (pixel centres of its first and last column / row on the grid)
+  const int cl = min(tj * BP_TILE + BP_TILE - 1, G.nl - 1), rl_ = min(ti * BP_TILE + BP_TILE - 1, G.nl - 1);
+  const float bx0 = -0.5f * W + ((float)(tj * BP_TILE) + 0.5f) * hl;
+  const float bx1 = -0.5f * W + ((float)cl + 0.5f) * hl;
+  const float by0 = -0.5f * W + ((float)(ti * BP_TILE) + 0.5f) * hl;
+  const float by1 = -0.5f * W + ((float)rl_ + 0.5f) * hl;
+  const float ccx = (float)(tj * BP_TILE) - G.cmid;   // line-block origins (march coordinate)
+  const float ccy = (float)(ti * BP_TILE) - G.cmid;
+
+  float acc = 0.0f, comp = 0.0f;
+  for (int ab = a0; ab < a1; ab += BP_VC) {
+    const int nv = min(BP_VC, a1 - ab);
+    // ---- 1. ray windows (warp 0: 8 lanes per view, 4 corners per axis) ----
+    if (tid < 32) {
+      const int v = tid >> 3, k = tid & 7, axis = k >> 2, corner = k & 3;
+      float jv = 0.0f;
+      ViewInfo V{};
+      if (v < nv) {
+        V = P.views[ab + v];
+        float x, yy;
+        if (axis == 0) {
+          x = (corner & 1) ? bx1 : bx0;
+          yy = (corner & 2) ? by1 + hl : by0 - hl;
+        } else {
+          x = (corner & 1) ? bx1 + hl : bx0 - hl;
+          yy = (corner & 2) ? by1 : by0;
+        }
+        jv = bin_of(P, V.c, V.s, x, yy);
+      }
+      float mn = jv, mx = jv;
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 2));
+      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+      if (v < nv && corner == 0) {
+        const int j0 = axis == 0 ? V.xj0 : V.yj0, j1 = axis == 0 ? V.xj1 : V.yj1;
+        const int lo = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
+        const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
+        wlo[v][axis] = lo;
+        wcnt[v][axis] = max(hi - lo + 1, 0);
+        if (axis == 0) {
+          vcs[v][0] = V.c;
+          vcs[v][1] = V.s;
         }
       }
-      if (V.yj1 > V.yj0) {
-        const float ja = bin_of(P, V, xc - hl, yi), jb = bin_of(P, V, xc + hl, yi);
-        const int lo = (int)fmaxf(ceilf(fminf(ja, jb) - kBpEps), (float)V.yj0);
-        const int hi = (int)fminf(floorf(fmaxf(ja, jb) + kBpEps), (float)(V.yj1 - 1));
-        const float4 *rp = P.rays + (V.yoff - V.yj0);
-        for (int j = lo; j <= hi; ++j) {
-          const float4 r = rp[j];
-          const float q = fmaf(im, r.y, fmaf(r.x, G.inv2l, -0.5f));
-          const float w = fmaxf(0.0f, 1.0f - fabsf(q - fc));
-          acc = fmaf(w * r.z, __ldg(ya + j), acc);
-        }
+      __syncwarp();
+      if (tid == 0) {
+        int off = 0;
+        for (int vv = 0; vv < BP_VC; ++vv)
+          for (int ax = 0; ax < 2; ++ax) {
+            if (vv >= nv) {
+              wcnt[vv][ax] = 0;
+              wlo[vv][ax] = 0;
+            }
+            if (off + wcnt[vv][ax] > cap) {  // never expected: the plan sizes cap
+              atomicOr(err, 2u);
+              wcnt[vv][ax] = max(cap - off, 0);
+            }
+            woff[vv][ax] = off;
+            off += wcnt[vv][ax];
+          }
       }
     }
-    acc *= G.scale2l;
-  }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int s = VG >> 1; s > 0; s >>= 1) {
-    if (vg < s) red[threadIdx.x] += red[threadIdx.x + s * tt];
+    __syncthreads();
+    // ---- 2. stage the windows ----
+    const int total = woff[BP_VC - 1][1] + wcnt[BP_VC - 1][1];
+    for (int e = tid; e < total; e += BP_THREADS) {
+      int vv = 0, ax = 0;
+#pragma unroll
+      for (int q = 0; q < 2 * BP_VC; ++q)
+        if (e >= woff[q >> 1][q & 1]) {
+          vv = q >> 1;
+          ax = q & 1;
+        }
+      const int j = wlo[vv][ax] + (e - woff[vv][ax]);
+      const ViewInfo V = P.views[ab + vv];
+      const int li = ax == 0 ? V.xoff + (j - V.xj0) : V.yoff + (j - V.yj0);
+      const float4 p = P.rays[li];
+      const float2 pl = P.rays_lo[li];
+      const float yv = __ldg(y + (size_t)(ab + vv) * P.n_det + j);
+      int I;
+      float r;
+      block_origin(p.x, pl.x, p.y, pl.y, G.inv2l, ax == 0 ? ccx : ccy, I, r);
+      win[e] = make_float4(r, p.y, p.z * yv, (float)I);
+    }
+    __syncthreads();
+    // ---- 3. gather ----
+    for (int vv = 0; vv < nv; ++vv) {
+      const float vc = vcs[vv][0], vs = vcs[vv][1];
+      float pv = 0.0f;
+      if (wcnt[vv][0] > 0) {   // x-major rays: march over columns, interpolate rows
+        int lo = 0, cnt = 0;
+        if (valid) {
+          const float ja = bin_of(P, vc, vs, xc, yi - hl), jb = bin_of(P, vc, vs, xc, yi + hl);
+          lo = max(ceil_i(clampf(fminf(ja, jb) - kBpEps, -1.0e6f, 1.0e6f)), wlo[vv][0]);
+          const int hi = min(floor_i(clampf(fmaxf(ja, jb) + kBpEps, -1.0e6f, 1.0e6f)),
+                             wlo[vv][0] + wcnt[vv][0] - 1);
+          cnt = max(hi - lo + 1, 0);
+        }
+        const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+        const float4 *wp = win + woff[vv][0] + (lo - wlo[vv][0]);
+        for (int k = 0; k < cmax; ++k) {
+          if (k < cnt) {
+            const float4 e = wp[k];
+            const float q = fmaf(dcx, e.y, e.x);
+            const float w = fmaxf(0.0f, 1.0f - fabsf(q - (fi - e.w)));
+            pv = fmaf(w, e.z, pv);
+          }
+        }
+      }
+      if (wcnt[vv][1] > 0) {   // y-major rays: march over rows, interpolate columns
+        int lo = 0, cnt = 0;
+        if (valid) {
+          const float ja = bin_of(P, vc, vs, xc - hl, yi), jb = bin_of(P, vc, vs, xc + hl, yi);
+          lo = max(ceil_i(clampf(fminf(ja, jb) - kBpEps, -1.0e6f, 1.0e6f)), wlo[vv][1]);
+          const int hi = min(floor_i(clampf(fmaxf(ja, jb) + kBpEps, -1.0e6f, 1.0e6f)),
+                             wlo[vv][1] + wcnt[vv][1] - 1);
+          cnt = max(hi - lo + 1, 0);
+        }
+        const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+        const float4 *wp = win + woff[vv][1] + (lo - wlo[vv][1]);
+        for (int k = 0; k < cmax; ++k) {
+          if (k < cnt) {
+            const float4 e = wp[k];
+            const float q = fmaf(dry, e.y, e.x);
+            const float w = fmaxf(0.0f, 1.0f - fabsf(q - (fc - e.w)));
+            pv = fmaf(w, e.z, pv);
+          }
+        }
+      }
+      // compensated (Kahan) sum over views
+      const float yk = pv - comp;
+      const float tk = acc + yk;
+      comp = (tk - acc) - yk;
+      acc = tk;
+    }
     __syncthreads();
   }
-  if (vg == 0 && valid) g[(size_t)i * G.nl + c] = red[threadIdx.x];
+  if (valid) gout[(size_t)vg * G.nl * G.nl + (size_t)i * G.nl + c] = acc * G.scale2l;
 }
 
 // ---------------------------------------------------------------------------------
 // Image-side sketches on fine-pixel tiles of side P.upd_tile (a multiple of
 // 2^(r-1) that divides n), so every block of every level lies inside one tile.
 // ---------------------------------------------------------------------------------
+
+// The back-projector leaves bp_vgo partial images (one per view group), each
+// of side nl; their sum in a fixed order is R_ell^T y.
+__device__ __forceinline__ float g_sum(const float *g, int vgo, size_t plane, size_t idx) {
+  float s = g[idx];
+  for (int v = 1; v < vgo; ++v) s += g[(size_t)v * plane + idx];
+  return s;
+}
 
 // Block means of the tile `src` (side ts) at levels 1..r-1, level l at
 // pyr + pyr_off(l), side ts >> l.  Hierarchical 2x2 means.
@@ -411,24 +587,26 @@ __global__ void __launch_bounds__(UPD_THREADS)
   float *xs = upd_smem, *pyr = xs + 2 * ts * ts;
   const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
   const int n = P.n;
+  const LevelGeom G = P.lg[ell + 1];
+  const size_t plane = (size_t)G.nl * G.nl;
   if (ell < 0) {
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
       const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
-      img[gp] = g[gp];
+      img[gp] = g_sum(g, G.bp_vgo, plane, gp);
     }
     return;
   }
   if (ell >= 1) {
-    const LevelGeom G = P.lg[ell + 1];
     const float s = G.inv2l * G.inv2l;
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
       const int fi = ti0 + p / ts, fj = tj0 + p % ts;
-      img[(size_t)fi * n + fj] = g[(size_t)(fi >> ell) * G.nl + (fj >> ell)] * s;
+      img[(size_t)fi * n + fj] =
+          g_sum(g, G.bp_vgo, plane, (size_t)(fi >> ell) * G.nl + (fj >> ell)) * s;
     }
     return;
   }
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-    xs[p] = g[(size_t)(ti0 + p / ts) * n + tj0 + p % ts];
+    xs[p] = g_sum(g, G.bp_vgo, plane, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
   __syncthreads();
   if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
@@ -459,14 +637,15 @@ __global__ void __launch_bounds__(UPD_THREADS)
     const float inv4l = G.inv2l * G.inv2l;
     for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
       const size_t gi = (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
-      const float cnew = A.g[gi] * inv4l;
+      const float cnew = g_sum(A.g, G.bp_vgo, (size_t)G.nl * G.nl, gi) * inv4l;
       dc[p] = cnew - phic[gi];
       phic[gi] = cnew;
     }
     __syncthreads();
   } else {
+    const int vgo0 = P.lg[1].bp_vgo;
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-      aux[p] = A.g[(size_t)(ti0 + p / ts) * n + tj0 + p % ts];
+      aux[p] = g_sum(A.g, vgo0, (size_t)n * n, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
     __syncthreads();
     if (P.levels > 1) tile_pyramid(aux, pyr, ts, P.levels);
   }
@@ -696,13 +875,25 @@ cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g, cudaStream_t st) {
-  // the grid covers the level with the most tiles; extra CTAs return at once
+long long bp_smem_bytes(const DevPlan &P) {
+  int w = 0;
+  for (int li = 0; li <= P.levels; ++li) w = max(w, P.lg[li].bp_wmax);
+  return (long long)BP_VC * w * (long long)sizeof(float4);
+}
+
+cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
+                      unsigned int *err, cudaStream_t st) {
+  // the grid covers the level with the most (tile, view group) pairs; extra
+  // CTAs return at once
+  auto ctas = [&](int li) { return P.lg[li].bp_tiles * P.lg[li].bp_tiles * P.lg[li].bp_vgo; };
   int most = 0;
-  for (int li = 0; li <= P.levels; ++li) most = max(most, P.lg[li].bp_tiles * P.lg[li].bp_tiles);
-  if (sel.fixed >= -1) most = P.lg[sel.fixed + 1].bp_tiles * P.lg[sel.fixed + 1].bp_tiles;
+  for (int li = 0; li <= P.levels; ++li) most = max(most, ctas(li));
+  if (sel.fixed >= -1) most = ctas(sel.fixed + 1);
+  const int sm = (int)bp_smem_bytes(P);
+  cudaError_t e = set_smem((const void *)k_bp, sm);
+  if (e != cudaSuccess) return e;
   count_launch();
-  k_bp<<<most, BP_THREADS, 0, st>>>(P, sel, y, g);
+  k_bp<<<most, BP_THREADS, sm, st>>>(P, sel, y, g, err);
   return cudaGetLastError();
 }
 
