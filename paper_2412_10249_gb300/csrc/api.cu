@@ -271,61 +271,7 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   // view groups across CTAs: aim at >= 4 CTAs per SM in total
   const int tiles = g.bp_tiles * g.bp_tiles;
   g.bp_vgo = std::max(1, std::min(d.n_angles, (4 * 152 + tiles - 1) / tiles));
-  g.bp_wmax = 0;   // filled in by bp_window_max
   return g;
-}
-
-// Largest number of rays (x- plus y-major) that the back-projector stages for
-// one tile and view at this level, evaluated in FP64 with the kernel's rule
-// (bins of the tile box corners, widened by 0.01 bins), plus 4 for FP32 slack.
-int bp_window_max(const imask_desc &d, const LevelGeom &g, const std::vector<int> &split,
-                  const std::vector<int> &first_x) {
-  const double pitch = pitch_of(d), W = d.fov, hl = W / (double)g.nl;
-  const double center = 0.5 * (double)(d.n_det - 1);
-  const double sd = d.src_dist + d.det_dist;
-  auto bin = [&](double c, double s, double x, double y) {
-    if (d.geometry == 0) return (x * c + y * s) / pitch + center;
-    return sd * (-x * s + y * c) / (d.src_dist - x * c - y * s) / pitch + center;
-  };
-  int best = 0;
-  const int nt = g.bp_tiles;
-  for (int a = 0; a < d.n_angles; ++a) {
-    const double ang = d.angle_start + d.angle_span * (double)a / (double)d.n_angles;
-    const double c = cos(ang), s = sin(ang);
-    const bool fx = first_x[a] != 0;
-    const int xj0 = fx ? 0 : split[a], xj1 = fx ? split[a] : d.n_det;
-    const int yj0 = fx ? split[a] : 0, yj1 = fx ? d.n_det : split[a];
-    for (int ti = 0; ti < nt; ++ti)
-      for (int tj = 0; tj < nt; ++tj) {
-        const int cl = std::min(tj * BP_TILE + BP_TILE - 1, g.nl - 1);
-        const int rl = std::min(ti * BP_TILE + BP_TILE - 1, g.nl - 1);
-        const double bx0 = -0.5 * W + (tj * BP_TILE + 0.5) * hl, bx1 = -0.5 * W + (cl + 0.5) * hl;
-        const double by0 = -0.5 * W + (ti * BP_TILE + 0.5) * hl, by1 = -0.5 * W + (rl + 0.5) * hl;
-        int total = 0;
-        for (int axis = 0; axis < 2; ++axis) {
-          double mn = 1e300, mx = -1e300;
-          for (int k = 0; k < 4; ++k) {
-            double x, y;
-            if (axis == 0) {
-              x = (k & 1) ? bx1 : bx0;
-              y = (k & 2) ? by1 + hl : by0 - hl;
-            } else {
-              x = (k & 1) ? bx1 + hl : bx0 - hl;
-              y = (k & 2) ? by1 : by0;
-            }
-            const double j = bin(c, s, x, y);
-            mn = std::min(mn, j);
-            mx = std::max(mx, j);
-          }
-          const int j0 = axis == 0 ? xj0 : yj0, j1 = axis == 0 ? xj1 : yj1;
-          const int lo = std::max((int)ceil(mn - 0.01), j0);
-          const int hi = std::min((int)floor(mx + 0.01), j1 - 1);
-          total += std::max(hi - lo + 1, 0);
-        }
-        best = std::max(best, total);
-      }
-  }
-  return best + 4;
 }
 
 int update_tile(int n, int levels) {
@@ -747,16 +693,13 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   for (int l = 0; l < r; ++l) dp.lg[l + 1] = level_geom(*desc, l);
   p->gcap = 0;
   for (int li = 0; li <= r; ++li) {
-    if (li >= 2) {
-      dp.lg[li].bp_wmax = bp_window_max(*desc, dp.lg[li], p->split, p->first_x);
-    } else if (li == 1) {
-      dp.lg[1].bp_wmax = dp.lg[0].bp_wmax = bp_window_max(*desc, dp.lg[1], p->split, p->first_x);
-    }
-    p->gcap = std::max(p->gcap, (size_t)dp.lg[li].bp_vgo * dp.lg[li].nl * dp.lg[li].nl);
+    LevelGeom &g = dp.lg[li];
+    g.bp_nv = (desc->n_angles + g.bp_vgo - 1) / g.bp_vgo;
+    p->gcap = std::max(p->gcap, (size_t)g.bp_vgo * g.nl * g.nl);
   }
   if (bp_smem_bytes(dp) > 200 * 1024) {
     imask_plan_destroy(p);
-    return fail(IMASK_ERR_SHAPE, "back-projector ray window too large for shared memory");
+    return fail(IMASK_ERR_SHAPE, "too many views per back-projector CTA for shared memory");
   }
   dp.upd_tile = update_tile(desc->n, r);
   p->n_cta_x = (m_x + FP_CHUNK - 1) / FP_CHUNK;
@@ -845,8 +788,6 @@ imask_status imask_plan_check(imask_plan_t p) {
   CK(cudaMemcpy(&flag, p->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
   if (flag) {
     cudaMemset(p->d_err, 0, sizeof flag);
-    if (flag & 2u)
-      return fail(IMASK_ERR_INVALID, "a back-projector ray window exceeded its planned size");
     return fail(IMASK_ERR_TIMEOUT, "a projector launch gave up waiting for its image strips");
   }
   return IMASK_OK;

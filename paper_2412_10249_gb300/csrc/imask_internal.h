@@ -16,7 +16,7 @@
 #define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
 #define BP_THREADS 256         // back-projector: threads per CTA (one per tile pixel)
 #define BP_TILE 16             // back-projector tile side, every level
-#define BP_VC 4                // back-projector: views staged per shared-memory chunk
+#define BP_SLOTS 512           // back-projector: ray slots per staged chunk (x + y)
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin)
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
 
@@ -42,7 +42,7 @@ struct LevelGeom {
   float cmid;      // (nl - 1) / 2
   int bp_tiles;    // back-projector tiles (BP_TILE x BP_TILE) per side
   int bp_vgo;      // back-projector view groups across CTAs (partial sums)
-  int bp_wmax;     // largest ray window of a tile and view, per major axis
+  int bp_nv;       // largest number of views handled by one CTA
 };
 
 // Everything the kernels need about a plan (passed by value).

@@ -274,22 +274,30 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------------
-// Pixel-driven back-projector: g = R_ell^T y on the level grid.
+// Back-projector: g = R_ell^T y on the level grid, owner-computes (no atomics).
 //
-// A CTA owns a BP_TILE x BP_TILE tile of level pixels (one per thread) and a
-// contiguous range of views (bp_vgo ranges across CTAs; their partial sums are
-// added by the consumer in a fixed order).  Views are processed BP_VC at a
-// time:
-//   1. warp 0 maps the corners of the tile's extended box to detector bins
-//      (the bin map is affine for parallel beam and linear-fractional for fan
-//      beam, so its extremes over the box sit at the corners) and fixes, per
-//      view and major axis, the window of rays that can touch the tile;
-//   2. the CTA stages the window in shared memory: for each ray its local
-//      frame (I, r) on the tile's line block, the slope and g * y;
-//   3. every pixel maps its own two interpolation limits to bins and gathers
-//      the rays in between, weight max(0, 1 - |q - i|) * g with q from the
-//      same local frame as k_fp.
-// No atomics: every output value is owned by one thread.
+// A CTA owns a BP_TILE x BP_TILE tile of level pixels and a contiguous range of
+// views (bp_vgo ranges across CTAs; the consumer adds the partial images in a
+// fixed order).  Thread t owns two private pixel segments of the tile: column
+// t % 16 (16 rows) for x-major rays and row t % 16 (16 columns) for y-major
+// rays, each with its own accumulators in shared memory, and it takes every
+// 16th ray of the staged ray list (t / 16 picks the residue).
+//   prologue  each view of the range gets its ray window: the bins of the
+//             corners of the tile box widened by one pixel across the major
+//             axis (the bin map is affine for parallel beam and
+//             linear-fractional for fan beam, so its extremes over the box
+//             are at corners); window lengths are prefix-summed into one flat
+//             x-major and one flat y-major ray list;
+//   pipeline  the lists are processed in chunks; while chunk k is scattered,
+//             the raw data of chunk k+1 (parameters, low words, y) stream into
+//             the other buffer by cp.async; after a barrier they are converted
+//             in place to (r, t, g y, I') in the local frame of the tile's line
+//             block (block_origin, as in k_fp);
+//   scatter   a thread applies a ray to its segment exactly as k_fp samples
+//             it: q = r + d t, row I + floor(q) gets (1 - f) g y and the next
+//             row f g y, f = q - floor(q); rows outside the tile land in guard
+//             slots.  Only the owner ever touches a slot.
+//   epilogue  every pixel sums its 16 x-major and 16 y-major partial slots.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float bin_of(const DevPlan &P, float c, float s, float x, float y) {
   if (P.geometry == 0) return fmaf(fmaf(x, c, y * s), P.inv_pitch, P.center);
@@ -310,175 +318,271 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) {
   return fminf(fmaxf(v, lo), hi);
 }
 
+__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes) {
+  const uint32_t d = smem_u32(dst);
+  if (bytes == 16)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+#define BP_HALF (BP_SLOTS / 2)   // x-major and y-major entries per chunk
+#define BP_ACC (BP_TILE + 4)     // accumulator slots per segment: 2 guards each side
+
+// shared-memory layout of k_bp
+__device__ __forceinline__ float4 *bp_win(float4 *raw, int b) { return raw + b * BP_SLOTS; }
+__device__ __forceinline__ float2 *bp_lo(float4 *raw, int b) {
+  return (float2 *)(raw + 2 * BP_SLOTS) + b * BP_SLOTS;
+}
+__device__ __forceinline__ float *bp_y(float4 *raw, int b) {
+  return (float *)((float2 *)(raw + 2 * BP_SLOTS) + 2 * BP_SLOTS) + b * BP_SLOTS;
+}
+__device__ __forceinline__ float *bp_acc(float4 *raw) { return bp_y(raw, 2); }
+__device__ __forceinline__ int4 *bp_vinfo(float4 *raw) {
+  return (int4 *)(bp_acc(raw) + 2 * BP_ACC * BP_THREADS);
+}
+
+// last index v in [0, n) with pref[v] <= e (pref non-decreasing, pref[0] = 0)
+__device__ __forceinline__ int find_view(const int *pref, int n, int e) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= e)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block-wide exclusive scan of two counters, each thread holding a run of
+// `per` consecutive values (vals read from / written to a and b in place).
+__device__ void scan2(int *a, int *b, int n, int *tot_a, int *tot_b) {
+  __shared__ int wa[BP_THREADS / 32], wb[BP_THREADS / 32];
+  const int per = (n + BP_THREADS - 1) / BP_THREADS;
+  const int v0 = threadIdx.x * per, v1 = min(v0 + per, n);
+  int sa = 0, sb = 0;
+  for (int v = v0; v < v1; ++v) {
+    sa += a[v];
+    sb += b[v];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int ia = sa, ib = sb;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += ta;
+      ib += tb;
+    }
+  }
+  if (lane == 31) {
+    wa[w] = ia;
+    wb[w] = ib;
+  }
+  __syncthreads();
+  int ba = 0, bb = 0, ta = 0, tb = 0;
+  for (int k = 0; k < BP_THREADS / 32; ++k) {
+    if (k < w) {
+      ba += wa[k];
+      bb += wb[k];
+    }
+    ta += wa[k];
+    tb += wb[k];
+  }
+  int ra = ba + ia - sa, rb = bb + ib - sb;   // exclusive prefix of this run
+  for (int v = v0; v < v1; ++v) {
+    const int ca = a[v], cb = b[v];
+    a[v] = ra;
+    b[v] = rb;
+    ra += ca;
+    rb += cb;
+  }
+  if (threadIdx.x == 0) {
+    a[n] = ta;
+    b[n] = tb;
+  }
+  *tot_a = ta;
+  *tot_b = tb;
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(BP_THREADS, 3)
     k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
-         unsigned int *err) {
-  extern __shared__ __align__(16) float4 win[];
-  __shared__ int wlo[BP_VC][2], wcnt[BP_VC][2], woff[BP_VC][2];
-  __shared__ float vcs[BP_VC][2];
+         unsigned int *err, int nv_cap) {
+  extern __shared__ __align__(16) float4 bp_raw[];
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
-  const int nt = G.bp_tiles, vgo = G.bp_vgo, cap = BP_VC * G.bp_wmax;
+  const int nt = G.bp_tiles, vgo = G.bp_vgo;
   const int vg = blockIdx.x / (nt * nt);
   if (vg >= vgo) return;
   const int tile = blockIdx.x % (nt * nt);
   const int ti = tile / nt, tj = tile % nt;
   const int tid = threadIdx.x;
-  const int i = ti * BP_TILE + tid / BP_TILE, c = tj * BP_TILE + tid % BP_TILE;
-  const bool valid = (i < G.nl) && (c < G.nl);
   const int a0 = (int)(((long long)vg * P.n_angles) / vgo);
   const int a1 = (int)(((long long)(vg + 1) * P.n_angles) / vgo);
+  const int nv = a1 - a0;
   const float hl = G.hl, W = P.fov;
-  const float xc = -0.5f * W + ((float)c + 0.5f) * hl;
-  const float yi = -0.5f * W + ((float)i + 0.5f) * hl;
-  const float dcx = (float)(c - tj * BP_TILE);   // offset in the x-major line block
-  const float dry = (float)(i - ti * BP_TILE);   // offset in the y-major line block
-  const float fi = (float)i, fc = (float)c;
-  // tile box (pixel centres of its first and last column / row on the grid)
-  const int cl = min(tj * BP_TILE + BP_TILE - 1, G.nl - 1), rl_ = min(ti * BP_TILE + BP_TILE - 1, G.nl - 1);
-  const float bx0 = -0.5f * W + ((float)(tj * BP_TILE) + 0.5f) * hl;
-  const float bx1 = -0.5f * W + ((float)cl + 0.5f) * hl;
-  const float by0 = -0.5f * W + ((float)(ti * BP_TILE) + 0.5f) * hl;
-  const float by1 = -0.5f * W + ((float)rl_ + 0.5f) * hl;
-  const float ccx = (float)(tj * BP_TILE) - G.cmid;   // line-block origins (march coordinate)
-  const float ccy = (float)(ti * BP_TILE) - G.cmid;
+  int4 *vinfo = bp_vinfo(bp_raw);                 // li0_x, yi0_x, li0_y, yi0_y per view
+  int *prx = (int *)(vinfo + nv_cap);             // nv_cap + 1 prefix counts (x-major)
+  int *pry = prx + nv_cap + 1;                    // nv_cap + 1 prefix counts (y-major)
+  float *acc = bp_acc(bp_raw);                    // [2 * BP_ACC][BP_THREADS]
 
-  float acc = 0.0f, comp = 0.0f;
-  for (int ab = a0; ab < a1; ab += BP_VC) {
-    const int nv = min(BP_VC, a1 - ab);
-    // ---- 1. ray windows (warp 0: 8 lanes per view, 4 corners per axis) ----
-    if (tid < 32) {
-      const int v = tid >> 3, k = tid & 7, axis = k >> 2, corner = k & 3;
-      float jv = 0.0f;
-      ViewInfo V{};
-      if (v < nv) {
-        V = P.views[ab + v];
-        float x, yy;
-        if (axis == 0) {
-          x = (corner & 1) ? bx1 : bx0;
-          yy = (corner & 2) ? by1 + hl : by0 - hl;
-        } else {
-          x = (corner & 1) ? bx1 + hl : bx0 - hl;
-          yy = (corner & 2) ? by1 : by0;
-        }
-        jv = bin_of(P, V.c, V.s, x, yy);
-      }
-      float mn = jv, mx = jv;
-      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 1));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-      mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, 2));
-      mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-      if (v < nv && corner == 0) {
-        const int j0 = axis == 0 ? V.xj0 : V.yj0, j1 = axis == 0 ? V.xj1 : V.yj1;
-        const int lo = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
-        const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
-        wlo[v][axis] = lo;
-        wcnt[v][axis] = max(hi - lo + 1, 0);
-        if (axis == 0) {
-          vcs[v][0] = V.c;
-          vcs[v][1] = V.s;
-        }
-      }
-      __syncwarp();
-      if (tid == 0) {
-        int off = 0;
-        for (int vv = 0; vv < BP_VC; ++vv)
-          for (int ax = 0; ax < 2; ++ax) {
-            if (vv >= nv) {
-              wcnt[vv][ax] = 0;
-              wlo[vv][ax] = 0;
-            }
-            if (off + wcnt[vv][ax] > cap) {  // never expected: the plan sizes cap
-              atomicOr(err, 2u);
-              wcnt[vv][ax] = max(cap - off, 0);
-            }
-            woff[vv][ax] = off;
-            off += wcnt[vv][ax];
-          }
-      }
-    }
-    __syncthreads();
-    // ---- 2. stage the windows ----
-    const int total = woff[BP_VC - 1][1] + wcnt[BP_VC - 1][1];
-    for (int e = tid; e < total; e += BP_THREADS) {
-      int vv = 0, ax = 0;
+  // ---- prologue: ray windows of every view ----
+  {
+    const int cl = min(tj * BP_TILE + BP_TILE - 1, G.nl - 1);
+    const int rlast = min(ti * BP_TILE + BP_TILE - 1, G.nl - 1);
+    const float bx0 = -0.5f * W + ((float)(tj * BP_TILE) + 0.5f) * hl;
+    const float bx1 = -0.5f * W + ((float)cl + 0.5f) * hl;
+    const float by0 = -0.5f * W + ((float)(ti * BP_TILE) + 0.5f) * hl;
+    const float by1 = -0.5f * W + ((float)rlast + 0.5f) * hl;
+    for (int v = tid; v < nv; v += BP_THREADS) {
+      const ViewInfo V = P.views[a0 + v];
+      int lo[2], cnt[2];
 #pragma unroll
-      for (int q = 0; q < 2 * BP_VC; ++q)
-        if (e >= woff[q >> 1][q & 1]) {
-          vv = q >> 1;
-          ax = q & 1;
+      for (int axis = 0; axis < 2; ++axis) {
+        float mn = 1.0e30f, mx = -1.0e30f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float x, yy;
+          if (axis == 0) {
+            x = (k & 1) ? bx1 : bx0;
+            yy = (k & 2) ? by1 + hl : by0 - hl;
+          } else {
+            x = (k & 1) ? bx1 + hl : bx0 - hl;
+            yy = (k & 2) ? by1 : by0;
+          }
+          const float j = bin_of(P, V.c, V.s, x, yy);
+          mn = fminf(mn, j);
+          mx = fmaxf(mx, j);
         }
-      const int j = wlo[vv][ax] + (e - woff[vv][ax]);
-      const ViewInfo V = P.views[ab + vv];
-      const int li = ax == 0 ? V.xoff + (j - V.xj0) : V.yoff + (j - V.yj0);
-      const float4 p = P.rays[li];
-      const float2 pl = P.rays_lo[li];
-      const float yv = __ldg(y + (size_t)(ab + vv) * P.n_det + j);
+        const int j0 = axis == 0 ? V.xj0 : V.yj0, j1 = axis == 0 ? V.xj1 : V.yj1;
+        lo[axis] = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
+        const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
+        cnt[axis] = max(hi - lo[axis] + 1, 0);
+      }
+      const int yrow = (a0 + v) * P.n_det;
+      vinfo[v] = make_int4(V.xoff - V.xj0 + lo[0], yrow + lo[0], V.yoff - V.yj0 + lo[1],
+                           yrow + lo[1]);
+      prx[v] = cnt[0];
+      pry[v] = cnt[1];
+    }
+    for (int k = tid; k < 2 * BP_ACC * BP_THREADS; k += BP_THREADS) acc[k] = 0.0f;
+  }
+  __syncthreads();
+  int NX, NY;
+  scan2(prx, pry, nv, &NX, &NY);
+
+  const int g = tid >> 4;                        // ray residue class of this thread
+  const float dseg = (float)(tid & (BP_TILE - 1));   // own line inside the block
+  const float ccx = (float)(tj * BP_TILE) - G.cmid;  // line-block origins
+  const float ccy = (float)(ti * BP_TILE) - G.cmid;
+  float *accx = acc + tid;                       // column segment (x-major rays)
+  float *accy = acc + BP_ACC * BP_THREADS + tid; // row segment (y-major rays)
+  const int nch = max((NX + BP_HALF - 1) / BP_HALF, (NY + BP_HALF - 1) / BP_HALF);
+
+  // raw data of chunk k into buffer b: slots [0, BP_HALF) x-major, the rest y-major
+  auto stage = [&](int k, int b) {
+    float4 *win = bp_win(bp_raw, b);
+    float2 *lo = bp_lo(bp_raw, b);
+    float *yv = bp_y(bp_raw, b);
+    for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
+      const bool xs = sl < BP_HALF;
+      const int e = k * BP_HALF + (xs ? sl : sl - BP_HALF);
+      if (e >= (xs ? NX : NY)) continue;
+      const int v = find_view(xs ? prx : pry, nv, e);
+      const int kk = e - (xs ? prx[v] : pry[v]);
+      const int4 vi = vinfo[v];
+      const int li = (xs ? vi.x : vi.z) + kk;
+      const int yi = (xs ? vi.y : vi.w) + kk;
+      cp_async(win + sl, P.rays + li, 16);
+      cp_async(lo + sl, P.rays_lo + li, 8);
+      cp_async(yv + sl, y + yi, 4);
+    }
+    cp_async_commit();
+  };
+  // in-place conversion to (r, t, g y, I - first line of the segment + 2)
+  auto convert = [&](int k, int b) {
+    float4 *win = bp_win(bp_raw, b);
+    const float2 *lo = bp_lo(bp_raw, b);
+    const float *yv = bp_y(bp_raw, b);
+    for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
+      const bool xs = sl < BP_HALF;
+      const int e = k * BP_HALF + (xs ? sl : sl - BP_HALF);
+      if (e >= (xs ? NX : NY)) continue;
+      const float4 p = win[sl];
+      const float2 pl = lo[sl];
       int I;
       float r;
-      block_origin(p.x, pl.x, p.y, pl.y, G.inv2l, ax == 0 ? ccx : ccy, I, r);
-      win[e] = make_float4(r, p.y, p.z * yv, (float)I);
+      block_origin(p.x, pl.x, p.y, pl.y, G.inv2l, xs ? ccx : ccy, I, r);
+      const int base = xs ? ti * BP_TILE : tj * BP_TILE;   // first cross line of the tile
+      win[sl] = make_float4(r, p.y, p.z * yv[sl], __int_as_float(I - base + 2));
     }
+  };
+
+  if (nch > 0) {
+    stage(0, 0);
+    cp_async_wait_all();
     __syncthreads();
-    // ---- 3. gather ----
-    for (int vv = 0; vv < nv; ++vv) {
-      const float vc = vcs[vv][0], vs = vcs[vv][1];
-      float pv = 0.0f;
-      if (wcnt[vv][0] > 0) {   // x-major rays: march over columns, interpolate rows
-        int lo = 0, cnt = 0;
-        if (valid) {
-          const float ja = bin_of(P, vc, vs, xc, yi - hl), jb = bin_of(P, vc, vs, xc, yi + hl);
-          lo = max(ceil_i(clampf(fminf(ja, jb) - kBpEps, -1.0e6f, 1.0e6f)), wlo[vv][0]);
-          const int hi = min(floor_i(clampf(fmaxf(ja, jb) + kBpEps, -1.0e6f, 1.0e6f)),
-                             wlo[vv][0] + wcnt[vv][0] - 1);
-          cnt = max(hi - lo + 1, 0);
-        }
-        const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-        const float4 *wp = win + woff[vv][0] + (lo - wlo[vv][0]);
-        for (int k = 0; k < cmax; ++k) {
-          if (k < cnt) {
-            const float4 e = wp[k];
-            const float q = fmaf(dcx, e.y, e.x);
-            const float w = fmaxf(0.0f, 1.0f - fabsf(q - (fi - e.w)));
-            pv = fmaf(w, e.z, pv);
-          }
-        }
-      }
-      if (wcnt[vv][1] > 0) {   // y-major rays: march over rows, interpolate columns
-        int lo = 0, cnt = 0;
-        if (valid) {
-          const float ja = bin_of(P, vc, vs, xc - hl, yi), jb = bin_of(P, vc, vs, xc + hl, yi);
-          lo = max(ceil_i(clampf(fminf(ja, jb) - kBpEps, -1.0e6f, 1.0e6f)), wlo[vv][1]);
-          const int hi = min(floor_i(clampf(fmaxf(ja, jb) + kBpEps, -1.0e6f, 1.0e6f)),
-                             wlo[vv][1] + wcnt[vv][1] - 1);
-          cnt = max(hi - lo + 1, 0);
-        }
-        const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-        const float4 *wp = win + woff[vv][1] + (lo - wlo[vv][1]);
-        for (int k = 0; k < cmax; ++k) {
-          if (k < cnt) {
-            const float4 e = wp[k];
-            const float q = fmaf(dry, e.y, e.x);
-            const float w = fmaxf(0.0f, 1.0f - fabsf(q - (fc - e.w)));
-            pv = fmaf(w, e.z, pv);
-          }
-        }
-      }
-      // compensated (Kahan) sum over views
-      const float yk = pv - comp;
-      const float tk = acc + yk;
-      comp = (tk - acc) - yk;
-      acc = tk;
-    }
+    convert(0, 0);
     __syncthreads();
   }
-  if (valid) gout[(size_t)vg * G.nl * G.nl + (size_t)i * G.nl + c] = acc * G.scale2l;
+  for (int k = 0; k < nch; ++k) {
+    const int b = k & 1;
+    if (k + 1 < nch) stage(k + 1, b ^ 1);
+    const float4 *win = bp_win(bp_raw, b);
+    const int nx = min(BP_HALF, NX - k * BP_HALF), ny = min(BP_HALF, NY - k * BP_HALF);
+    for (int sl = g; sl < nx; sl += BP_THREADS / BP_TILE) {
+      const float4 e = win[sl];
+      const float q = fmaf(dseg, e.y, e.x);
+      const float tq = __fadd_rd(q, kMagic);
+      const int slot = min(max(__float_as_int(tq) - kMagicBits + __float_as_int(e.w), 0), BP_ACC - 2);
+      const float f = q - (tq - kMagic);
+      const float w1 = f * e.z;
+      float *pa = accx + slot * BP_THREADS;
+      pa[0] += e.z - w1;
+      pa[BP_THREADS] += w1;
+    }
+    for (int sl = g; sl < ny; sl += BP_THREADS / BP_TILE) {
+      const float4 e = win[BP_HALF + sl];
+      const float q = fmaf(dseg, e.y, e.x);
+      const float tq = __fadd_rd(q, kMagic);
+      const int slot = min(max(__float_as_int(tq) - kMagicBits + __float_as_int(e.w), 0), BP_ACC - 2);
+      const float f = q - (tq - kMagic);
+      const float w1 = f * e.z;
+      float *pa = accy + slot * BP_THREADS;
+      pa[0] += e.z - w1;
+      pa[BP_THREADS] += w1;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (k + 1 < nch) {
+      convert(k + 1, b ^ 1);
+      __syncthreads();
+    }
+  }
+  // ---- epilogue: pixel (i, c) of the tile sums its owners' slots ----
+  const int il = tid / BP_TILE, cl2 = tid % BP_TILE;
+  const int i = ti * BP_TILE + il, c = tj * BP_TILE + cl2;
+  if (i < G.nl && c < G.nl) {
+    float sx = 0.0f, sy = 0.0f;
+#pragma unroll
+    for (int gg = 0; gg < BP_THREADS / BP_TILE; ++gg) {
+      sx += acc[(il + 2) * BP_THREADS + cl2 + BP_TILE * gg];
+      sy += acc[(BP_ACC + cl2 + 2) * BP_THREADS + il + BP_TILE * gg];
+    }
+    gout[(size_t)vg * G.nl * G.nl + (size_t)i * G.nl + c] = (sx + sy) * G.scale2l;
+  }
 }
-
-// ---------------------------------------------------------------------------------
-// Image-side sketches on fine-pixel tiles of side P.upd_tile (a multiple of
-// 2^(r-1) that divides n), so every block of every level lies inside one tile.
-// ---------------------------------------------------------------------------------
 
 // The back-projector leaves bp_vgo partial images (one per view group), each
 // of side nl; their sum in a fixed order is R_ell^T y.
@@ -875,10 +979,15 @@ cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, 
   return cudaGetLastError();
 }
 
+static int bp_nv_cap(const DevPlan &P) {
+  int nv = 0;
+  for (int li = 0; li <= P.levels; ++li) nv = max(nv, P.lg[li].bp_nv);
+  return nv;
+}
+
 long long bp_smem_bytes(const DevPlan &P) {
-  int w = 0;
-  for (int li = 0; li <= P.levels; ++li) w = max(w, P.lg[li].bp_wmax);
-  return (long long)BP_VC * w * (long long)sizeof(float4);
+  return 2LL * BP_SLOTS * (16 + 8 + 4) + 2LL * BP_ACC * BP_THREADS * 4 +
+         (long long)bp_nv_cap(P) * 16 + 2LL * (bp_nv_cap(P) + 1) * 4;
 }
 
 cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
@@ -893,7 +1002,7 @@ cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
   cudaError_t e = set_smem((const void *)k_bp, sm);
   if (e != cudaSuccess) return e;
   count_launch();
-  k_bp<<<most, BP_THREADS, sm, st>>>(P, sel, y, g, err);
+  k_bp<<<most, BP_THREADS, sm, st>>>(P, sel, y, g, err, bp_nv_cap(P));
   return cudaGetLastError();
 }
 
