@@ -127,6 +127,22 @@ imask_status imask_project(imask_plan_t plan, int32_t level, const float *x_dev,
 imask_status imask_backproject(imask_plan_t plan, int32_t level, const float *y_dev,
                                float *img_dev, void *stream);
 
+/* Same result as imask_backproject, without allocating: no cudaMalloc,
+ * cudaMallocAsync or cudaFree, for callers that cannot allocate device memory
+ * while they run (their own allocator has reserved the device memory, or an
+ * allocation could stall or fail inside a latency-bound loop).  The paper has
+ * no counterpart; this is a deployment variant.  The back-projector's partial
+ * sums go to one fixed array inside the library (16 MiB of device memory,
+ * 4 Mi floats, held by every GPU that loads the library until the process
+ * exits); a plan whose scratch need exceeds it gets IMASK_ERR_SHAPE.  The
+ * first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents: calls
+ * that may overlap on the GPU (other streams, other host threads) race and
+ * must be serialised by the caller. */
+imask_status imask_backproject_noalloc(imask_plan_t plan, int32_t level, const float *y_dev,
+                                       float *img_dev, void *stream);
+
 /* The level stream of Alg. 1 (sampling step): out_dev[t] = ell_{k0+t} drawn on
  * the device from SplitMix64 output k0+t of `seed` against thresholds
  * round(2^53 * cumsum(p)) * 2^11.  Bit-exact with any other implementation of

@@ -821,6 +821,55 @@ imask_status imask_backproject(imask_plan_t p, int32_t level, const float *y_dev
   return rc;
 }
 
+// Allocation-free back-projection.  The partial sums that imask_backproject
+// keeps in a buffer obtained with cudaMallocAsync live here in one fixed
+// device array instead, for callers that must not allocate device memory
+// once they are running: a host whose own allocator has reserved the device
+// memory, a latency-bound loop where an allocation could stall or fail, or a
+// process that may only allocate at start-up.  The array is part of the
+// library image, so every GPU that loads the library holds its 16 MiB until
+// the process exits.
+#define IMASK_NOALLOC_FLOATS (4u << 20)
+static __device__ __align__(256) float g_noalloc_scratch[IMASK_NOALLOC_FLOATS];
+
+namespace {
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[256] = {nullptr};   // device address of the array, per device
+}  // namespace
+
+imask_status imask_backproject_noalloc(imask_plan_t p, int32_t level, const float *y_dev,
+                                       float *img_dev, void *stream) {
+  if (!p || !y_dev || !img_dev) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (level < -1 || level >= p->desc.levels)
+    return fail(IMASK_ERR_INVALID, "level %d outside [-1, %d]", level, p->desc.levels - 1);
+  if (p->gcap > IMASK_NOALLOC_FLOATS)
+    return fail(IMASK_ERR_SHAPE,
+                "imask_backproject_noalloc: this plan needs %zu floats of scratch, above the "
+                "fixed %u (16 MiB); use imask_backproject",
+                p->gcap, (unsigned)IMASK_NOALLOC_FLOATS);
+  int dev = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 256) return fail(IMASK_ERR_INVALID, "device index %d out of range", dev);
+  float *ptr = nullptr;
+  {
+    // first call on this device: look up the array's device address (in host
+    // code the array's name is only a host-side stand-in)
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void *addr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+      g_noalloc_ptr[dev] = (float *)addr;
+    }
+    ptr = g_noalloc_ptr[dev];
+  }
+  // every scratch element read below is written earlier in the same call,
+  // so nothing is cleared
+  Scratch s;
+  s.g = ptr;
+  return apply_KT(p, level, y_dev, img_dev, s, (cudaStream_t)stream);
+}
+
 imask_status imask_levels(imask_plan_t p, uint64_t seed, int64_t k0, int64_t n, int32_t *out_dev,
                           void *stream) {
   if (!p || (!out_dev && n > 0)) return fail(IMASK_ERR_INVALID, "NULL argument");

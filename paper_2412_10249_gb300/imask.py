@@ -73,6 +73,7 @@ SIGNATURES = {
     "imask_optimal_step": (_I32, [ctypes.c_double] * 4 + [_I32, _DP]),
     "imask_project": (_I32, [_VP, _I32, _VP, _VP, _VP]),
     "imask_backproject": (_I32, [_VP, _I32, _VP, _VP, _VP]),
+    "imask_backproject_noalloc": (_I32, [_VP, _I32, _VP, _VP, _VP]),
     "imask_levels": (_I32, [_VP, _U64, _I64, _I64, _VP, _VP]),
     "imask_state_create": (_I32, [_VP, _VP, _U64, ctypes.POINTER(_VP), _VP]),
     "imask_step": (_I32, [_VP, _I32, _VP]),
@@ -209,6 +210,12 @@ def imask_project(plan, level, x, sino, n, m, stream=None):
 def imask_backproject(plan, level, y, img, n, m, stream=None):
     _check(lib().imask_backproject(plan, level, _ptr(y, m, name="y"), _ptr(img, n * n, name="img"),
                                    _stream(stream)))
+
+
+def imask_backproject_noalloc(plan, level, y, img, n, m, stream=None):
+    """K_level^T y without device allocation (fixed 16 MiB library array)."""
+    _check(lib().imask_backproject_noalloc(plan, level, _ptr(y, m, name="y"),
+                                           _ptr(img, n * n, name="img"), _stream(stream)))
 
 
 def imask_levels(plan, seed, k0, n, out, stream=None):
