@@ -258,7 +258,7 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   LevelGeom g{};
   const int sh = ell > 0 ? ell : 0;
   g.nl = d.n >> sh;
-  g.ls = g.nl + 2 * IMASK_PAD;
+  g.ls = g.nl + IMASK_PAD + IMASK_PAD_END;
   int tc = (FP_STAGE_FLOATS / g.ls) & ~3;
   tc = std::min(32, std::max(4, tc));
   g.tc = tc;
@@ -268,7 +268,7 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   g.hl = (float)(d.fov / (double)g.nl);
   g.cmid = 0.5f * (float)(g.nl - 1);
   g.bp_tiles = (g.nl + BP_TILE - 1) / BP_TILE;
-  // view groups across CTAs: aim at >= 4 CTAs per SM in total
+  // view groups across CTAs: aim at about four CTAs per SM in total
   const int tiles = g.bp_tiles * g.bp_tiles;
   g.bp_vgo = std::max(1, std::min(d.n_angles, (4 * 152 + tiles - 1) / tiles));
   return g;

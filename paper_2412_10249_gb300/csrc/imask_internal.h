@@ -8,7 +8,8 @@
 #include "../../include/imask.h"
 
 #define IMASK_MAX_LEVELS 8
-#define IMASK_PAD 4            // zero entries before and after every padded image line
+#define IMASK_PAD 34           // zero entries before every padded image line
+#define IMASK_PAD_END 18       // zero entries after every padded image line
 #define FP_THREADS 512         // forward projector: threads per CTA
 #define FP_RAYS 4              // forward projector: rays per thread
 #define FP_CHUNK (FP_THREADS * FP_RAYS)
@@ -16,7 +17,7 @@
 #define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
 #define BP_THREADS 256         // back-projector: threads per CTA (one per tile pixel)
 #define BP_TILE 16             // back-projector tile side, every level
-#define BP_SLOTS 512           // back-projector: ray slots per staged chunk (x + y)
+#define BP_SLOTS 256           // back-projector: ray slots per staged chunk (x + y)
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin)
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
 
@@ -33,7 +34,7 @@ struct ViewInfo {
 // full-resolution grid (level -1), index ell + 1 is level ell.
 struct LevelGeom {
   int nl;          // grid side
-  int ls;          // padded line stride, nl + 2 * IMASK_PAD
+  int ls;          // padded line stride, nl + IMASK_PAD + IMASK_PAD_END
   int lines;       // lines allocated (a multiple of tc)
   int tc;          // lines per TMA strip
   float inv2l;     // 2^-ell (1 for level -1)

@@ -135,14 +135,18 @@ __device__ __forceinline__ void block_origin(float a_hi, float a_lo, float t_hi,
 // contiguous) and interpolates linearly between the rows I + floor(r + d t) and
 // the next one.  Strips of tc lines are streamed through FP_STAGES
 // shared-memory buffers by cp.async.bulk.  Every line carries IMASK_PAD zeros
-// on both sides; clamping the row index into [-2, nl] therefore reads zeros for
-// rows off the grid without a branch.
+// before and IMASK_PAD_END after the grid rows.  Within one block of LBLOCK
+// lines a ray moves by at most 16 rows (|slope| <= 1), so a block that touches
+// the grid reads rows in [-18, nl + 16], inside the padding, and a block that
+// misses the grid entirely is redirected into the leading zeros: no per-sample
+// bounds check is needed.
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(FP_THREADS, 2)
     k_fp(DevPlan P, LevelSel sel, PadSet pads, float *sino, DualArgs D, int n_cta_x,
          unsigned int *err) {
   extern __shared__ __align__(128) float fp_smem[];
   __shared__ __align__(8) unsigned long long full_bar[FP_STAGES];
+  __shared__ unsigned int released[FP_STAGES];   // warps done with each stage (monotone)
 
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
@@ -178,10 +182,12 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 
   const int tc = G.tc, ls = G.ls;
   const int nstrips = G.lines / tc;
-  const int ilo = IMASK_PAD - 2, ihi = IMASK_PAD + G.nl;
   const uint32_t strip_bytes = (uint32_t)(tc * ls) * 4u;
   if (tid == 0) {
-    for (int s = 0; s < FP_STAGES; ++s) mbar_init(smem_u32(&full_bar[s]), 1);
+    for (int s = 0; s < FP_STAGES; ++s) {
+      mbar_init(smem_u32(&full_bar[s]), 1);
+      released[s] = 0u;
+    }
     mbar_fence_init();
   }
   __syncthreads();
@@ -190,12 +196,22 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
       bulk_load(smem_u32(fp_smem + s * FP_STAGE_FLOATS), img + (size_t)s * tc * ls, strip_bytes,
                 smem_u32(&full_bar[s]));
   }
+  constexpr unsigned kWarps = FP_THREADS / 32;
+  const int lane = tid & 31;
 
+  // Warps move through the strips independently (up to FP_STAGES apart): a
+  // warp releases a stage when it is done with it, and the warp that releases
+  // it last refills it with the strip FP_STAGES further on.
   bool failed = false;
+  unsigned act = 0u;   // ray slots with at least one on-grid ray in the warp (this block)
   for (int s = 0; s < nstrips; ++s) {
     const int st = s % FP_STAGES;
     const uint32_t parity = (uint32_t)((s / FP_STAGES) & 1);
-    const bool ok = mbar_wait(smem_u32(&full_bar[st]), parity);
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[st]), parity));
+    if (!ok) {
+      failed = true;
+      break;
+    }
     const float *buf = fp_smem + st * FP_STAGE_FLOATS;
     float part[FP_RAYS];
 #pragma unroll
@@ -204,44 +220,59 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
       const int c = s * tc + cc;
       if ((c & (LBLOCK - 1)) == 0) {
         const float ccm = (float)c - G.cmid;
+        act = 0u;
 #pragma unroll
         for (int r = 0; r < FP_RAYS; ++r) {
           int I;
           block_origin(ahi[r], alo[r], thi[r], tlo[r], G.inv2l, ccm, I, rl[r]);
-          boff[r] = IMASK_PAD + I;
+          // rows of the block's first and last sample
+          const int f0 = __float_as_int(__fadd_rd(rl[r], kMagic)) - kMagicBits;
+          const int f1 =
+              __float_as_int(__fadd_rd(fmaf((float)(LBLOCK - 1), thi[r], rl[r]), kMagic)) -
+              kMagicBits;
+          const int lo = I + min(f0, f1), hi = I + max(f0, f1);
+          // off the grid (no row in [0, nl-1] is read): land in the leading zeros
+          const bool off = (hi + 1 < 0) || (lo > G.nl - 1);
+          boff[r] = off ? (IMASK_PAD / 2) - f0 : IMASK_PAD + I;
+          // a slot whose 32 rays all miss the grid in this block adds exactly
+          // zero: the warp skips its samples (the branch is warp-uniform)
+          act |= (__any_sync(0xffffffffu, !off) ? 1u : 0u) << r;
         }
       }
       const float d0 = (float)(c & (LBLOCK - 1));
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const float dcf = d0 + (float)u;
-        const float *line = buf + (cc + u) * ls;
+      for (int r = 0; r < FP_RAYS; ++r) {
+        if (!(act & (1u << r))) continue;
+        float a[4];
 #pragma unroll
-        for (int r = 0; r < FP_RAYS; ++r) {
+        for (int u = 0; u < 4; ++u) {
+          const float dcf = d0 + (float)u;
+          const float *line = buf + (cc + u) * ls;
           const float q = fmaf(dcf, thi[r], rl[r]);
           const float tq = __fadd_rd(q, kMagic);
-          int i0 = boff[r] + (__float_as_int(tq) - kMagicBits);
-          i0 = min(max(i0, ilo), ihi);
+          const int i0 = boff[r] + (__float_as_int(tq) - kMagicBits);
           const float f = q - (tq - kMagic);
           const float v0 = line[i0];
           const float v1 = line[i0 + 1];
-          part[r] = fmaf(f, v1 - v0, part[r] + v0);
+          a[u] = fmaf(f, v1 - v0, v0);   // independent samples, summed as a tree
         }
+        part[r] += (a[0] + a[1]) + (a[2] + a[3]);
       }
     }
 #pragma unroll
     for (int r = 0; r < FP_RAYS; ++r) acc[r] += part[r];
-    if (__syncthreads_or(!ok)) {
-      failed = true;
-      break;
-    }
-    if (tid == 0 && s + FP_STAGES < nstrips) {
-      fence_proxy_async();
-      bulk_load(smem_u32(fp_smem + st * FP_STAGE_FLOATS), img + (size_t)(s + FP_STAGES) * tc * ls,
-                strip_bytes, smem_u32(&full_bar[st]));
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();   // this warp's reads of the stage come first
+      const unsigned n = atomicAdd(&released[st], 1u) + 1u;
+      if (n % kWarps == 0u && s + FP_STAGES < nstrips) {
+        fence_proxy_async();
+        bulk_load(smem_u32(fp_smem + st * FP_STAGE_FLOATS),
+                  img + (size_t)(s + FP_STAGES) * tc * ls, strip_bytes, smem_u32(&full_bar[st]));
+      }
     }
   }
-  if (failed) {
+  if (__syncthreads_or(failed)) {
     if (tid == 0) {
       atomicOr(err, 1u);
       // give the copies still in flight a bounded chance to land before exit
@@ -347,10 +378,7 @@ __device__ __forceinline__ float2 *bp_lo(float4 *raw, int b) {
 __device__ __forceinline__ float *bp_y(float4 *raw, int b) {
   return (float *)((float2 *)(raw + 2 * BP_SLOTS) + 2 * BP_SLOTS) + b * BP_SLOTS;
 }
-__device__ __forceinline__ float *bp_acc(float4 *raw) { return bp_y(raw, 2); }
-__device__ __forceinline__ int4 *bp_vinfo(float4 *raw) {
-  return (int4 *)(bp_acc(raw) + 2 * BP_ACC * BP_THREADS);
-}
+__device__ __forceinline__ int4 *bp_vinfo(float4 *raw) { return (int4 *)bp_y(raw, 2); }
 
 // last index v in [0, n) with pref[v] <= e (pref non-decreasing, pref[0] = 0)
 __device__ __forceinline__ int find_view(const int *pref, int n, int e) {
@@ -420,6 +448,10 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
     k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
          unsigned int *err, int nv_cap) {
   extern __shared__ __align__(16) float4 bp_raw[];
+  // private accumulators: [slot][thread], slots 0..19 = rows -2..17 of the
+  // owner's segment; separate arrays so x- and y-major updates never alias
+  __shared__ float accx_s[BP_ACC * BP_THREADS];
+  __shared__ float accy_s[BP_ACC * BP_THREADS];
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
   const int nt = G.bp_tiles, vgo = G.bp_vgo;
@@ -435,7 +467,6 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
   int4 *vinfo = bp_vinfo(bp_raw);                 // li0_x, yi0_x, li0_y, yi0_y per view
   int *prx = (int *)(vinfo + nv_cap);             // nv_cap + 1 prefix counts (x-major)
   int *pry = prx + nv_cap + 1;                    // nv_cap + 1 prefix counts (y-major)
-  float *acc = bp_acc(bp_raw);                    // [2 * BP_ACC][BP_THREADS]
 
   // ---- prologue: ray windows of every view ----
   {
@@ -476,7 +507,10 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
       prx[v] = cnt[0];
       pry[v] = cnt[1];
     }
-    for (int k = tid; k < 2 * BP_ACC * BP_THREADS; k += BP_THREADS) acc[k] = 0.0f;
+    for (int k = tid; k < BP_ACC * BP_THREADS; k += BP_THREADS) {
+      accx_s[k] = 0.0f;
+      accy_s[k] = 0.0f;
+    }
   }
   __syncthreads();
   int NX, NY;
@@ -486,8 +520,8 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
   const float dseg = (float)(tid & (BP_TILE - 1));   // own line inside the block
   const float ccx = (float)(tj * BP_TILE) - G.cmid;  // line-block origins
   const float ccy = (float)(ti * BP_TILE) - G.cmid;
-  float *accx = acc + tid;                       // column segment (x-major rays)
-  float *accy = acc + BP_ACC * BP_THREADS + tid; // row segment (y-major rays)
+  float *accx = accx_s + tid;                    // column segment (x-major rays)
+  float *accy = accy_s + tid;                    // row segment (y-major rays)
   const int nch = max((NX + BP_HALF - 1) / BP_HALF, (NY + BP_HALF - 1) / BP_HALF);
 
   // raw data of chunk k into buffer b: slots [0, BP_HALF) x-major, the rest y-major
@@ -541,27 +575,42 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
     if (k + 1 < nch) stage(k + 1, b ^ 1);
     const float4 *win = bp_win(bp_raw, b);
     const int nx = min(BP_HALF, NX - k * BP_HALF), ny = min(BP_HALF, NY - k * BP_HALF);
-    for (int sl = g; sl < nx; sl += BP_THREADS / BP_TILE) {
-      const float4 e = win[sl];
-      const float q = fmaf(dseg, e.y, e.x);
-      const float tq = __fadd_rd(q, kMagic);
-      const int slot = min(max(__float_as_int(tq) - kMagicBits + __float_as_int(e.w), 0), BP_ACC - 2);
-      const float f = q - (tq - kMagic);
-      const float w1 = f * e.z;
-      float *pa = accx + slot * BP_THREADS;
-      pa[0] += e.z - w1;
-      pa[BP_THREADS] += w1;
-    }
-    for (int sl = g; sl < ny; sl += BP_THREADS / BP_TILE) {
-      const float4 e = win[BP_HALF + sl];
-      const float q = fmaf(dseg, e.y, e.x);
-      const float tq = __fadd_rd(q, kMagic);
-      const int slot = min(max(__float_as_int(tq) - kMagicBits + __float_as_int(e.w), 0), BP_ACC - 2);
-      const float f = q - (tq - kMagic);
-      const float w1 = f * e.z;
-      float *pa = accy + slot * BP_THREADS;
-      pa[0] += e.z - w1;
-      pa[BP_THREADS] += w1;
+    const int nmax = max(nx, ny);
+    constexpr int STEP = BP_THREADS / BP_TILE;
+    // x- and y-major rays interleaved (independent accumulator arrays), the
+    // next pair of entries loaded while the current one is applied
+    // indices clamped into the buffer: loads beyond a list are harmless and unused
+    const int xlast = max(nx - 1, 0), ylast = max(ny - 1, 0);
+    float4 ex = win[min(g, xlast)];
+    float4 ey = win[BP_HALF + min(g, ylast)];
+    for (int sl = g; sl < nmax; sl += STEP) {
+      const int sn = sl + STEP;
+      const float4 exn = win[min(sn, xlast)];
+      const float4 eyn = win[BP_HALF + min(sn, ylast)];
+      if (sl < nx) {
+        const float q = fmaf(dseg, ex.y, ex.x);
+        const float tq = __fadd_rd(q, kMagic);
+        const int slot =
+            min(max(__float_as_int(tq) - kMagicBits + __float_as_int(ex.w), 0), BP_ACC - 2);
+        const float f = q - (tq - kMagic);
+        const float w1 = f * ex.z;
+        float *pa = accx + slot * BP_THREADS;
+        pa[0] += ex.z - w1;
+        pa[BP_THREADS] += w1;
+      }
+      if (sl < ny) {
+        const float q = fmaf(dseg, ey.y, ey.x);
+        const float tq = __fadd_rd(q, kMagic);
+        const int slot =
+            min(max(__float_as_int(tq) - kMagicBits + __float_as_int(ey.w), 0), BP_ACC - 2);
+        const float f = q - (tq - kMagic);
+        const float w1 = f * ey.z;
+        float *pa = accy + slot * BP_THREADS;
+        pa[0] += ey.z - w1;
+        pa[BP_THREADS] += w1;
+      }
+      ex = exn;
+      ey = eyn;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -577,8 +626,8 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
     float sx = 0.0f, sy = 0.0f;
 #pragma unroll
     for (int gg = 0; gg < BP_THREADS / BP_TILE; ++gg) {
-      sx += acc[(il + 2) * BP_THREADS + cl2 + BP_TILE * gg];
-      sy += acc[(BP_ACC + cl2 + 2) * BP_THREADS + il + BP_TILE * gg];
+      sx += accx_s[(il + 2) * BP_THREADS + cl2 + BP_TILE * gg];
+      sy += accy_s[(cl2 + 2) * BP_THREADS + il + BP_TILE * gg];
     }
     gout[(size_t)vg * G.nl * G.nl + (size_t)i * G.nl + c] = (sx + sy) * G.scale2l;
   }
@@ -985,9 +1034,9 @@ static int bp_nv_cap(const DevPlan &P) {
   return nv;
 }
 
-long long bp_smem_bytes(const DevPlan &P) {
-  return 2LL * BP_SLOTS * (16 + 8 + 4) + 2LL * BP_ACC * BP_THREADS * 4 +
-         (long long)bp_nv_cap(P) * 16 + 2LL * (bp_nv_cap(P) + 1) * 4;
+long long bp_smem_bytes(const DevPlan &P) {   // dynamic part only
+  return 2LL * BP_SLOTS * (16 + 8 + 4) + (long long)bp_nv_cap(P) * 16 +
+         2LL * (bp_nv_cap(P) + 1) * 4;
 }
 
 cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
