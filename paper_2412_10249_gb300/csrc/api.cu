@@ -267,10 +267,9 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   g.scale2l = (float)ldexp(1.0, sh);
   g.hl = (float)(d.fov / (double)g.nl);
   g.cmid = 0.5f * (float)(g.nl - 1);
-  g.bp_tiles = (g.nl + BP_TILE - 1) / BP_TILE;
-  // view groups across CTAs: aim at about four CTAs per SM in total
-  const int tiles = g.bp_tiles * g.bp_tiles;
-  g.bp_vgo = std::max(1, std::min(d.n_angles, (4 * 152 + tiles - 1) / tiles));
+  g.bp_nm = (g.nl + BP_W - 1) / BP_W;
+  g.bp_nc = (g.nl + BP_SEG - 1) / BP_SEG;
+  g.bp_vgo = 1;   // chosen per device in imask_plan
   return g;
 }
 
@@ -691,19 +690,59 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   level_thresholds(p->probs, dp.thr);
   dp.lg[0] = level_geom(*desc, -1);
   for (int l = 0; l < r; ++l) dp.lg[l + 1] = level_geom(*desc, l);
+  dp.upd_tile = update_tile(desc->n, r);
+  // Grid sizes from the SM count: the projector runs exactly one wave of
+  // 2 CTAs per SM (ray chunks shrink below FP_CHUNK to fill it); the
+  // back-projector's view groups are chosen for the best last-wave occupancy
+  // of 3 CTAs per SM.
+  int n_sm = 152;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      int v = 0;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+        n_sm = v;
+    }
+  }
+  {
+    const int m_y = dp.m - m_x;
+    const int target = 2 * n_sm;
+    int cx = m_x > 0 ? std::max(1, (int)std::lround((double)target * m_x / dp.m)) : 0;
+    int cy = m_y > 0 ? std::max(1, target - cx) : 0;
+    cx = std::max(cx, (m_x + FP_CHUNK - 1) / FP_CHUNK);
+    cy = std::max(cy, (m_y + FP_CHUNK - 1) / FP_CHUNK);
+    dp.fp_chunk_x = cx > 0 ? (m_x + cx - 1) / cx : 1;
+    dp.fp_chunk_y = cy > 0 ? (m_y + cy - 1) / cy : 1;
+    p->n_cta_x = cx > 0 ? (m_x + dp.fp_chunk_x - 1) / dp.fp_chunk_x : 0;
+    p->n_cta_y = cy > 0 ? (m_y + dp.fp_chunk_y - 1) / dp.fp_chunk_y : 0;
+  }
+  for (int li = 0; li <= r; ++li) {
+    LevelGeom &g = dp.lg[li];
+    const double slots = 3.0 * n_sm;
+    const int tiles = 2 * g.bp_nm * g.bp_nc;   // x- and y-major CTAs per view group
+    const int vmax = std::max(1, std::min(desc->n_angles, (int)std::ceil(4.0 * slots / tiles)));
+    double best = -1.0;
+    int bv = 1;
+    for (int v = 1; v <= vmax; ++v) {
+      const double waves = tiles * (double)v / slots;
+      const double eff = waves / std::ceil(waves);
+      if (eff > best + 0.03) {   // a larger split must buy a clearly fuller last wave
+        best = eff;
+        bv = v;
+      }
+    }
+    g.bp_vgo = bv;
+  }
   p->gcap = 0;
   for (int li = 0; li <= r; ++li) {
     LevelGeom &g = dp.lg[li];
     g.bp_nv = (desc->n_angles + g.bp_vgo - 1) / g.bp_vgo;
-    p->gcap = std::max(p->gcap, (size_t)g.bp_vgo * g.nl * g.nl);
+    p->gcap = std::max(p->gcap, (size_t)2 * g.bp_vgo * g.nl * g.nl);
   }
-  if (bp_smem_bytes(dp) > 200 * 1024) {
+  if (bp_smem_bytes(dp) > 160 * 1024) {
     imask_plan_destroy(p);
     return fail(IMASK_ERR_SHAPE, "too many views per back-projector CTA for shared memory");
   }
-  dp.upd_tile = update_tile(desc->n, r);
-  p->n_cta_x = (m_x + FP_CHUNK - 1) / FP_CHUNK;
-  p->n_cta_y = (dp.m - m_x + FP_CHUNK - 1) / FP_CHUNK;
 
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_rays, rays.size() * sizeof(float4))) != cudaSuccess ||

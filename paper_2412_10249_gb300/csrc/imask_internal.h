@@ -15,10 +15,12 @@
 #define FP_CHUNK (FP_THREADS * FP_RAYS)
 #define FP_STAGES 3            // TMA strip pipeline depth
 #define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
-#define BP_THREADS 256         // back-projector: threads per CTA (one per tile pixel)
-#define BP_TILE 16             // back-projector tile side, every level
-#define BP_SLOTS 256           // back-projector: ray slots per staged chunk (x + y)
-#define LBLOCK 16              // lines per local interpolation frame (see block_origin)
+#define BP_THREADS 256         // back-projector: threads per CTA
+#define BP_W 16                // back-projector tile: lines along the major axis
+#define BP_SEG 32              // back-projector tile: lines across (one owner segment)
+#define BP_SLOTS 256           // back-projector: ray slots per staged chunk
+#define LBLOCK 16              // lines per local interpolation frame (see block_origin);
+                               // equal to BP_W so a back-projector tile is one block
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
 
 // Per-view data for the pixel-driven back-projector (32 bytes).
@@ -41,8 +43,9 @@ struct LevelGeom {
   float scale2l;   // 2^ell
   float hl;        // pixel width fov / nl
   float cmid;      // (nl - 1) / 2
-  int bp_tiles;    // back-projector tiles (BP_TILE x BP_TILE) per side
-  int bp_vgo;      // back-projector view groups across CTAs (partial sums)
+  int bp_nm;       // back-projector tiles along the major axis (BP_W lines each)
+  int bp_nc;       // back-projector tiles across it (BP_SEG lines each)
+  int bp_vgo;      // back-projector view groups per major axis (partial sums)
   int bp_nv;       // largest number of views handled by one CTA
 };
 
@@ -56,6 +59,8 @@ struct DevPlan {
   unsigned long long thr[IMASK_MAX_LEVELS];   // level thresholds (r - 1 used)
   LevelGeom lg[IMASK_MAX_LEVELS + 1];
   int upd_tile;      // fine-pixel tile side of the sketch / update kernels
+  int fp_chunk_x;    // projector: x-major rays per CTA (<= FP_CHUNK)
+  int fp_chunk_y;    // projector: y-major rays per CTA (<= FP_CHUNK)
   const float4 *rays;      // ray list: (a_hi, t_hi, g, sino index bits)
   const float2 *rays_lo;   // ray list: (a_lo, t_lo), the low words of a and t
   const ViewInfo *views;   // per view

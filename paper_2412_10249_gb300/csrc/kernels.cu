@@ -130,7 +130,8 @@ __device__ __forceinline__ void block_origin(float a_hi, float a_lo, float t_hi,
 // Forward projector (Joseph) with the fused dual epilogue.
 //
 // Rays are listed x-major first, then y-major.  CTA b < n_cta_x takes x-major
-// rays [b*FP_CHUNK, ...), the others y-major rays.  An x-major ray marches over
+// rays [b*fp_chunk_x, ...), the others y-major rays (chunks sized so that the
+// grid fills the GPU in one wave).  An x-major ray marches over
 // the columns of the x-major padded image (one line per column, rows
 // contiguous) and interpolates linearly between the rows I + floor(r + d t) and
 // the next one.  Strips of tc lines are streamed through FP_STAGES
@@ -152,8 +153,9 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
   const LevelGeom G = P.lg[ell + 1];
   const bool xaxis = (int)blockIdx.x < n_cta_x;
   const int chunk = xaxis ? (int)blockIdx.x : (int)blockIdx.x - n_cta_x;
-  const int begin = xaxis ? chunk * FP_CHUNK : P.m_x + chunk * FP_CHUNK;
-  const int end = xaxis ? min(begin + FP_CHUNK, P.m_x) : min(begin + FP_CHUNK, P.m);
+  const int csz = xaxis ? P.fp_chunk_x : P.fp_chunk_y;
+  const int begin = xaxis ? chunk * csz : P.m_x + chunk * csz;
+  const int end = xaxis ? min(begin + csz, P.m_x) : min(begin + csz, P.m);
   const float *img = xaxis ? pads.T[ell + 1] : pads.R[ell + 1];
   const int tid = threadIdx.x;
 
@@ -307,28 +309,29 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 // ---------------------------------------------------------------------------------
 // Back-projector: g = R_ell^T y on the level grid, owner-computes (no atomics).
 //
-// A CTA owns a BP_TILE x BP_TILE tile of level pixels and a contiguous range of
-// views (bp_vgo ranges across CTAs; the consumer adds the partial images in a
-// fixed order).  Thread t owns two private pixel segments of the tile: column
-// t % 16 (16 rows) for x-major rays and row t % 16 (16 columns) for y-major
-// rays, each with its own accumulators in shared memory, and it takes every
-// 16th ray of the staged ray list (t / 16 picks the residue).
+// The x-major and y-major rays go to separate CTAs.  An x-major CTA owns a tile
+// of BP_W columns x BP_SEG rows of level pixels and a contiguous range of views
+// (bp_vgo ranges across CTAs; the consumer adds the partial images, 2 bp_vgo of
+// them, in a fixed order).  Thread t owns the column t % BP_W of the tile, a
+// segment of BP_SEG rows with private accumulators in shared memory, and takes
+// every (BP_THREADS / BP_W)-th staged ray.  y-major CTAs do the same with rows
+// and columns exchanged.
 //   prologue  each view of the range gets its ray window: the bins of the
 //             corners of the tile box widened by one pixel across the major
 //             axis (the bin map is affine for parallel beam and
 //             linear-fractional for fan beam, so its extremes over the box
 //             are at corners); window lengths are prefix-summed into one flat
-//             x-major and one flat y-major ray list;
-//   pipeline  the lists are processed in chunks; while chunk k is scattered,
+//             ray list;
+//   pipeline  the list is processed in chunks; while chunk k is scattered,
 //             the raw data of chunk k+1 (parameters, low words, y) stream into
 //             the other buffer by cp.async; after a barrier they are converted
 //             in place to (r, t, g y, I') in the local frame of the tile's line
 //             block (block_origin, as in k_fp);
 //   scatter   a thread applies a ray to its segment exactly as k_fp samples
 //             it: q = r + d t, row I + floor(q) gets (1 - f) g y and the next
-//             row f g y, f = q - floor(q); rows outside the tile land in guard
-//             slots.  Only the owner ever touches a slot.
-//   epilogue  every pixel sums its 16 x-major and 16 y-major partial slots.
+//             row f g y, f = q - floor(q); rows outside the segment land in
+//             guard slots.  Only the owner ever touches a slot.
+//   epilogue  every pixel sums its BP_THREADS / BP_W owners' slots.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float bin_of(const DevPlan &P, float c, float s, float x, float y) {
   if (P.geometry == 0) return fmaf(fmaf(x, c, y * s), P.inv_pitch, P.center);
@@ -367,10 +370,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-#define BP_HALF (BP_SLOTS / 2)   // x-major and y-major entries per chunk
-#define BP_ACC (BP_TILE + 4)     // accumulator slots per segment: 2 guards each side
+#define BP_GROUPS (BP_THREADS / BP_W)   // ray residue classes per CTA
+#define BP_ACC (BP_SEG + 4)             // accumulator slots per segment: 2 guards each side
 
-// shared-memory layout of k_bp
+// shared-memory layout of k_bp (dynamic part)
 __device__ __forceinline__ float4 *bp_win(float4 *raw, int b) { return raw + b * BP_SLOTS; }
 __device__ __forceinline__ float2 *bp_lo(float4 *raw, int b) {
   return (float2 *)(raw + 2 * BP_SLOTS) + b * BP_SLOTS;
@@ -378,7 +381,7 @@ __device__ __forceinline__ float2 *bp_lo(float4 *raw, int b) {
 __device__ __forceinline__ float *bp_y(float4 *raw, int b) {
   return (float *)((float2 *)(raw + 2 * BP_SLOTS) + 2 * BP_SLOTS) + b * BP_SLOTS;
 }
-__device__ __forceinline__ int4 *bp_vinfo(float4 *raw) { return (int4 *)bp_y(raw, 2); }
+__device__ __forceinline__ int2 *bp_vinfo(float4 *raw) { return (int2 *)bp_y(raw, 2); }
 
 // last index v in [0, n) with pref[v] <= e (pref non-decreasing, pref[0] = 0)
 __device__ __forceinline__ int find_view(const int *pref, int n, int e) {
@@ -393,173 +396,130 @@ __device__ __forceinline__ int find_view(const int *pref, int n, int e) {
   return lo;
 }
 
-// Block-wide exclusive scan of two counters, each thread holding a run of
-// `per` consecutive values (vals read from / written to a and b in place).
-__device__ void scan2(int *a, int *b, int n, int *tot_a, int *tot_b) {
-  __shared__ int wa[BP_THREADS / 32], wb[BP_THREADS / 32];
+// Block-wide exclusive scan of n counters held in a[0..n) (in place); a[n]
+// receives the total, which is also returned.
+__device__ int scan_counts(int *a, int n) {
+  __shared__ int wsum[BP_THREADS / 32];
   const int per = (n + BP_THREADS - 1) / BP_THREADS;
   const int v0 = threadIdx.x * per, v1 = min(v0 + per, n);
-  int sa = 0, sb = 0;
-  for (int v = v0; v < v1; ++v) {
-    sa += a[v];
-    sb += b[v];
-  }
+  int sa = 0;
+  for (int v = v0; v < v1; ++v) sa += a[v];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int ia = sa, ib = sb;
+  int ia = sa;
   for (int o = 1; o < 32; o <<= 1) {
-    const int ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
-    if (lane >= o) {
-      ia += ta;
-      ib += tb;
-    }
+    const int ta = __shfl_up_sync(0xffffffffu, ia, o);
+    if (lane >= o) ia += ta;
   }
-  if (lane == 31) {
-    wa[w] = ia;
-    wb[w] = ib;
-  }
+  if (lane == 31) wsum[w] = ia;
   __syncthreads();
-  int ba = 0, bb = 0, ta = 0, tb = 0;
+  int ba = 0, tot = 0;
   for (int k = 0; k < BP_THREADS / 32; ++k) {
-    if (k < w) {
-      ba += wa[k];
-      bb += wb[k];
-    }
-    ta += wa[k];
-    tb += wb[k];
+    if (k < w) ba += wsum[k];
+    tot += wsum[k];
   }
-  int ra = ba + ia - sa, rb = bb + ib - sb;   // exclusive prefix of this run
+  int ra = ba + ia - sa;   // exclusive prefix of this thread's run
   for (int v = v0; v < v1; ++v) {
-    const int ca = a[v], cb = b[v];
+    const int ca = a[v];
     a[v] = ra;
-    b[v] = rb;
     ra += ca;
-    rb += cb;
   }
-  if (threadIdx.x == 0) {
-    a[n] = ta;
-    b[n] = tb;
-  }
-  *tot_a = ta;
-  *tot_b = tb;
+  if (threadIdx.x == 0) a[n] = tot;
   __syncthreads();
+  return tot;
 }
 
 __global__ void __launch_bounds__(BP_THREADS, 3)
     k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
          unsigned int *err, int nv_cap) {
   extern __shared__ __align__(16) float4 bp_raw[];
-  // private accumulators: [slot][thread], slots 0..19 = rows -2..17 of the
-  // owner's segment; separate arrays so x- and y-major updates never alias
-  __shared__ float accx_s[BP_ACC * BP_THREADS];
-  __shared__ float accy_s[BP_ACC * BP_THREADS];
+  // private accumulators: [slot][thread]; slots 0..BP_ACC-1 are cross lines
+  // -2..BP_SEG+1 of the owner's segment
+  __shared__ float acc_s[BP_ACC * BP_THREADS];
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
-  const int nt = G.bp_tiles, vgo = G.bp_vgo;
-  const int vg = blockIdx.x / (nt * nt);
+  const int nm = G.bp_nm, nc = G.bp_nc, vgo = G.bp_vgo;
+  const int ntile = nm * nc;
+  const int role = (int)blockIdx.x >= ntile * vgo ? 1 : 0;   // 0: x-major rays, 1: y-major
+  const int bid = (int)blockIdx.x - role * ntile * vgo;
+  const int vg = bid / ntile;
   if (vg >= vgo) return;
-  const int tile = blockIdx.x % (nt * nt);
-  const int ti = tile / nt, tj = tile % nt;
+  const int tile = bid % ntile;
+  const int mb = tile % nm, cb = tile / nm;   // march block (BP_W lines), cross block (BP_SEG)
   const int tid = threadIdx.x;
   const int a0 = (int)(((long long)vg * P.n_angles) / vgo);
   const int a1 = (int)(((long long)(vg + 1) * P.n_angles) / vgo);
   const int nv = a1 - a0;
   const float hl = G.hl, W = P.fov;
-  int4 *vinfo = bp_vinfo(bp_raw);                 // li0_x, yi0_x, li0_y, yi0_y per view
-  int *prx = (int *)(vinfo + nv_cap);             // nv_cap + 1 prefix counts (x-major)
-  int *pry = prx + nv_cap + 1;                    // nv_cap + 1 prefix counts (y-major)
+  int2 *vinfo = bp_vinfo(bp_raw);   // per view: ray-list index and y index of the window start
+  int *pref = (int *)(vinfo + nv_cap);   // nv_cap + 1 prefix counts
 
-  // ---- prologue: ray windows of every view ----
+  // ---- prologue: ray windows of every view (this CTA's major axis only) ----
   {
-    const int cl = min(tj * BP_TILE + BP_TILE - 1, G.nl - 1);
-    const int rlast = min(ti * BP_TILE + BP_TILE - 1, G.nl - 1);
-    const float bx0 = -0.5f * W + ((float)(tj * BP_TILE) + 0.5f) * hl;
-    const float bx1 = -0.5f * W + ((float)cl + 0.5f) * hl;
-    const float by0 = -0.5f * W + ((float)(ti * BP_TILE) + 0.5f) * hl;
-    const float by1 = -0.5f * W + ((float)rlast + 0.5f) * hl;
+    const int m0 = mb * BP_W, m1 = min(m0 + BP_W, G.nl) - 1;      // march lines
+    const int c0 = cb * BP_SEG, c1 = min(c0 + BP_SEG, G.nl) - 1;  // cross lines
+    const float mlo = -0.5f * W + ((float)m0 + 0.5f) * hl, mhi = -0.5f * W + ((float)m1 + 0.5f) * hl;
+    const float clo = -0.5f * W + ((float)c0 + 0.5f) * hl - hl;
+    const float chi = -0.5f * W + ((float)c1 + 0.5f) * hl + hl;
     for (int v = tid; v < nv; v += BP_THREADS) {
       const ViewInfo V = P.views[a0 + v];
-      int lo[2], cnt[2];
+      float mn = 1.0e30f, mx = -1.0e30f;
 #pragma unroll
-      for (int axis = 0; axis < 2; ++axis) {
-        float mn = 1.0e30f, mx = -1.0e30f;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          float x, yy;
-          if (axis == 0) {
-            x = (k & 1) ? bx1 : bx0;
-            yy = (k & 2) ? by1 + hl : by0 - hl;
-          } else {
-            x = (k & 1) ? bx1 + hl : bx0 - hl;
-            yy = (k & 2) ? by1 : by0;
-          }
-          const float j = bin_of(P, V.c, V.s, x, yy);
-          mn = fminf(mn, j);
-          mx = fmaxf(mx, j);
-        }
-        const int j0 = axis == 0 ? V.xj0 : V.yj0, j1 = axis == 0 ? V.xj1 : V.yj1;
-        lo[axis] = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
-        const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
-        cnt[axis] = max(hi - lo[axis] + 1, 0);
+      for (int k = 0; k < 4; ++k) {
+        const float mcoord = (k & 1) ? mhi : mlo, ccoord = (k & 2) ? chi : clo;
+        const float j = role == 0 ? bin_of(P, V.c, V.s, mcoord, ccoord)
+                                  : bin_of(P, V.c, V.s, ccoord, mcoord);
+        mn = fminf(mn, j);
+        mx = fmaxf(mx, j);
       }
-      const int yrow = (a0 + v) * P.n_det;
-      vinfo[v] = make_int4(V.xoff - V.xj0 + lo[0], yrow + lo[0], V.yoff - V.yj0 + lo[1],
-                           yrow + lo[1]);
-      prx[v] = cnt[0];
-      pry[v] = cnt[1];
+      const int j0 = role == 0 ? V.xj0 : V.yj0, j1 = role == 0 ? V.xj1 : V.yj1;
+      const int lo = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
+      const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
+      const int base = role == 0 ? V.xoff - V.xj0 : V.yoff - V.yj0;
+      vinfo[v] = make_int2(base + lo, (a0 + v) * P.n_det + lo);
+      pref[v] = max(hi - lo + 1, 0);
     }
-    for (int k = tid; k < BP_ACC * BP_THREADS; k += BP_THREADS) {
-      accx_s[k] = 0.0f;
-      accy_s[k] = 0.0f;
-    }
+    for (int k = tid; k < BP_ACC * BP_THREADS; k += BP_THREADS) acc_s[k] = 0.0f;
   }
   __syncthreads();
-  int NX, NY;
-  scan2(prx, pry, nv, &NX, &NY);
+  const int NR = scan_counts(pref, nv);
 
-  const int g = tid >> 4;                        // ray residue class of this thread
-  const float dseg = (float)(tid & (BP_TILE - 1));   // own line inside the block
-  const float ccx = (float)(tj * BP_TILE) - G.cmid;  // line-block origins
-  const float ccy = (float)(ti * BP_TILE) - G.cmid;
-  float *accx = accx_s + tid;                    // column segment (x-major rays)
-  float *accy = accy_s + tid;                    // row segment (y-major rays)
-  const int nch = max((NX + BP_HALF - 1) / BP_HALF, (NY + BP_HALF - 1) / BP_HALF);
+  const int g = tid / BP_W;                          // ray residue class of this thread
+  const float dseg = (float)(tid % BP_W);            // own march line inside the block
+  const float cco = (float)(mb * BP_W) - G.cmid;     // line-block origin (march coordinate)
+  const int cross0 = cb * BP_SEG;                    // first cross line of the segment
+  float *acc = acc_s + tid;
+  const int nch = (NR + BP_SLOTS - 1) / BP_SLOTS;
 
-  // raw data of chunk k into buffer b: slots [0, BP_HALF) x-major, the rest y-major
+  // raw data of chunk k into buffer b
   auto stage = [&](int k, int b) {
     float4 *win = bp_win(bp_raw, b);
     float2 *lo = bp_lo(bp_raw, b);
     float *yv = bp_y(bp_raw, b);
     for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
-      const bool xs = sl < BP_HALF;
-      const int e = k * BP_HALF + (xs ? sl : sl - BP_HALF);
-      if (e >= (xs ? NX : NY)) continue;
-      const int v = find_view(xs ? prx : pry, nv, e);
-      const int kk = e - (xs ? prx[v] : pry[v]);
-      const int4 vi = vinfo[v];
-      const int li = (xs ? vi.x : vi.z) + kk;
-      const int yi = (xs ? vi.y : vi.w) + kk;
-      cp_async(win + sl, P.rays + li, 16);
-      cp_async(lo + sl, P.rays_lo + li, 8);
-      cp_async(yv + sl, y + yi, 4);
+      const int e = k * BP_SLOTS + sl;
+      if (e >= NR) break;
+      const int v = find_view(pref, nv, e);
+      const int kk = e - pref[v];
+      const int2 vi = vinfo[v];
+      cp_async(win + sl, P.rays + vi.x + kk, 16);
+      cp_async(lo + sl, P.rays_lo + vi.x + kk, 8);
+      cp_async(yv + sl, y + vi.y + kk, 4);
     }
     cp_async_commit();
   };
-  // in-place conversion to (r, t, g y, I - first line of the segment + 2)
+  // in-place conversion to (r, t, g y, I - cross0 + 2)
   auto convert = [&](int k, int b) {
     float4 *win = bp_win(bp_raw, b);
     const float2 *lo = bp_lo(bp_raw, b);
     const float *yv = bp_y(bp_raw, b);
     for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
-      const bool xs = sl < BP_HALF;
-      const int e = k * BP_HALF + (xs ? sl : sl - BP_HALF);
-      if (e >= (xs ? NX : NY)) continue;
+      if (k * BP_SLOTS + sl >= NR) break;
       const float4 p = win[sl];
       const float2 pl = lo[sl];
       int I;
       float r;
-      block_origin(p.x, pl.x, p.y, pl.y, G.inv2l, xs ? ccx : ccy, I, r);
-      const int base = xs ? ti * BP_TILE : tj * BP_TILE;   // first cross line of the tile
-      win[sl] = make_float4(r, p.y, p.z * yv[sl], __int_as_float(I - base + 2));
+      block_origin(p.x, pl.x, p.y, pl.y, G.inv2l, cco, I, r);
+      win[sl] = make_float4(r, p.y, p.z * yv[sl], __int_as_float(I - cross0 + 2));
     }
   };
 
@@ -574,43 +534,19 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
     const int b = k & 1;
     if (k + 1 < nch) stage(k + 1, b ^ 1);
     const float4 *win = bp_win(bp_raw, b);
-    const int nx = min(BP_HALF, NX - k * BP_HALF), ny = min(BP_HALF, NY - k * BP_HALF);
-    const int nmax = max(nx, ny);
-    constexpr int STEP = BP_THREADS / BP_TILE;
-    // x- and y-major rays interleaved (independent accumulator arrays), the
-    // next pair of entries loaded while the current one is applied
-    // indices clamped into the buffer: loads beyond a list are harmless and unused
-    const int xlast = max(nx - 1, 0), ylast = max(ny - 1, 0);
-    float4 ex = win[min(g, xlast)];
-    float4 ey = win[BP_HALF + min(g, ylast)];
-    for (int sl = g; sl < nmax; sl += STEP) {
-      const int sn = sl + STEP;
-      const float4 exn = win[min(sn, xlast)];
-      const float4 eyn = win[BP_HALF + min(sn, ylast)];
-      if (sl < nx) {
-        const float q = fmaf(dseg, ex.y, ex.x);
-        const float tq = __fadd_rd(q, kMagic);
-        const int slot =
-            min(max(__float_as_int(tq) - kMagicBits + __float_as_int(ex.w), 0), BP_ACC - 2);
-        const float f = q - (tq - kMagic);
-        const float w1 = f * ex.z;
-        float *pa = accx + slot * BP_THREADS;
-        pa[0] += ex.z - w1;
-        pa[BP_THREADS] += w1;
-      }
-      if (sl < ny) {
-        const float q = fmaf(dseg, ey.y, ey.x);
-        const float tq = __fadd_rd(q, kMagic);
-        const int slot =
-            min(max(__float_as_int(tq) - kMagicBits + __float_as_int(ey.w), 0), BP_ACC - 2);
-        const float f = q - (tq - kMagic);
-        const float w1 = f * ey.z;
-        float *pa = accy + slot * BP_THREADS;
-        pa[0] += ey.z - w1;
-        pa[BP_THREADS] += w1;
-      }
-      ex = exn;
-      ey = eyn;
+    const int n = min(BP_SLOTS, NR - k * BP_SLOTS);
+#pragma unroll 2
+    for (int sl = g; sl < n; sl += BP_GROUPS) {
+      const float4 e = win[sl];
+      const float q = fmaf(dseg, e.y, e.x);
+      const float tq = __fadd_rd(q, kMagic);
+      const int slot =
+          min(max(__float_as_int(tq) - kMagicBits + __float_as_int(e.w), 0), BP_ACC - 2);
+      const float f = q - (tq - kMagic);
+      const float w1 = f * e.z;
+      float *pa = acc + slot * BP_THREADS;
+      pa[0] += e.z - w1;
+      pa[BP_THREADS] += w1;
     }
     cp_async_wait_all();
     __syncthreads();
@@ -619,22 +555,22 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
       __syncthreads();
     }
   }
-  // ---- epilogue: pixel (i, c) of the tile sums its owners' slots ----
-  const int il = tid / BP_TILE, cl2 = tid % BP_TILE;
-  const int i = ti * BP_TILE + il, c = tj * BP_TILE + cl2;
-  if (i < G.nl && c < G.nl) {
-    float sx = 0.0f, sy = 0.0f;
+  // ---- epilogue: every pixel of the tile sums its owners' slots ----
+  float *plane = gout + (size_t)(role * vgo + vg) * G.nl * G.nl;
+  for (int p = tid; p < BP_W * BP_SEG; p += BP_THREADS) {
+    const int ml = p % BP_W, cl = p / BP_W;          // march, cross offsets
+    const int mline = mb * BP_W + ml, cline = cross0 + cl;
+    if (mline >= G.nl || cline >= G.nl) continue;
+    float sum = 0.0f;
 #pragma unroll
-    for (int gg = 0; gg < BP_THREADS / BP_TILE; ++gg) {
-      sx += accx_s[(il + 2) * BP_THREADS + cl2 + BP_TILE * gg];
-      sy += accy_s[(cl2 + 2) * BP_THREADS + il + BP_TILE * gg];
-    }
-    gout[(size_t)vg * G.nl * G.nl + (size_t)i * G.nl + c] = (sx + sy) * G.scale2l;
+    for (int gg = 0; gg < BP_GROUPS; ++gg) sum += acc_s[(cl + 2) * BP_THREADS + ml + BP_W * gg];
+    const int i = role == 0 ? cline : mline, c = role == 0 ? mline : cline;
+    plane[(size_t)i * G.nl + c] = sum * G.scale2l;
   }
 }
 
-// The back-projector leaves bp_vgo partial images (one per view group), each
-// of side nl; their sum in a fixed order is R_ell^T y.
+// The back-projector leaves 2 bp_vgo partial images (x- and y-major rays, one
+// per view group), each of side nl; their sum in a fixed order is R_ell^T y.
 __device__ __forceinline__ float g_sum(const float *g, int vgo, size_t plane, size_t idx) {
   float s = g[idx];
   for (int v = 1; v < vgo; ++v) s += g[(size_t)v * plane + idx];
@@ -745,7 +681,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
   if (ell < 0) {
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
       const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
-      img[gp] = g_sum(g, G.bp_vgo, plane, gp);
+      img[gp] = g_sum(g, 2 * G.bp_vgo, plane, gp);
     }
     return;
   }
@@ -754,12 +690,12 @@ __global__ void __launch_bounds__(UPD_THREADS)
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
       const int fi = ti0 + p / ts, fj = tj0 + p % ts;
       img[(size_t)fi * n + fj] =
-          g_sum(g, G.bp_vgo, plane, (size_t)(fi >> ell) * G.nl + (fj >> ell)) * s;
+          g_sum(g, 2 * G.bp_vgo, plane, (size_t)(fi >> ell) * G.nl + (fj >> ell)) * s;
     }
     return;
   }
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-    xs[p] = g_sum(g, G.bp_vgo, plane, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
+    xs[p] = g_sum(g, 2 * G.bp_vgo, plane, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
   __syncthreads();
   if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
@@ -790,13 +726,13 @@ __global__ void __launch_bounds__(UPD_THREADS)
     const float inv4l = G.inv2l * G.inv2l;
     for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
       const size_t gi = (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
-      const float cnew = g_sum(A.g, G.bp_vgo, (size_t)G.nl * G.nl, gi) * inv4l;
+      const float cnew = g_sum(A.g, 2 * G.bp_vgo, (size_t)G.nl * G.nl, gi) * inv4l;
       dc[p] = cnew - phic[gi];
       phic[gi] = cnew;
     }
     __syncthreads();
   } else {
-    const int vgo0 = P.lg[1].bp_vgo;
+    const int vgo0 = 2 * P.lg[1].bp_vgo;
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
       aux[p] = g_sum(A.g, vgo0, (size_t)n * n, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
     __syncthreads();
@@ -1035,15 +971,15 @@ static int bp_nv_cap(const DevPlan &P) {
 }
 
 long long bp_smem_bytes(const DevPlan &P) {   // dynamic part only
-  return 2LL * BP_SLOTS * (16 + 8 + 4) + (long long)bp_nv_cap(P) * 16 +
-         2LL * (bp_nv_cap(P) + 1) * 4;
+  return 2LL * BP_SLOTS * (16 + 8 + 4) + (long long)bp_nv_cap(P) * 8 +
+         (long long)(bp_nv_cap(P) + 1) * 4;
 }
 
 cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
                       unsigned int *err, cudaStream_t st) {
   // the grid covers the level with the most (tile, view group) pairs; extra
   // CTAs return at once
-  auto ctas = [&](int li) { return P.lg[li].bp_tiles * P.lg[li].bp_tiles * P.lg[li].bp_vgo; };
+  auto ctas = [&](int li) { return 2 * P.lg[li].bp_nm * P.lg[li].bp_nc * P.lg[li].bp_vgo; };
   int most = 0;
   for (int li = 0; li <= P.levels; ++li) most = max(most, ctas(li));
   if (sel.fixed >= -1) most = ctas(sel.fixed + 1);
