@@ -716,22 +716,28 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
     p->n_cta_x = cx > 0 ? (m_x + dp.fp_chunk_x - 1) / dp.fp_chunk_x : 0;
     p->n_cta_y = cy > 0 ? (m_y + dp.fp_chunk_y - 1) / dp.fp_chunk_y : 0;
   }
-  for (int li = 0; li <= r; ++li) {
-    LevelGeom &g = dp.lg[li];
-    const double slots = 3.0 * n_sm;
-    const int tiles = 2 * g.bp_nm * g.bp_nc;   // x- and y-major CTAs per view group
-    const int vmax = std::max(1, std::min(desc->n_angles, (int)std::ceil(4.0 * slots / tiles)));
-    double best = -1.0;
-    int bv = 1;
-    for (int v = 1; v <= vmax; ++v) {
-      const double waves = tiles * (double)v / slots;
-      const double eff = waves / std::ceil(waves);
-      if (eff > best + 0.03) {   // a larger split must buy a clearly fuller last wave
-        best = eff;
-        bv = v;
+  {
+    // resident back-projector CTAs per SM, for the largest per-CTA view range
+    for (int li = 0; li <= r; ++li) dp.lg[li].bp_nv = desc->n_angles;
+    const int occ = bp_blocks_per_sm(bp_smem_bytes(dp));
+    const double slots = (double)occ * n_sm;
+    for (int li = 0; li <= r; ++li) {
+      LevelGeom &g = dp.lg[li];
+      const int tiles = 2 * g.bp_nm * g.bp_nc;   // x- and y-major CTAs per view group
+      const int vmax = std::max(1, std::min(desc->n_angles, (int)std::ceil(8.0 * slots / tiles)));
+      // at least two waves where the views allow it, then the fullest last wave
+      double best = -1.0;
+      int bv = 1;
+      for (int v = 1; v <= vmax; ++v) {
+        const double waves = tiles * (double)v / slots;
+        const double eff = (waves / std::ceil(waves)) * std::min(1.0, waves / 2.0);
+        if (eff > best + 0.03) {   // a larger split must buy a clearly better fill
+          best = eff;
+          bv = v;
+        }
       }
+      g.bp_vgo = bv;
     }
-    g.bp_vgo = bv;
   }
   p->gcap = 0;
   for (int li = 0; li <= r; ++li) {

@@ -117,6 +117,7 @@ cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, 
 cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
                       unsigned int *err, cudaStream_t st);
 long long bp_smem_bytes(const DevPlan &P);
+int bp_blocks_per_sm(long long dyn_smem);
 cudaError_t launch_adjsketch(const DevPlan &P, int ell, const float *g, float *img,
                              cudaStream_t st);
 cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int write_sketch,

@@ -577,6 +577,39 @@ __device__ __forceinline__ float g_sum(const float *g, int vgo, size_t plane, si
   return s;
 }
 
+// Sum of the back-projector's npl partial planes for the cs x cs coarse pixels
+// starting at (I0, J0) of a level grid of side nl, into out[cs * cs]: K lanes
+// per pixel add planes k, k+K, ..., then the lanes are added in a fixed order.
+// Ends with a barrier.
+__device__ void coarse_planes_sum(const float *g, int npl, int nl, int I0, int J0, int cs,
+                                  float *out) {
+  __shared__ float red[UPD_THREADS];
+  const int ncp = cs * cs;
+  const int K = max(1, min(UPD_THREADS / ncp, npl));   // K = 1 when ncp >= UPD_THREADS
+  const size_t plane = (size_t)nl * nl;
+  if (K > 1) {
+    for (int u = threadIdx.x; u < ncp * K; u += blockDim.x) {
+      const int p = u % ncp, k = u / ncp;
+      const size_t gi = (size_t)(I0 + p / cs) * nl + J0 + p % cs;
+      float sum = 0.0f;
+      for (int v = k; v < npl; v += K) sum += g[(size_t)v * plane + gi];
+      red[u] = sum;
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < ncp; p += blockDim.x) {
+    float sum = 0.0f;
+    if (K > 1) {
+      for (int k = 0; k < K; ++k) sum += red[k * ncp + p];
+    } else {
+      const size_t gi = (size_t)(I0 + p / cs) * nl + J0 + p % cs;
+      for (int v = 0; v < npl; ++v) sum += g[(size_t)v * plane + gi];
+    }
+    out[p] = sum;
+  }
+  __syncthreads();
+}
+
 // Block means of the tile `src` (side ts) at levels 1..r-1, level l at
 // pyr + pyr_off(l), side ts >> l.  Hierarchical 2x2 means.
 __device__ void tile_pyramid(const float *src, float *pyr, int ts, int r) {
@@ -687,10 +720,11 @@ __global__ void __launch_bounds__(UPD_THREADS)
   }
   if (ell >= 1) {
     const float s = G.inv2l * G.inv2l;
+    const int cs = ts >> ell;
+    coarse_planes_sum(g, 2 * G.bp_vgo, G.nl, ti0 >> ell, tj0 >> ell, cs, xs);
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
-      const int fi = ti0 + p / ts, fj = tj0 + p % ts;
-      img[(size_t)fi * n + fj] =
-          g_sum(g, 2 * G.bp_vgo, plane, (size_t)(fi >> ell) * G.nl + (fj >> ell)) * s;
+      const int li = p / ts, lj = p % ts;
+      img[(size_t)(ti0 + li) * n + tj0 + lj] = xs[(li >> ell) * cs + (lj >> ell)] * s;
     }
     return;
   }
@@ -724,9 +758,10 @@ __global__ void __launch_bounds__(UPD_THREADS)
     const int I0 = ti0 >> ell, J0 = tj0 >> ell;
     float *phic = A.phic + A.phic_off[ell];
     const float inv4l = G.inv2l * G.inv2l;
+    coarse_planes_sum(A.g, 2 * G.bp_vgo, G.nl, I0, J0, cs, dc);
     for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
       const size_t gi = (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
-      const float cnew = g_sum(A.g, 2 * G.bp_vgo, (size_t)G.nl * G.nl, gi) * inv4l;
+      const float cnew = dc[p] * inv4l;
       dc[p] = cnew - phic[gi];
       phic[gi] = cnew;
     }
@@ -968,6 +1003,17 @@ static int bp_nv_cap(const DevPlan &P) {
   int nv = 0;
   for (int li = 0; li <= P.levels; ++li) nv = max(nv, P.lg[li].bp_nv);
   return nv;
+}
+
+// Resident back-projector CTAs per SM for a given dynamic shared-memory size.
+int bp_blocks_per_sm(long long dyn_smem) {
+  if (set_smem((const void *)k_bp, (int)dyn_smem) != cudaSuccess) return 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bp, BP_THREADS, (size_t)dyn_smem) !=
+          cudaSuccess ||
+      n < 1)
+    return 1;
+  return n;
 }
 
 long long bp_smem_bytes(const DevPlan &P) {   // dynamic part only
