@@ -204,6 +204,72 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------------
+# roofline
+# ---------------------------------------------------------------------------------
+KINDS = ["forward projector (k_fp)", "back-projector (k_bp)", "primal update (k_update)"]
+KNAMES = ["k_fp", "k_bp", "k_update"]
+# algorithmic work per (ray, line) sample: FP32 flops and shared-memory bytes
+FLOPS_PER_SAMPLE = {0: 6.0, 1: 7.0}          # q FMA 2, f 1, lerp 3 | q 2, f 1, weights 2, adds 2
+SMEM_BYTES_PER_SAMPLE = {0: 8.0, 1: 17.0}    # two pixel loads | two accumulator RMWs + 1/16 entry
+N_SM, MAX_CLK = 152, 2.07e9
+SMEM_PEAK_GBS = N_SM * 128 * MAX_CLK / 1e9    # 128 B per clock per SM
+
+
+def _kernels_sha() -> str:
+    import hashlib
+    path = os.path.join(ROOT, "paper_2412_10249_gb300", "csrc", "kernels.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _dram_traffic(kname: str, level: int):
+    """DRAM bytes per launch from the committed ncu summary, if it still
+    describes the current kernel source (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_counters.json")) as f:
+            c = json.load(f)
+        if c.get("kernels_cu_sha256_prefix") != _kernels_sha():
+            return None
+        return c[kname][str(level)]["dram_bytes_per_launch"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops):
+    """Dominant (kernel, level) by total event time; its average launch against
+    the FP32 CUDA-core peak (bound "alu": the projectors are limited by issue
+    slots and the shared-memory pipe, not by DRAM), plus the shared-memory
+    bandwidth view of the same launches."""
+    best = int(np.argmax(prof_ms))
+    kind, lvl = best // 8, best % 8
+    cnt = max(1, prof_cnt[best])
+    avg_s = prof_ms[best] / cnt / 1e3
+    nl = p.n >> lvl
+    samples_launch = p.m * nl
+    rep = {"kernel": f"{KINDS[kind]} at level {lvl} ({nl}x{nl} grid)", "bound": "alu",
+           "unit": "TFLOP/s", "peak": alu_peak_tflops,
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+           "avg_launch_us": avg_s * 1e6, "launches": int(prof_cnt[best]),
+           "gsamples_per_s": samples_launch / avg_s / 1e9}
+    if kind in FLOPS_PER_SAMPLE:
+        ach = samples_launch * FLOPS_PER_SAMPLE[kind] / avg_s / 1e12
+        smem = samples_launch * SMEM_BYTES_PER_SAMPLE[kind] / avg_s / 1e9
+        rep.update(achieved=ach, frac=ach / alu_peak_tflops,
+                   traffic=_dram_traffic(KNAMES[kind], lvl),
+                   algorithmic={"samples_per_launch": samples_launch,
+                                "flops_per_sample": FLOPS_PER_SAMPLE[kind],
+                                "smem_bytes_per_sample": SMEM_BYTES_PER_SAMPLE[kind]},
+                   smem={"achieved_gbs": smem, "peak_gbs": SMEM_PEAK_GBS,
+                         "frac": smem / SMEM_PEAK_GBS})
+    else:
+        rep.update(achieved=None, frac=None, traffic=None)
+    total = max(1e-12, float(sum(prof_ms)))
+    rep["time_share"] = {f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / total, 4)
+                         for k in range(24) if prof_cnt[k] > 0}
+    return rep
+
+
+# ---------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------
 def run_ours(args):
@@ -221,8 +287,10 @@ def run_ours(args):
     _, b, _ = inputs.measurements(p, seed=rank)
     bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
     # mu and sigma: derived by the plan (power method + Thm. 3) unless given
+    n_launch_start = imask.imask_launch_count()
     plan = imask.Plan(dict(p.params(), mu=max(args.mu, 0.0), sigma=max(args.sigma, 0.0)))
     info = plan.info
+    n_launch_plan = imask.imask_launch_count() - n_launch_start
     stream = torch.cuda.Stream()
     x = torch.empty(p.d, device="cuda", dtype=torch.float32)
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
@@ -292,26 +360,7 @@ def run_ours(args):
     e2e_value = total_solves / T_e2e
 
     # ---- roofline of the dominant kernel (kind, level) ----
-    kinds = ["forward projector (k_fp)", "back-projector (k_bp)", "primal update (k_update)"]
-    best = int(np.argmax(prof_ms))
-    kind, lvl = best // 8, best % 8
-    cnt = max(1, prof_cnt[best])
-    avg_s = prof_ms[best] / cnt / 1e3
-    nl = p.n >> lvl
-    samples_launch = p.m * nl
-    flops_per_sample = 7.0 if kind == 0 else 14.0   # see the design notes
-    peak_tf = args.alu_peak_tflops
-    achieved_tf = samples_launch * flops_per_sample / avg_s / 1e12
-    share = {f"{kinds[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / max(1e-9, sum(prof_ms)), 4)
-             for k in range(24) if prof_cnt[k] > 0}
-    roofline = {
-        "kernel": f"{kinds[kind]} at level {lvl} ({nl}x{nl} grid)",
-        "bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-        "frac": achieved_tf / peak_tf, "traffic": None,
-        "gsamples_per_s": samples_launch / avg_s / 1e9,
-        "avg_launch_us": avg_s * 1e6, "launches": int(prof_cnt[best]),
-        "time_share": share,
-    }
+    roofline = roofline_report(p, prof_ms, prof_cnt, args.alu_peak_tflops)
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
@@ -344,6 +393,8 @@ def run_ours(args):
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 4 * p.m,
                     "d2h_bytes_per_step": 4 * p.d},
             "gpu_launches": int(launches),
+            "launches_before_timed": int(launches0),
+            "launches_plan": int(n_launch_plan),
             "clocks": clk,
             "roofline": roofline,
             "cpu_baseline": cpu,
