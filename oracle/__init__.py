@@ -59,6 +59,11 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(_D)
 
 
+class OrcVariant(ctypes.Structure):
+    _fields_ = [("sequential", ctypes.c_int32), ("theta", ctypes.c_double),
+                ("snapshots", ctypes.c_int32), ("independent", ctypes.c_int32)]
+
+
 class Oracle:
     """numpy front end of the C oracle for one problem description.
 
@@ -98,6 +103,15 @@ class Oracle:
                 "orc_imask_run": (ctypes.c_int32, [ctypes.c_void_p, _D, ctypes.c_uint64,
                                                    ctypes.c_int64, ctypes.c_int32, _D, _D, _D,
                                                    _D, _I32]),
+                "orc_imask_seq_run": (ctypes.c_int32, [ctypes.c_void_p, _D, ctypes.c_uint64,
+                                                       ctypes.c_int64, ctypes.c_int32,
+                                                       ctypes.c_double, _D, _D, _D, _D, _D,
+                                                       _I32]),
+                "orc_primal_seed": (ctypes.c_uint64, [ctypes.c_uint64]),
+                "orc_imask_variant_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, _D,
+                                                           ctypes.c_uint64, ctypes.c_int64,
+                                                           ctypes.c_int32] + [_D] * 7
+                                          + [_I32, _I32]),
                 "orc_power_eig": (ctypes.c_double, [ctypes.c_void_p, _D, ctypes.c_int32,
                                                     ctypes.c_int32, ctypes.c_int32]),
                 "orc_constants_dense": (None, [_D, ctypes.c_int32, _D, ctypes.c_int32,
@@ -292,6 +306,63 @@ class Oracle:
             raise ValueError("oracle: sigma and mu must be positive")
         state["k"] += iters
         return state, lv[:iters]
+
+    def run_seq(self, b: np.ndarray, seed: int, iters: int, theta: float = 1.0, state=None):
+        """Alg. 7 (ImaSk-Seq) for ``iters`` iterations; the state gains ``xbar``."""
+        if state is None:
+            state = self.new_state()
+        state.setdefault("xbar", np.zeros(self.n * self.n))
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        lv = np.zeros(max(1, iters), dtype=np.int32)
+        rc = self.L.orc_imask_seq_run(self.ref, _dp(b), seed, state["k"], iters, theta,
+                                      _dp(state["x"]), _dp(state["xbar"]), _dp(state["y"]),
+                                      _dp(state["phi"]), _dp(state["psi"]),
+                                      lv.ctypes.data_as(_I32))
+        if rc != 0:
+            raise ValueError("oracle: sigma and mu must be positive")
+        state["k"] += iters
+        return state, lv[:iters]
+
+    def primal_seed(self, seed: int) -> int:
+        return int(self.L.orc_primal_seed(seed))
+
+    def new_variant_state(self, snapshots: bool):
+        n, m, r = self.n, self.m, self.r
+        d = n * n
+        st = {"x": np.zeros(d), "xbar": np.zeros(d), "y": np.zeros(m),
+              "phi": np.zeros(r * d), "k": 0}
+        if snapshots:
+            st["snap"] = np.zeros(r * d)
+            st["psi_mean"] = np.zeros(m)
+        else:
+            st["psi"] = np.zeros(r * m)
+        return st
+
+    def run_variant(self, b: np.ndarray, seed: int, iters: int, sequential=False, theta=1.0,
+                    snapshots=False, independent=False, state=None):
+        """Alg. 1 / Alg. 7 with the snapshot tables and independent-draw options.
+
+        Returns (state, dual levels, primal levels)."""
+        if state is None:
+            state = self.new_variant_state(snapshots)
+        var = OrcVariant(int(bool(sequential)), float(theta), int(bool(snapshots)),
+                         int(bool(independent)))
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        ld = np.zeros(max(1, iters), dtype=np.int32)
+        lp = np.zeros(max(1, iters), dtype=np.int32)
+        null = ctypes.cast(None, _D)
+
+        def opt(key):
+            return _dp(state[key]) if key in state else null
+
+        rc = self.L.orc_imask_variant_run(
+            self.ref, ctypes.byref(var), _dp(b), seed, state["k"], iters, _dp(state["x"]),
+            opt("xbar"), _dp(state["y"]), _dp(state["phi"]), opt("psi"), opt("snap"),
+            opt("psi_mean"), ld.ctypes.data_as(_I32), lp.ctypes.data_as(_I32))
+        if rc != 0:
+            raise ValueError(f"oracle: variant run failed ({rc})")
+        state["k"] += iters
+        return state, ld[:iters], lp[:iters]
 
     # -- step-size theory -----------------------------------------------------------
     def power_eig(self, w, cross: bool, transposed: bool, iters: int) -> float:

@@ -476,6 +476,156 @@ int32_t orc_imask_run(const orc_desc *d, const double *b, uint64_t seed, int64_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* Alg. 7 (ImaSk-Seq): the dual step first, on the extrapolated iterate; the  */
+/* primal step with the new dual iterate; then the extrapolation.             */
+/* ------------------------------------------------------------------------ */
+
+int32_t orc_imask_seq_run(const orc_desc *d, const double *b, uint64_t seed, int64_t k0,
+                          int32_t iters, double theta, double *x, double *xbar, double *y,
+                          double *phi, double *psi, int32_t *levels_out) {
+  const int32_t r = n_levels(d);
+  const int64_t np = n_pix(d), m = n_meas(d);
+  const double sigma = d->sigma, mu = d->mu;
+  if (!(sigma > 0.0) || !(mu > 0.0)) return 1;
+  double *phi_new = dalloc(np), *psi_new = dalloc(m);
+  double *xi = dalloc(np), *zeta = dalloc(m), *v = dalloc(np), *xn = dalloc(np);
+  for (int32_t it = 0; it < iters; ++it) {
+    const uint64_t k = (uint64_t)(k0 + it);
+    /* sample i_k */
+    const int32_t l = orc_level(d, seed, k);
+    if (levels_out) levels_out[it] = l;
+    /* psi_l refreshed with K_l xbar^k */
+    orc_apply_K(d, l, xbar, psi_new);
+    /* zeta = psi_new - psi_l + sum_i p_i psi_i (tables before the update) */
+    for (int64_t q = 0; q < m; ++q) {
+      double s = 0.0;
+      for (int32_t i = 0; i < r; ++i) s += prob(d, i) * psi[(int64_t)i * m + q];
+      zeta[q] = psi_new[q] - psi[(int64_t)l * m + q] + s;
+    }
+    /* dual update y^{k+1} = (y^k + sigma zeta - sigma b) / (1 + sigma) */
+    for (int64_t q = 0; q < m; ++q) y[q] = (y[q] + sigma * zeta[q] - sigma * b[q]) / (1.0 + sigma);
+    /* phi_l refreshed with K_l^T y^{k+1}, the new dual iterate */
+    orc_apply_KT(d, l, y, phi_new);
+    /* xi = phi_new - phi_l + sum_i p_i phi_i */
+    for (int64_t p = 0; p < np; ++p) {
+      double s = 0.0;
+      for (int32_t i = 0; i < r; ++i) s += prob(d, i) * phi[(int64_t)i * np + p];
+      xi[p] = phi_new[p] - phi[(int64_t)l * np + p] + s;
+    }
+    /* x^{k+1} = prox_{sigma/mu R}(x^k - sigma/mu xi) */
+    for (int64_t p = 0; p < np; ++p) v[p] = x[p] - (sigma / mu) * xi[p];
+    orc_prox(d, sigma / mu, v, xn);
+    /* extrapolation xbar^{k+1} = x^{k+1} + theta (x^{k+1} - x^k) */
+    for (int64_t p = 0; p < np; ++p) {
+      xbar[p] = xn[p] + theta * (xn[p] - x[p]);
+      x[p] = xn[p];
+    }
+    memcpy(phi + (int64_t)l * np, phi_new, sizeof(double) * (size_t)np);
+    memcpy(psi + (int64_t)l * m, psi_new, sizeof(double) * (size_t)m);
+  }
+  free(phi_new);
+  free(psi_new);
+  free(xi);
+  free(zeta);
+  free(v);
+  free(xn);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Variants of Alg. 1 / Alg. 7 on one loop:                                   */
+/*  - sequential: Alg. 7's order and extrapolation (else Alg. 1's);           */
+/*  - snapshots: the measurement-side tables are kept as the projector inputs */
+/*    of each level's last refresh (the remark after Alg. 3: store x instead  */
+/*    of A_i x, same number of products by linearity), with the running sum   */
+/*    sum_i p_i psi_i kept as its own m-vector;                               */
+/*  - independent: the primal level (back-projector, phi tables) is drawn     */
+/*    from a second stream, the dual level (projector, psi tables) from the   */
+/*    first (the separate primal and dual samples named as an open question   */
+/*    in the concluding section).                                             */
+/* ------------------------------------------------------------------------ */
+
+uint64_t orc_primal_seed(uint64_t seed) {
+  /* the SplitMix64 finaliser applied to the seed itself */
+  uint64_t z = seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const double *b,
+                              uint64_t seed, int64_t k0, int32_t iters, double *x, double *xbar,
+                              double *y, double *phi, double *psi, double *snap,
+                              double *psi_mean, int32_t *levels_dual, int32_t *levels_primal) {
+  const int32_t r = n_levels(d);
+  const int64_t np = n_pix(d), m = n_meas(d);
+  const double sigma = d->sigma, mu = d->mu;
+  if (!(sigma > 0.0) || !(mu > 0.0)) return 1;
+  if (var->sequential && !xbar) return 2;
+  if (var->snapshots ? (!snap || !psi_mean) : !psi) return 2;
+  const uint64_t seed_x = var->independent ? orc_primal_seed(seed) : seed;
+  double *phi_new = dalloc(np), *kx = dalloc(m), *delta = dalloc(m), *diff = dalloc(np);
+  double *u = dalloc(np), *xi = dalloc(np), *zeta = dalloc(m), *v = dalloc(np), *xn = dalloc(np);
+  double *yn = dalloc(m);
+  for (int32_t it = 0; it < iters; ++it) {
+    const uint64_t k = (uint64_t)(k0 + it);
+    const int32_t ld = orc_level(d, seed, k);   /* dual level: projector, psi tables */
+    const int32_t lp = orc_level(d, seed_x, k); /* primal level: back-projector, phi tables */
+    if (levels_dual) levels_dual[it] = ld;
+    if (levels_primal) levels_primal[it] = lp;
+    /* projector input: x^k (Alg. 1) or xbar^k (Alg. 7) */
+    memcpy(u, var->sequential ? xbar : x, sizeof(double) * (size_t)np);
+    /* delta = (refreshed psi_ld) - psi_ld and zeta = delta + sum_i p_i psi_i */
+    if (var->snapshots) {
+      for (int64_t p = 0; p < np; ++p) diff[p] = u[p] - snap[(int64_t)ld * np + p];
+      orc_apply_K(d, ld, diff, delta);
+      for (int64_t q = 0; q < m; ++q) zeta[q] = delta[q] + psi_mean[q];
+    } else {
+      orc_apply_K(d, ld, u, kx);
+      for (int64_t q = 0; q < m; ++q) {
+        double s = 0.0;
+        for (int32_t i = 0; i < r; ++i) s += prob(d, i) * psi[(int64_t)i * m + q];
+        delta[q] = kx[q] - psi[(int64_t)ld * m + q];
+        zeta[q] = delta[q] + s;
+      }
+    }
+    /* Alg. 1 back-projects y^k; Alg. 7 back-projects y^{k+1} */
+    for (int64_t q = 0; q < m; ++q) yn[q] = (y[q] + sigma * zeta[q] - sigma * b[q]) / (1.0 + sigma);
+    orc_apply_KT(d, lp, var->sequential ? yn : y, phi_new);
+    for (int64_t p = 0; p < np; ++p) {
+      double s = 0.0;
+      for (int32_t i = 0; i < r; ++i) s += prob(d, i) * phi[(int64_t)i * np + p];
+      xi[p] = phi_new[p] - phi[(int64_t)lp * np + p] + s;
+    }
+    for (int64_t p = 0; p < np; ++p) v[p] = x[p] - (sigma / mu) * xi[p];
+    orc_prox(d, sigma / mu, v, xn);
+    if (var->sequential)
+      for (int64_t p = 0; p < np; ++p) xbar[p] = xn[p] + var->theta * (xn[p] - x[p]);
+    memcpy(x, xn, sizeof(double) * (size_t)np);
+    memcpy(y, yn, sizeof(double) * (size_t)m);
+    /* table updates */
+    memcpy(phi + (int64_t)lp * np, phi_new, sizeof(double) * (size_t)np);
+    if (var->snapshots) {
+      for (int64_t q = 0; q < m; ++q) psi_mean[q] += prob(d, ld) * delta[q];
+      memcpy(snap + (int64_t)ld * np, u, sizeof(double) * (size_t)np);
+    } else {
+      memcpy(psi + (int64_t)ld * m, kx, sizeof(double) * (size_t)m);
+    }
+  }
+  free(phi_new);
+  free(kx);
+  free(delta);
+  free(diff);
+  free(u);
+  free(xi);
+  free(zeta);
+  free(v);
+  free(xn);
+  free(yn);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Step-size constants -- Sec. 3.4 (B, Bbar, Bbar_p with A_i = p_i K_i and the */
 /* normalisation of Sec. 3.3 by sqrt(mu)), estimated by the power method.     */
 /* ------------------------------------------------------------------------ */

@@ -82,6 +82,31 @@ int32_t orc_imask_run(const orc_desc *d, const double *b, uint64_t seed, int64_t
                       int32_t iters, double *x, double *y, double *phi, double *psi,
                       int32_t *levels_out);
 
+/* ---- Alg. 7 (ImaSk-Seq) ---- */
+/* Iterations k0 .. k0+iters-1 of Alg. 7 in place on (x[d], xbar[d], y[m],
+ * phi[r*d], psi[r*m]); theta is the extrapolation weight.  Returns 0. */
+int32_t orc_imask_seq_run(const orc_desc *d, const double *b, uint64_t seed, int64_t k0,
+                          int32_t iters, double theta, double *x, double *xbar, double *y,
+                          double *phi, double *psi, int32_t *levels_out);
+
+/* ---- variants on one loop ---- */
+typedef struct {
+  int32_t sequential;  /* 0: Alg. 1 order; 1: Alg. 7 order with extrapolation */
+  double theta;        /* Alg. 7 extrapolation weight */
+  int32_t snapshots;   /* 1: dual tables kept as projector-input snapshots */
+  int32_t independent; /* 1: primal level drawn from the stream of orc_primal_seed(seed) */
+} orc_variant;
+
+uint64_t orc_primal_seed(uint64_t seed);
+/* State: x[d], xbar[d] (sequential), y[m], phi[r*d], and either psi[r*m]
+ * (snapshots = 0) or snap[r*d] with psi_mean[m] (snapshots = 1); unused
+ * arrays may be NULL.  levels_dual / levels_primal may be NULL.  Returns 0,
+ * 1 for a non-positive sigma or mu, 2 for a missing array. */
+int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const double *b,
+                              uint64_t seed, int64_t k0, int32_t iters, double *x, double *xbar,
+                              double *y, double *phi, double *psi, double *snap,
+                              double *psi_mean, int32_t *levels_dual, int32_t *levels_primal);
+
 /* ---- step-size theory (Sec. 3.4-3.6, Thm. 3) ---- */
 /* Power method on sum_l w_l K_l^T K_l (transposed=0, size d) or
  * sum_l w_l K_l K_l^T (transposed=1, size m); cross=1 applies
