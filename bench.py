@@ -270,6 +270,140 @@ def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops):
 
 
 # ---------------------------------------------------------------------------------
+# iteration variants (Alg. 7, snapshot tables, independent draws)
+# ---------------------------------------------------------------------------------
+def variant_params(variant: str, dual_tables: int, draws: int) -> dict:
+    return {"variant": 1 if variant == "seq" else 0, "theta": 1.0,
+            "dual_tables": int(dual_tables), "draws": int(draws)}
+
+
+VARIANT_SET = {
+    "alg7_seq": ("seq", 0, 0),
+    "snapshot_tables": ("alg1", 1, 0),
+    "independent_draws": ("alg1", 0, 1),
+    "alg7_seq_snapshot_tables": ("seq", 1, 0),
+}
+
+
+def time_variants(imask, p, bt, info, iters, stream, flush, x, steps=3):
+    """solves/s of each variant over `steps` solves (after one warm-up solve),
+    same workload, mu and (Alg. 1) sigma; Alg. 7 takes sigma = 0.05."""
+    import torch
+    out = {}
+    for name, (v, dt, dr) in VARIANT_SET.items():
+        sigma = 0.05 if v == "seq" else info["sigma"]
+        plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=sigma,
+                               **variant_params(v, dt, dr)))
+        with torch.cuda.stream(stream):
+            plan.solve(bt, 777, iters, out=x, stream=stream)
+        ms = []
+        for k in range(steps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                a.record(stream)
+                plan.solve(bt, 5000 + k, iters, out=x, stream=stream)
+                e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        plan.check()
+        out[name] = {"solves_per_s": 1e3 * steps / float(sum(ms)), "sigma": sigma,
+                     "ms_per_solve": float(np.mean(ms))}
+        plan.close()
+    return out
+
+
+def cg_fixed_point(plan, p, b, mu, iters=150):
+    """x_nat = argmin 1/2|Kbar x - b|^2 + mu/2|x|^2 (eq. min_obj_new), Kbar =
+    sum_l p_l K_l, by conjugate gradients on the normal equations; operator
+    applications through the library (FP32), vectors in FP64."""
+    import torch
+    pr = np.asarray(p.probs if p.probs is not None else [1.0 / p.levels] * p.levels)
+
+    def apply_K(v):
+        v32 = v.float()
+        acc = torch.zeros(p.m, dtype=torch.float64, device=v.device)
+        for ell in range(p.levels):
+            acc += pr[ell] * plan.project(ell, v32).double()
+        return acc
+
+    def apply_KT(w):
+        w32 = w.float()
+        acc = torch.zeros(p.d, dtype=torch.float64, device=w.device)
+        for ell in range(p.levels):
+            acc += pr[ell] * plan.backproject(ell, w32).double()
+        return acc
+
+    def normal(v):
+        return apply_KT(apply_K(v)) + mu * v
+
+    bb = b.double()
+    rhs = apply_KT(bb)
+    xk = torch.zeros_like(rhs)
+    r = rhs.clone()
+    d = r.clone()
+    rr = float(r @ r)
+    r0 = math.sqrt(rr)
+    for _ in range(iters):
+        q = normal(d)
+        a = rr / float(d @ q)
+        xk += a * d
+        r -= a * q
+        rn = float(r @ r)
+        if math.sqrt(rn) < 1e-9 * r0:
+            break
+        d = r + (rn / rr) * d
+        rr = rn
+    return xk.float(), math.sqrt(rr) / r0
+
+
+def run_ablation(args):
+    """Step-size ablation (sigma*/2, sigma*, sigma_B of Sec. 3.6) and Alg. 7 on
+    the fan512 workload: relative distance to the fixed point x_nat after K
+    iterations, mean over seeds."""
+    import torch
+    from paper_2412_10249_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask
+    p = inputs.fan512_problem()
+    _, b, _ = inputs.measurements(p, seed=0)
+    bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
+    base = imask.Plan(dict(p.params(), mu=0.0, sigma=0.0))
+    info = base.info
+    mu = info["mu"]
+    xnat, cg_res = cg_fixed_point(base, p, bt, mu)
+    sig_star = info["sigma"]
+    sig_b = 1.0 / (info["L"] ** 2 + 3.0 * info["Lbar"] ** 2)
+    runs = {"alg1_sigma_star_half": dict(sigma=0.5 * sig_star),
+            "alg1_sigma_star": dict(sigma=sig_star),
+            "alg1_sigma_B": dict(sigma=sig_b),
+            "alg7_seq_sigma_0.05_theta_1": dict(sigma=0.05, variant=1, theta=1.0)}
+    marks = [50, 100, 200, 500, 1000, 2000]
+    res = {}
+    for name, extra in runs.items():
+        plan = imask.Plan(dict(p.params(), mu=mu, **extra))
+        dist = np.zeros(len(marks))
+        for seed in range(args.ablation_seeds):
+            s = plan.state(bt, seed)
+            done = 0
+            for i, k in enumerate(marks):
+                s.step(k - done)
+                done = k
+                dist[i] += imask.imask_rel_distance(s.get(s.X), xnat)
+            s.close()
+        plan.close()
+        res[name] = {"sigma": extra["sigma"],
+                     "rel_dist": {str(k): float(v / args.ablation_seeds)
+                                  for k, v in zip(marks, dist)}}
+    line = {"ablation": "step size and variant, fan512", "mu": mu, "sigma_star": sig_star,
+            "theta_star": info["theta"], "sigma_B": sig_b, "L": info["L"], "Lbar": info["Lbar"],
+            "Lbar_p": info["Lbar_p"], "cg_rel_residual": cg_res, "seeds": args.ablation_seeds,
+            "runs": res}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------
 def run_ours(args):
@@ -288,7 +422,9 @@ def run_ours(args):
     bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
     # mu and sigma: derived by the plan (power method + Thm. 3) unless given
     n_launch_start = imask.imask_launch_count()
-    plan = imask.Plan(dict(p.params(), mu=max(args.mu, 0.0), sigma=max(args.sigma, 0.0)))
+    vopts = variant_params(args.variant, args.dual_tables, args.draws)
+    plan = imask.Plan(dict(p.params(), mu=max(args.mu, 0.0), sigma=max(args.sigma, 0.0),
+                           **vopts))
     info = plan.info
     n_launch_plan = imask.imask_launch_count() - n_launch_start
     stream = torch.cuda.Stream()
@@ -362,6 +498,11 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (kind, level) ----
     roofline = roofline_report(p, prof_ms, prof_cnt, args.alu_peak_tflops)
 
+    # ---- the other iteration variants on the same workload (short runs) ----
+    variants = None
+    if not args.no_variants:
+        variants = time_variants(imask, p, bt, info, args.iters, stream, flush, x)
+
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -383,6 +524,7 @@ def run_ours(args):
                     "Poisson I0=1e4)",
             "config": {"workload": WORKLOAD, "n": p.n, "views": p.n_angles, "bins": p.n_det,
                        "levels": p.levels, "iters_per_solve": args.iters,
+                       "iteration": vopts,
                        "mu": info["mu"], "sigma": info["sigma"], "theta": info["theta"],
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"replicas x{world}"},
@@ -398,6 +540,7 @@ def run_ours(args):
             "clocks": clk,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "variants": variants,
         }
         print(json.dumps(line))
     return 0
@@ -415,6 +558,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--probe", action="store_true",
                     help="time the bare projector / back-projector per level and exit")
+    ap.add_argument("--variant", default="alg1", choices=["alg1", "seq"],
+                    help="iteration timed on the headline line: Alg. 1 or Alg. 7")
+    ap.add_argument("--dual-tables", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--draws", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--ablation", action="store_true",
+                    help="distance to the fixed point for the step sizes of Sec. 3.6 and Alg. 7")
+    ap.add_argument("--ablation-seeds", type=int, default=3)
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--sigma", type=float, default=0.0)
     # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
@@ -431,6 +582,8 @@ def main():
         return run_reference(args)
     if args.probe:
         return run_probe(args)
+    if args.ablation:
+        return run_ablation(args)
     return run_ours(args)
 
 

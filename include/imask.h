@@ -66,8 +66,29 @@ typedef struct imask_state_s *imask_state_t; /* one solve: x, y, SAGA tables, co
  * offset (-sin, cos).  probs[ell] (NULL: uniform) are the p_ell of Alg. 1.
  * R(x) = mu/2 |x|^2 (reg 0) or mu/2 |x|^2 + tv_lambda sum sqrt(|grad x|^2 +
  * tv_eps^2) with forward differences (reg 1, prox by tv_inner FISTA steps).
- * mu <= 0 picks mu = |K|^2 / 2.46^2; sigma <= 0 picks the step of Thm. 3 from
- * power-method estimates of L, Lbar, Lbar_p (Sec. 3.4-3.6). */
+ * mu <= 0 picks mu = |K|^2 / 2.46^2; sigma <= 0 picks a step from power-method
+ * estimates of L, Lbar, Lbar_p (Sec. 3.4-3.6) by step_rule: 0 the Thm. 3
+ * optimum sigma*, 1 half of sigma*, 2 sigma_B = 1/(L^2 + 3 Lbar^2) (the comparison
+ * step of Sec. 3.6); for variant 1 sigma <= 0 picks 0.05, the value the paper
+ * found by grid search for Alg. 7.
+ *
+ * Iteration options (a zero-filled tail selects plain Alg. 1):
+ *  variant      0: Alg. 1 (parallel primal and dual updates);
+ *               1: Alg. 7, ImaSk-Seq: the dual update first (projector on the
+ *               extrapolated iterate xbar), the back-projector on the new dual
+ *               iterate, then xbar = x+ + theta (x+ - x).
+ *  theta        the extrapolation weight of Alg. 7 (the paper uses 1).
+ *  dual_tables  0: the measurement-side tables psi_l = K_l x (levels * m
+ *               floats); 1: per level the sketched projector input of its
+ *               last refresh (n^2 + sum_{l>=1} (n/2^l)^2 floats; the remark
+ *               after Alg. 3), the projector then applies K_l to the
+ *               difference.  Same iterates up to rounding.
+ *  draws        0: one level per iteration (Alg. 1); 1: the primal level
+ *               (back-projector, image-side tables) is drawn from a second
+ *               SplitMix64 stream whose seed is the SplitMix64 finaliser of
+ *               the seed, the dual level (projector) from the first
+ *               (independent primal and dual samples, an open question of the
+ *               paper's concluding section). */
 typedef struct {
   int32_t n, n_angles, n_det, geometry;  /* geometry: 0 parallel, 1 fan */
   double fov, det_spacing, angle_start, angle_span, src_dist, det_dist;
@@ -78,10 +99,16 @@ typedef struct {
   int32_t tv_inner;
   double sigma;
   int32_t storage;                       /* 0: fp32 (the only storage implemented) */
+  int32_t variant;                       /* 0 Alg. 1, 1 Alg. 7 */
+  double theta;                          /* Alg. 7 extrapolation */
+  int32_t dual_tables;                   /* 0 K_l x tables, 1 input snapshots */
+  int32_t draws;                         /* 0 common level, 1 independent primal/dual */
+  int32_t step_rule;                     /* sigma <= 0: 0 sigma*, 1 half, 2 sigma_B */
 } imask_desc;
 
 /* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,
- * Lbar_p; sigma and theta of Thm. 3 (theta = 0 when sigma was given). */
+ * Lbar_p; sigma, and theta, the contraction factor of Thm. 3 for that sigma
+ * (0 when sigma was given or for variant 1). */
 typedef struct {
   double mu, sigma, theta, L, Lbar, Lbar_p, norm_K;
   int64_t n_meas, n_pix;

@@ -130,10 +130,12 @@ struct imask_state_s {
   int cur = 0;
   cudaStream_t stream = nullptr;
   float *block = nullptr;
+  unsigned long long seed_x = 0;   // primal level stream (= seed unless draws = 1)
   float *x = nullptr, *y[2] = {nullptr, nullptr}, *b = nullptr, *psi = nullptr,
         *psi_mean = nullptr, *phi0 = nullptr, *phic = nullptr, *phi_mean = nullptr, *g = nullptr,
-        *tv = nullptr;
+        *tv = nullptr, *x_prev = nullptr;
   long long phic_off[IMASK_MAX_LEVELS] = {0};
+  SnapArgs snap{};   // dual_tables = 1: sketched projector inputs per level
   PadSet pads{};
 };
 
@@ -177,6 +179,15 @@ imask_status validate(const imask_desc *d) {
   if (d->reg == 1 && (!(d->tv_eps > 0.0) || d->tv_lambda < 0.0 || d->tv_inner < 0))
     return fail(IMASK_ERR_INVALID, "smoothed TV needs tv_eps > 0, tv_lambda >= 0, tv_inner >= 0");
   if (d->storage != 0) return fail(IMASK_ERR_INVALID, "only fp32 storage (0) is implemented");
+  if (d->variant != 0 && d->variant != 1)
+    return fail(IMASK_ERR_INVALID, "variant must be 0 (Alg. 1) or 1 (Alg. 7)");
+  if (d->variant == 1 && !isfinite(d->theta))
+    return fail(IMASK_ERR_INVALID, "theta must be finite");
+  if (d->dual_tables != 0 && d->dual_tables != 1)
+    return fail(IMASK_ERR_INVALID, "dual_tables must be 0 or 1");
+  if (d->draws != 0 && d->draws != 1) return fail(IMASK_ERR_INVALID, "draws must be 0 or 1");
+  if (d->step_rule < 0 || d->step_rule > 2)
+    return fail(IMASK_ERR_INVALID, "step_rule must be 0, 1 or 2");
   if (d->geometry == 1) {
     if (!(d->src_dist > 0.5 * d->fov * 1.4142135623730951))
       return fail(IMASK_ERR_INVALID, "fan source must lie outside the field of view");
@@ -352,7 +363,7 @@ DualArgs no_dual() {
 imask_status apply_K(const imask_plan_s *p, int ell, const float *x, float *sino, Scratch &s,
                      cudaStream_t st) {
   const LevelSel sel = fixed_level(ell);
-  CK(launch_sketch(p->dp, sel, x, s.pads, st), "sketch launch");
+  CK(launch_sketch(p->dp, sel, x, s.pads, ExtrapArgs{}, SnapArgs{}, st), "sketch launch");
   {
     ProfScope ps(0, ell < 0 ? 0 : ell, st);
     CK(launch_fp(p->dp, sel, s.pads, sino, no_dual(), p->n_cta_x, p->n_cta_y, p->d_err, st),
@@ -450,9 +461,11 @@ imask_status power_method(const imask_plan_s *p, const double *w, bool cross, bo
 
 imask_status plan_constants(imask_plan_s *p, cudaStream_t st) {
   const bool need_mu = !(p->desc.mu > 0.0);
-  const bool need_sigma = !(p->desc.sigma > 0.0);
   p->mu = p->desc.mu;
   p->sigma = p->desc.sigma;
+  // Alg. 7 has no step-size theory; the paper tuned sigma = 0.05 by grid search
+  if (p->desc.variant == 1 && !(p->sigma > 0.0)) p->sigma = 0.05;
+  const bool need_sigma = !(p->sigma > 0.0);
   if (!need_mu && !need_sigma) return IMASK_OK;
   const int iters = 100;
   const long long d = p->dp.d, m = p->dp.m;
@@ -510,6 +523,14 @@ imask_status plan_constants(imask_plan_s *p, cudaStream_t st) {
     imask_optimal_step(p->L, p->Lbar, p->Lbar_p, pmin, 200, out);
     p->sigma = out[0];
     p->theta = out[1];
+    if (p->desc.step_rule == 1) {
+      p->sigma = 0.5 * out[0];
+      p->theta = 0.0;
+    } else if (p->desc.step_rule == 2) {
+      // the step of the SAGA primal-dual method the paper compares with
+      p->sigma = 1.0 / (p->L * p->L + 3.0 * p->Lbar * p->Lbar);
+      p->theta = 0.0;
+    }
   } while (false);
   cudaFreeAsync(mem, st);
   scratch_free(s);
@@ -936,8 +957,18 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   const int r = p->desc.levels;
   const size_t d = p->dp.d, m = p->dp.m;
   Carve cv;
+  const bool snapshots = p->desc.dual_tables == 1;
+  const bool seq = p->desc.variant == 1;
   size_t o_x = cv.take(d), o_y0 = cv.take(m), o_y1 = cv.take(m), o_b = cv.take(m);
-  size_t o_psi = cv.take(m * r), o_psim = cv.take(m), o_phi0 = cv.take(d), o_phim = cv.take(d);
+  size_t o_psi = snapshots ? 0 : cv.take(m * r);
+  size_t o_psim = cv.take(m), o_phi0 = cv.take(d), o_phim = cv.take(d);
+  size_t o_snap[IMASK_MAX_LEVELS] = {0};
+  if (snapshots)
+    for (int l = 0; l < r; ++l) {
+      const size_t nl = (size_t)p->dp.lg[l + 1].nl;
+      o_snap[l] = cv.take(nl * nl);
+    }
+  size_t o_xprev = (seq && p->desc.reg == 1) ? cv.take(d) : 0;
   size_t o_g = cv.take(p->gcap);
   size_t o_phic[IMASK_MAX_LEVELS] = {0};
   for (int l = 1; l < r; ++l) {
@@ -962,8 +993,14 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   s->y[0] = B + o_y0;
   s->y[1] = B + o_y1;
   s->b = B + o_b;
-  s->psi = B + o_psi;
+  s->psi = snapshots ? nullptr : B + o_psi;
   s->psi_mean = B + o_psim;
+  s->seed_x = p->desc.draws == 1 ? primal_seed(seed) : seed;
+  if (snapshots) {
+    s->snap.snap = B;
+    for (int l = 0; l < r; ++l) s->snap.snap_off[l] = (long long)o_snap[l];
+  }
+  s->x_prev = o_xprev ? B + o_xprev : nullptr;
   s->phi0 = B + o_phi0;
   s->phi_mean = B + o_phim;
   s->g = B + o_g;
@@ -992,15 +1029,21 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
   s->stream = st;
   const imask_plan_s *p = s->plan;
   const DevPlan &P = p->dp;
+  const bool seq = p->desc.variant == 1;
   const float sigma = (float)p->sigma;
   const float inv_1ps = (float)(1.0 / (1.0 + p->sigma));
   const float tau = (float)(p->sigma / p->mu);
+  const float theta = (float)p->desc.theta;
   for (int it = 0; it < n_iters; ++it) {
     LevelSel sel{};
     sel.fixed = -2;
     sel.seed = s->seed;
+    sel.seed_x = s->seed_x;
     sel.k = s->k;
     const int lvl = g_prof.on ? lvl_host_draw(P, s->seed, s->k) : 0;
+    const int lvl_x = g_prof.on ? lvl_host_draw(P, s->seed_x, s->k) : 0;
+    // dual half: projector on the sketch of x^k (Alg. 1) or xbar^k (Alg. 7)
+    // prepared by the previous iteration, fused with the zeta and y updates
     DualArgs D{};
     D.on = 1;
     D.y_in = s->y[s->cur];
@@ -1015,9 +1058,11 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
       CK(launch_fp(P, sel, s->pads, nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, st),
          "projector launch");
     }
+    // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
     {
-      ProfScope ps(1, lvl, st);
-      CK(launch_bp(P, sel, s->y[s->cur], s->g, p->d_err, st), "back-projector launch");
+      ProfScope ps(1, lvl_x, st);
+      CK(launch_bp(P, sel, seq ? s->y[1 - s->cur] : s->y[s->cur], s->g, p->d_err, st),
+         "back-projector launch");
     }
     PrimalArgs A{};
     A.g = s->g;
@@ -1029,8 +1074,12 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
     A.tau = tau;
     A.inv_1ps = inv_1ps;
     A.prox_in_place = p->desc.reg == 0 ? 1 : 0;
+    A.x_prev = p->desc.reg == 0 ? nullptr : s->x_prev;
+    A.extrapolate = seq ? 1 : 0;
+    A.theta = theta;
+    A.snap = s->snap;
     {
-      ProfScope ps(2, lvl, st);
+      ProfScope ps(2, lvl_x, st);
       CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
     }
     if (p->desc.reg == 1) {
@@ -1039,7 +1088,12 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
          "TV prox launch");
       LevelSel nxt = sel;
       nxt.k = s->k + 1;
-      CK(launch_sketch(P, nxt, s->x, s->pads, st), "sketch launch");
+      ExtrapArgs ex{};
+      if (seq) {
+        ex.x_prev = s->x_prev;
+        ex.theta = theta;
+      }
+      CK(launch_sketch(P, nxt, s->x, s->pads, ex, s->snap, st), "sketch launch");
     }
     s->cur = 1 - s->cur;
     s->k += 1;

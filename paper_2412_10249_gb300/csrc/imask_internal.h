@@ -74,11 +74,30 @@ struct PadSet {
 };
 
 // Level selection for a launch: fixed >= -1 uses that level, otherwise the
-// level is drawn from (seed, k) on the device.
+// level is drawn on the device from (seed, k) for the projector side and from
+// (seed_x, k) for the back-projector / image side (seed_x = seed unless the
+// primal and dual levels are drawn independently).
 struct LevelSel {
   int fixed;
   unsigned long long seed;
+  unsigned long long seed_x;
   long long k;
+};
+
+// Snapshot form of the measurement-side tables: per level the sketched
+// projector input of its last refresh, level ell at snap + snap_off[ell]
+// (n*n floats for ell = 0, (n >> ell)^2 for ell >= 1).  snap == nullptr: the
+// sketch is written as is.
+struct SnapArgs {
+  float *snap;
+  long long snap_off[IMASK_MAX_LEVELS];
+};
+
+// Projector input of Alg. 7: xbar = x + theta (x - x_prev); x_prev == nullptr
+// (and theta unused) gives x itself.
+struct ExtrapArgs {
+  const float *x_prev;
+  float theta;
 };
 
 // Dual epilogue (Alg. 1, the zeta and y updates) fused into the projector.
@@ -87,7 +106,8 @@ struct DualArgs {
   const float *y_in;
   float *y_out;
   const float *b;
-  float *psi;        // table base, level ell at psi + ell * m
+  float *psi;        // table base, level ell at psi + ell * m; nullptr: the
+                     // projector output is already the table difference
   float *psi_mean;   // sum_l p_l psi_l
   float sigma, inv_1ps;
 };
@@ -103,6 +123,10 @@ struct PrimalArgs {
   float tau;         // sigma / mu
   float inv_1ps;     // 1 / (1 + sigma)
   int prox_in_place; // 1: quadratic prox here; 0: store v, a TV prox follows
+  float *x_prev;     // nullptr, or receives x^k (Alg. 7 with a TV prox)
+  int extrapolate;   // 1: the fused sketch is of x+ + theta (x+ - x^k) (Alg. 7)
+  float theta;
+  SnapArgs snap;
 };
 
 // ---- kernel launchers (kernels.cu) -------------------------------------------
@@ -111,7 +135,8 @@ int lvl_host_draw(const DevPlan &P, unsigned long long seed, long long k);
 cudaError_t launch_levels(const DevPlan &P, unsigned long long seed, long long k0, long long n,
                           int *out, cudaStream_t st);
 cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet pads,
-                          cudaStream_t st);
+                          ExtrapArgs ex, SnapArgs snap, cudaStream_t st);
+unsigned long long primal_seed(unsigned long long seed);
 cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
                       int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st);
 cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,

@@ -46,8 +46,14 @@ __host__ __device__ __forceinline__ int draw_level(const DevPlan &P, unsigned lo
   return l;
 }
 
+// Projector-side (dual) level of a launch.
 __device__ __forceinline__ int sel_level(const DevPlan &P, const LevelSel &s) {
   return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed, s.k);
+}
+
+// Back-projector / image-side (primal) level of a launch.
+__device__ __forceinline__ int sel_level_x(const DevPlan &P, const LevelSel &s) {
+  return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed_x, s.k);
 }
 
 // ---------------------------------------------------------------------------------
@@ -294,14 +300,19 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
       sino[q] = v;
     } else {
       // Alg. 1: zeta = psi_new - psi_l + sum p psi; y+ = (y + s zeta - s b)/(1+s);
-      // the running mean and the table entry take the refreshed value.
-      float *psil = D.psi + (size_t)ell * P.m;
-      const float po = psil[q];
+      // the running mean and the table entry take the refreshed value.  With
+      // snapshot tables the projector already applied K_l to the input
+      // difference, so v is psi_new - psi_l itself.
+      float delta = v;
+      if (D.psi) {
+        float *psil = D.psi + (size_t)ell * P.m;
+        delta = v - psil[q];
+        psil[q] = v;
+      }
       const float pm = D.psi_mean[q];
-      const float zeta = v - po + pm;
+      const float zeta = delta + pm;
       D.y_out[q] = fmaf(D.sigma, zeta - D.b[q], D.y_in[q]) * D.inv_1ps;
-      D.psi_mean[q] = fmaf(P.probs[ell], v - po, pm);
-      psil[q] = v;
+      D.psi_mean[q] = fmaf(P.probs[ell], delta, pm);
     }
   }
 }
@@ -435,7 +446,7 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
   // private accumulators: [slot][thread]; slots 0..BP_ACC-1 are cross lines
   // -2..BP_SEG+1 of the owner's segment
   __shared__ float acc_s[BP_ACC * BP_THREADS];
-  const int ell = sel_level(P, sel);
+  const int ell = sel_level_x(P, sel);
   const LevelGeom G = P.lg[ell + 1];
   const int nm = G.bp_nm, nc = G.bp_nc, vgo = G.bp_vgo;
   const int ntile = nm * nc;
@@ -651,14 +662,25 @@ __device__ __forceinline__ float compensate_px(const DevPlan &P, float v, const 
 
 // Writes the tile's contribution to the padded images of level `ell`
 // (-1: plain grid).  `vals` holds the level values of the tile (side `side`).
-__device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, const float *vals,
-                             int side, int ti0, int tj0) {
+// With a snapshot array S of the level (ell >= 0) the images receive
+// vals - S, S takes vals, and vals is overwritten with the difference.
+__device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, float *vals,
+                             int side, int ti0, int tj0, float *S) {
   const int li = ell + 1;
   const LevelGeom G = P.lg[li];
   const int sh = ell > 0 ? ell : 0;
   const int I0 = ti0 >> sh, J0 = tj0 >> sh;
   float *R = pads.R[li];
   float *T = pads.T[li];
+  if (S) {
+    for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
+      const size_t gi = (size_t)(I0 + p / side) * G.nl + J0 + p % side;
+      const float v = vals[p];
+      vals[p] = v - S[gi];
+      S[gi] = v;
+    }
+    __syncthreads();
+  }
   for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
     const int I = p / side, J = p % side;
     R[(size_t)(I0 + I) * G.ls + IMASK_PAD + J0 + J] = vals[I * side + J];
@@ -670,10 +692,11 @@ __device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, cons
 }
 
 // Sketch of the tile held in xs (fine values) for level ell; uses aux and pyr.
+// S: the level's snapshot array (snapshot tables) or nullptr.
 __device__ void sketch_tile(const DevPlan &P, const PadSet &pads, int ell, float *xs, float *aux,
-                            float *pyr, int ts, int ti0, int tj0) {
+                            float *pyr, int ts, int ti0, int tj0, float *S) {
   if (ell < 0) {
-    write_padded(P, pads, -1, xs, ts, ti0, tj0);
+    write_padded(P, pads, -1, xs, ts, ti0, tj0, nullptr);
     return;
   }
   if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
@@ -681,23 +704,30 @@ __device__ void sketch_tile(const DevPlan &P, const PadSet &pads, int ell, float
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
       aux[p] = compensate_px(P, xs[p], pyr, ts, p / ts, p % ts);
     __syncthreads();
-    write_padded(P, pads, 0, aux, ts, ti0, tj0);
+    write_padded(P, pads, 0, aux, ts, ti0, tj0, S);
   } else {
-    write_padded(P, pads, ell, pyr + pyr_off(ts, ell), ts >> ell, ti0, tj0);
+    write_padded(P, pads, ell, pyr + pyr_off(ts, ell), ts >> ell, ti0, tj0, S);
   }
 }
 
+// Sketch of x (or of Alg. 7's xbar = x + theta (x - x_prev)) for the
+// projector-side level of sel.
 __global__ void __launch_bounds__(UPD_THREADS)
-    k_sketch(DevPlan P, LevelSel sel, const float *__restrict__ x, PadSet pads) {
+    k_sketch(DevPlan P, LevelSel sel, const float *__restrict__ x, PadSet pads, ExtrapArgs ex,
+             SnapArgs sn) {
   extern __shared__ __align__(16) float upd_smem[];
   const int ts = P.upd_tile, ntx = P.n / ts;
   float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
   const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
   const int ell = sel_level(P, sel);
-  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-    xs[p] = x[(size_t)(ti0 + p / ts) * P.n + tj0 + p % ts];
+  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
+    const size_t gp = (size_t)(ti0 + p / ts) * P.n + tj0 + p % ts;
+    const float v = x[gp];
+    xs[p] = ex.x_prev ? fmaf(ex.theta, v - ex.x_prev[gp], v) : v;
+  }
   __syncthreads();
-  sketch_tile(P, pads, ell, xs, aux, pyr, ts, ti0, tj0);
+  float *S = (sn.snap && ell >= 0) ? sn.snap + sn.snap_off[ell] : nullptr;
+  sketch_tile(P, pads, ell, xs, aux, pyr, ts, ti0, tj0, S);
 }
 
 // img = K_ell^T-side image map of g: ell >= 1: 4^-ell T^* g; ell = 0: S_r g;
@@ -748,7 +778,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
   float *dc = pyr + ts * ts / 2 + 4;
   const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
   const int n = P.n;
-  const int ell = sel_level(P, sel);
+  const int ell = sel_level_x(P, sel);
   const float pl = P.probs[ell];
 
   int cs = 0;
@@ -787,16 +817,20 @@ __global__ void __launch_bounds__(UPD_THREADS)
     }
     const float pm = A.phi_mean[gp];
     const float xi = delta + pm;
-    const float v = fmaf(-A.tau, xi, A.x[gp]);
+    const float xo = A.x[gp];
+    const float v = fmaf(-A.tau, xi, xo);
     A.phi_mean[gp] = fmaf(pl, delta, pm);
     const float xn = A.prox_in_place ? v * A.inv_1ps : v;
     A.x[gp] = xn;
-    xs[p] = xn;
+    if (A.x_prev) A.x_prev[gp] = xo;
+    // the next projector input: x+ (Alg. 1) or x+ + theta (x+ - x) (Alg. 7)
+    xs[p] = A.extrapolate ? fmaf(A.theta, xn - xo, xn) : xn;
   }
   if (!write_sketch) return;
   __syncthreads();
   const int elln = draw_level(P, sel.seed, sel.k + 1);
-  sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0);
+  float *S = A.snap.snap ? A.snap.snap + A.snap.snap_off[elln] : nullptr;
+  sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0, S);
 }
 
 // ---------------------------------------------------------------------------------
@@ -964,6 +998,15 @@ int lvl_host_draw(const DevPlan &P, unsigned long long seed, long long k) {
   return draw_level(P, seed, k);
 }
 
+// Seed of the primal stream when the levels are drawn independently: the
+// SplitMix64 finaliser applied to the seed.
+unsigned long long primal_seed(unsigned long long seed) {
+  unsigned long long z = seed;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
 cudaError_t launch_levels(const DevPlan &P, unsigned long long seed, long long k0, long long n,
                           int *out, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -978,13 +1021,13 @@ static cudaError_t set_smem(const void *fn, int bytes) {
 }
 
 cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet pads,
-                          cudaStream_t st) {
+                          ExtrapArgs ex, SnapArgs snap, cudaStream_t st) {
   const int nt = P.n / P.upd_tile;
   const int sm = upd_smem_bytes(P);
   cudaError_t e = set_smem((const void *)k_sketch, sm);
   if (e != cudaSuccess) return e;
   count_launch();
-  k_sketch<<<nt * nt, UPD_THREADS, sm, st>>>(P, sel, x, pads);
+  k_sketch<<<nt * nt, UPD_THREADS, sm, st>>>(P, sel, x, pads, ex, snap);
   return cudaGetLastError();
 }
 

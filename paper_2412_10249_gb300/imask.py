@@ -41,6 +41,9 @@ class Desc(ctypes.Structure):
         ("reg", ctypes.c_int32), ("mu", ctypes.c_double), ("tv_lambda", ctypes.c_double),
         ("tv_eps", ctypes.c_double), ("tv_inner", ctypes.c_int32), ("sigma", ctypes.c_double),
         ("storage", ctypes.c_int32),
+        ("variant", ctypes.c_int32), ("theta", ctypes.c_double),
+        ("dual_tables", ctypes.c_int32), ("draws", ctypes.c_int32),
+        ("step_rule", ctypes.c_int32),
     ]
 
 
@@ -160,6 +163,11 @@ def make_desc(params: dict):
     d.tv_inner = int(params.get("tv_inner", 20))
     d.sigma = float(params.get("sigma", 0.0))
     d.storage = int(params.get("storage", 0))
+    d.variant = int(params.get("variant", 0))
+    d.theta = float(params.get("theta", 1.0))
+    d.dual_tables = int(params.get("dual_tables", 0))
+    d.draws = int(params.get("draws", 0))
+    d.step_rule = int(params.get("step_rule", 0))
     return d, keep
 
 

@@ -43,7 +43,9 @@ def test_every_declared_symbol_is_exported(imask):
 @pytest.mark.parametrize("bad,status", [
     (dict(n=0), 2), (dict(levels=9), 1), (dict(n=60, levels=4), 2),
     (dict(probs=[0.5, 0.6]), 1), (dict(geometry=2), 1), (dict(storage=1), 1),
-    (dict(fov=-1.0), 1), (dict(n=4096), 2),
+    (dict(fov=-1.0), 1), (dict(n=4096), 2), (dict(variant=2), 1),
+    (dict(variant=1, theta=float("nan")), 1), (dict(dual_tables=2), 1), (dict(draws=-1), 1),
+    (dict(step_rule=3), 1),
 ])
 def test_descriptor_validation_without_device(imask, bad, status):
     p = dict(n=64, n_angles=10, n_det=20, levels=2)
