@@ -235,7 +235,7 @@ def _dram_traffic(kname: str, level: int):
         return None
 
 
-def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops):
+def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops, period=1):
     """Dominant (kernel, level) by total event time; its average launch against
     the FP32 CUDA-core peak (bound "alu": the projectors are limited by issue
     slots and the shared-memory pipe, not by DRAM), plus the shared-memory
@@ -250,6 +250,8 @@ def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops):
            "unit": "TFLOP/s", "peak": alu_peak_tflops,
            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
            "avg_launch_us": avg_s * 1e6, "launches": int(prof_cnt[best]),
+           "timed_launches": f"CUDA events around the launches of every {period}-th iteration "
+                             f"inside the timed region",
            "gsamples_per_s": samples_launch / avg_s / 1e9}
     if kind in FLOPS_PER_SAMPLE:
         ach = samples_launch * FLOPS_PER_SAMPLE[kind] / avg_s / 1e12
@@ -359,8 +361,9 @@ def cg_fixed_point(plan, p, b, mu, iters=150):
 
 def run_ablation(args):
     """Step-size ablation (sigma*/2, sigma*, sigma_B of Sec. 3.6) and Alg. 7 on
-    the fan512 workload: relative distance to the fixed point x_nat after K
-    iterations, mean over seeds."""
+    the fan512 workload: squared relative distance |x^k - x_nat|^2 / |x_nat|^2
+    to the fixed point after K iterations (the paper's convergence measure),
+    mean over seeds."""
     import torch
     from paper_2412_10249_gb300 import build as pkg_build
     pkg_build.build()
@@ -389,11 +392,11 @@ def run_ablation(args):
             for i, k in enumerate(marks):
                 s.step(k - done)
                 done = k
-                dist[i] += imask.imask_rel_distance(s.get(s.X), xnat)
+                dist[i] += imask.imask_rel_distance(s.get(s.X), xnat)   # squared
             s.close()
         plan.close()
         res[name] = {"sigma": extra["sigma"],
-                     "rel_dist": {str(k): float(v / args.ablation_seeds)
+                     "rel_dist_sq": {str(k): float(v / args.ablation_seeds)
                                   for k, v in zip(marks, dist)}}
     line = {"ablation": "step size and variant, fan512", "mu": mu, "sigma_star": sig_star,
             "theta_star": info["theta"], "sigma_B": sig_b, "L": info["L"], "Lbar": info["Lbar"],
@@ -447,7 +450,7 @@ def run_ours(args):
     starts = [torch.cuda.Event(enable_timing=True) for _ in seeds]
     ends = [torch.cuda.Event(enable_timing=True) for _ in seeds]
     imask.imask_profile_read(reset=True)
-    imask.imask_profile_enable(True)
+    imask.imask_profile_enable(args.profile_period)
     launches0 = imask.imask_launch_count()
     dist_barrier(world)
     torch.cuda.synchronize()
@@ -496,7 +499,8 @@ def run_ours(args):
     e2e_value = total_solves / T_e2e
 
     # ---- roofline of the dominant kernel (kind, level) ----
-    roofline = roofline_report(p, prof_ms, prof_cnt, args.alu_peak_tflops)
+    roofline = roofline_report(p, prof_ms, prof_cnt, args.alu_peak_tflops,
+                               args.profile_period)
 
     # ---- the other iteration variants on the same workload (short runs) ----
     variants = None
@@ -566,6 +570,8 @@ def main():
     ap.add_argument("--ablation", action="store_true",
                     help="distance to the fixed point for the step sizes of Sec. 3.6 and Alg. 7")
     ap.add_argument("--ablation-seeds", type=int, default=3)
+    ap.add_argument("--profile-period", type=int, default=8,
+                    help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--sigma", type=float, default=0.0)
     # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz

@@ -204,13 +204,16 @@ imask_status imask_objective(imask_plan_t plan, const float *x_dev, const float 
 imask_status imask_rel_distance(int64_t n, const float *a_dev, const float *b_dev, double *out,
                                 void *stream);
 
-/* Kernel timing for roofline reports.  While enabled, every projector and
- * back-projector launch made by this process is bracketed by CUDA events on
- * its stream.  imask_profile_read synchronises those events and returns, per
+/* Kernel timing for roofline reports.  While enabled (period >= 1), the
+ * projector, back-projector and update launches of every period-th iteration
+ * of imask_step (iteration counter k with k % period == 0), and every launch
+ * of imask_project / imask_backproject, are bracketed by CUDA events on their
+ * stream; period 0 disables.  Sampling keeps the events' own cost out of most
+ * iterations.  imask_profile_read synchronises those events and returns, per
  * kind (0 forward projection, 1 back-projection, 2 primal update) and level
  * (0..7), the total milliseconds and launch counts accumulated since the last
  * reset: ms[kind*8 + level], count[kind*8 + level]. */
-imask_status imask_profile_enable(int32_t on);
+imask_status imask_profile_enable(int32_t period);
 imask_status imask_profile_read(double ms[24], int64_t count[24], int32_t reset);
 /* Number of kernels this library has launched in the process so far. */
 int64_t imask_launch_count(void);

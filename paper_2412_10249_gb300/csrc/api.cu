@@ -62,6 +62,7 @@ struct ProfRec {
 struct Profiler {
   std::mutex mu;
   bool on = false;
+  int period = 0;   // imask_step times the iterations with k % period == 0
   std::vector<cudaEvent_t> pool;
   std::vector<ProfRec> pending;
   double ms[24] = {0};
@@ -86,7 +87,8 @@ struct ProfScope {
   bool active = false;
   ProfRec rec{};
   cudaStream_t st = nullptr;
-  ProfScope(int kind, int level, cudaStream_t s) : st(s) {
+  ProfScope(int kind, int level, cudaStream_t s, bool sampled = true) : st(s) {
+    if (!sampled) return;
     std::lock_guard<std::mutex> lk(g_prof.mu);
     if (!g_prof.on || level < 0 || level > 7) return;
     rec.kind = kind;
@@ -1040,8 +1042,9 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
     sel.seed = s->seed;
     sel.seed_x = s->seed_x;
     sel.k = s->k;
-    const int lvl = g_prof.on ? lvl_host_draw(P, s->seed, s->k) : 0;
-    const int lvl_x = g_prof.on ? lvl_host_draw(P, s->seed_x, s->k) : 0;
+    const bool prof = g_prof.on && g_prof.period > 0 && s->k % g_prof.period == 0;
+    const int lvl = prof ? lvl_host_draw(P, s->seed, s->k) : 0;
+    const int lvl_x = prof ? lvl_host_draw(P, s->seed_x, s->k) : 0;
     // dual half: projector on the sketch of x^k (Alg. 1) or xbar^k (Alg. 7)
     // prepared by the previous iteration, fused with the zeta and y updates
     DualArgs D{};
@@ -1054,13 +1057,13 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
     D.sigma = sigma;
     D.inv_1ps = inv_1ps;
     {
-      ProfScope ps(0, lvl, st);
+      ProfScope ps(0, lvl, st, prof);
       CK(launch_fp(P, sel, s->pads, nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, st),
          "projector launch");
     }
     // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
     {
-      ProfScope ps(1, lvl_x, st);
+      ProfScope ps(1, lvl_x, st, prof);
       CK(launch_bp(P, sel, seq ? s->y[1 - s->cur] : s->y[s->cur], s->g, p->d_err, st),
          "back-projector launch");
     }
@@ -1079,7 +1082,7 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
     A.theta = theta;
     A.snap = s->snap;
     {
-      ProfScope ps(2, lvl_x, st);
+      ProfScope ps(2, lvl_x, st, prof);
       CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
     }
     if (p->desc.reg == 1) {
@@ -1210,9 +1213,11 @@ imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_
   return IMASK_OK;
 }
 
-imask_status imask_profile_enable(int32_t on) {
+imask_status imask_profile_enable(int32_t period) {
+  if (period < 0) return fail(IMASK_ERR_INVALID, "profile period must be >= 0");
   std::lock_guard<std::mutex> lk(g_prof.mu);
-  g_prof.on = on != 0;
+  g_prof.on = period != 0;
+  g_prof.period = period;
   return IMASK_OK;
 }
 

@@ -243,8 +243,9 @@ def imask_rel_distance(a, b, stream=None) -> float:
     return out.value
 
 
-def imask_profile_enable(on: bool):
-    _check(lib().imask_profile_enable(1 if on else 0))
+def imask_profile_enable(period):
+    """0/False: off; True/1: every launch; N: every N-th solver iteration."""
+    _check(lib().imask_profile_enable(int(period)))
 
 
 def imask_profile_read(reset: bool = False):
