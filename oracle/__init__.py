@@ -70,7 +70,8 @@ class Oracle:
     ``params`` holds the geometry and solver fields of the problem (the same
     keys as the CUDA library's descriptor: n, n_angles, n_det, geometry, fov,
     det_spacing, angle_start, angle_span, src_dist, det_dist, levels, probs,
-    reg, mu, tv_lambda, tv_eps, tv_inner, sigma).
+    reg, mu, tv_lambda, tv_eps, tv_inner, sigma); reg 2 is TV with a
+    nonnegativity constraint.
     """
 
     _lib = None
@@ -112,6 +113,11 @@ class Oracle:
                                                            ctypes.c_uint64, ctypes.c_int64,
                                                            ctypes.c_int32] + [_D] * 7
                                           + [_I32, _I32]),
+                "orc_pdhg_params": (None, [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           _D]),
+                "orc_pdhg_run": (ctypes.c_int32, [ctypes.c_void_p, _D, ctypes.c_int32,
+                                                  ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_double, _D, _D, _D]),
                 "orc_power_eig": (ctypes.c_double, [ctypes.c_void_p, _D, ctypes.c_int32,
                                                     ctypes.c_int32, ctypes.c_int32]),
                 "orc_constants_dense": (None, [_D, ctypes.c_int32, _D, ctypes.c_int32,
@@ -363,6 +369,25 @@ class Oracle:
             raise ValueError(f"oracle: variant run failed ({rc})")
         state["k"] += iters
         return state, ld[:iters], lp[:iters]
+
+    # -- PDHG on Kbar (comparison method / x_nat generator) ---------------------------
+    @classmethod
+    def pdhg_params(cls, norm_K: float, mu: float, rho: float = 0.99):
+        out = np.zeros(3)
+        cls.lib().orc_pdhg_params(norm_K, mu, rho, _dp(out))
+        return out   # s, t, theta
+
+    def pdhg(self, b: np.ndarray, iters: int, s: float, t: float, theta: float, state=None):
+        d, m = self.n * self.n, self.m
+        if state is None:
+            state = {"x": np.zeros(d), "xbar": np.zeros(d), "y": np.zeros(m), "k": 0}
+        b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        rc = self.L.orc_pdhg_run(self.ref, _dp(b), iters, s, t, theta, _dp(state["x"]),
+                                 _dp(state["xbar"]), _dp(state["y"]))
+        if rc != 0:
+            raise ValueError("oracle: PDHG steps must be positive")
+        state["k"] += iters
+        return state
 
     # -- step-size theory -----------------------------------------------------------
     def power_eig(self, w, cross: bool, transposed: bool, iters: int) -> float:

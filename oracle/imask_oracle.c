@@ -359,9 +359,21 @@ static void grad_fwd_T(int32_t n, const double *w1, const double *w2, double *ou
     }
 }
 
-/* R(x) = mu/2 |x|^2 (+ lambda sum_p sqrt(|grad x|_p^2 + eps^2) when reg = 1). */
+/* R(x) = mu/2 |x|^2 (+ lambda sum_p sqrt(|grad x|_p^2 + eps^2) when reg = 1);
+ * reg = 2: lambda sum_p |grad x|_p (TV with a nonnegativity constraint). */
 double orc_regulariser(const orc_desc *d, const double *x) {
   const int64_t np = n_pix(d);
+  if (d->reg == 2) {
+    /* lambda |grad x|_{1,2}; the nonnegativity indicator is not evaluated
+     * (the iterates are nonnegative by construction of the prox) */
+    double *g1 = dalloc(np), *g2 = dalloc(np);
+    grad_fwd(d->n, x, g1, g2);
+    double tv = 0.0;
+    for (int64_t p = 0; p < np; ++p) tv += sqrt(g1[p] * g1[p] + g2[p] * g2[p]);
+    free(g1);
+    free(g2);
+    return d->tv_lambda * tv;
+  }
   double r = 0.5 * d->mu * dot(x, x, np);
   if (d->reg == 1) {
     double *g1 = dalloc(np), *g2 = dalloc(np);
@@ -375,6 +387,72 @@ double orc_regulariser(const orc_desc *d, const double *x) {
   return r;
 }
 
+/* argmin_{x >= 0} 1/2 |x - v|^2 + alpha |grad x|_{1,2} (Sec. 5.3: TV with a
+ * nonnegativity constraint, prox by FISTA) by exactly tv_inner iterations of
+ * the fast gradient projection on the dual (Beck & Teboulle, IEEE TIP 2009):
+ * for a dual field p = (p1, p2) with |p_j| <= 1 the primal point is
+ * x(p) = P_{>=0}(v - alpha grad^T p); a projected gradient step on the dual
+ * is p <- P_{|.|<=1}(r + grad x(r) / (8 alpha)) (|grad|^2 <= 8), with Nesterov
+ * extrapolation r = p_k + (t_k - 1)/t_{k+1} (p_k - p_{k-1}), starting from
+ * p = r = 0, t_1 = 1.  The result is x(p_N).  alpha = 0 or tv_inner = 0
+ * gives the projection P_{>=0}(v). */
+static void prox_tv_nonneg(const orc_desc *d, double alpha, const double *v, double *out) {
+  const int32_t n = d->n;
+  const int64_t np = n_pix(d);
+  if (!(alpha > 0.0) || d->tv_inner <= 0) {
+    for (int64_t p = 0; p < np; ++p) out[p] = v[p] > 0.0 ? v[p] : 0.0;
+    return;
+  }
+  double *p1 = dalloc(np), *p2 = dalloc(np), *q1 = dalloc(np), *q2 = dalloc(np);
+  double *r1 = dalloc(np), *r2 = dalloc(np), *x = dalloc(np), *dt = dalloc(np);
+  double *g1 = dalloc(np), *g2 = dalloc(np);
+  double t = 1.0;
+  for (int32_t k = 0; k < d->tv_inner; ++k) {
+    /* x(r) = P_{>=0}(v - alpha grad^T r) */
+    for (int64_t p = 0; p < np; ++p) dt[p] = 0.0;
+    grad_fwd_T(n, r1, r2, dt);
+    for (int64_t p = 0; p < np; ++p) {
+      const double u = v[p] - alpha * dt[p];
+      x[p] = u > 0.0 ? u : 0.0;
+    }
+    /* p_k = P(r + grad x / (8 alpha)) */
+    grad_fwd(n, x, g1, g2);
+    for (int64_t p = 0; p < np; ++p) {
+      q1[p] = p1[p];   /* p_{k-1} */
+      q2[p] = p2[p];
+      const double a = r1[p] + g1[p] / (8.0 * alpha);
+      const double b = r2[p] + g2[p] / (8.0 * alpha);
+      const double nrm = sqrt(a * a + b * b);
+      const double sc = nrm > 1.0 ? 1.0 / nrm : 1.0;
+      p1[p] = a * sc;
+      p2[p] = b * sc;
+    }
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const double beta = (t - 1.0) / tn;
+    for (int64_t p = 0; p < np; ++p) {
+      r1[p] = p1[p] + beta * (p1[p] - q1[p]);
+      r2[p] = p2[p] + beta * (p2[p] - q2[p]);
+    }
+    t = tn;
+  }
+  for (int64_t p = 0; p < np; ++p) dt[p] = 0.0;
+  grad_fwd_T(n, p1, p2, dt);
+  for (int64_t p = 0; p < np; ++p) {
+    const double u = v[p] - alpha * dt[p];
+    out[p] = u > 0.0 ? u : 0.0;
+  }
+  free(p1);
+  free(p2);
+  free(q1);
+  free(q2);
+  free(r1);
+  free(r2);
+  free(x);
+  free(dt);
+  free(g1);
+  free(g2);
+}
+
 /* prox_{tau R}(v) = argmin_x 1/2 |x - v|^2 + tau R(x).
  * Quadratic R: v / (1 + tau mu).
  * Quadratic + smoothed TV: exactly tv_inner FISTA steps (Beck & Teboulle) on
@@ -382,6 +460,10 @@ double orc_regulariser(const orc_desc *d, const double *x) {
  * with step 1/L_in, L_in = 1 + tau mu + 8 tau lambda / eps (|grad|^2 <= 8). */
 void orc_prox(const orc_desc *d, double tau, const double *v, double *out) {
   const int64_t np = n_pix(d);
+  if (d->reg == 2) {
+    prox_tv_nonneg(d, tau * d->tv_lambda, v, out);
+    return;
+  }
   if (d->reg != 1) {
     for (int64_t p = 0; p < np; ++p) out[p] = v[p] / (1.0 + tau * d->mu);
     return;
@@ -622,6 +704,49 @@ int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const d
   free(v);
   free(xn);
   free(yn);
+  return 0;
+}
+
+static void apply_Kbar(const orc_desc *d, const double *x, double *out);
+static void apply_KbarT(const orc_desc *d, const double *y, double *out);
+
+/* ------------------------------------------------------------------------ */
+/* PDHG (Chambolle & Pock 2011), the comparison method and x_nat generator of */
+/* Sec. 5.4, on min_x 1/2 |Kbar x - b|^2 + R(x) with Kbar = sum_l p_l K_l:     */
+/*   y+ = prox_{s f*}(y + s Kbar xbar) = (y + s Kbar xbar - s b) / (1 + s)     */
+/*   x+ = prox_{t R}(x - t Kbar^T y+),  xbar = x+ + theta (x+ - x).            */
+/* ------------------------------------------------------------------------ */
+
+/* The parameters printed with the comparison of Sec. 5.4 for a mu-strongly
+ * convex R: kappa = sqrt(1 + |K|^2 / (mu rho^2)), s = 1/(kappa - 1),
+ * t = 1/((kappa - 1) mu), theta = 1 - 2/(1 + kappa).  out = {s, t, theta}. */
+void orc_pdhg_params(double norm_K, double mu, double rho, double out[3]) {
+  const double kappa = sqrt(1.0 + norm_K * norm_K / (mu * rho * rho));
+  out[0] = 1.0 / (kappa - 1.0);
+  out[1] = 1.0 / ((kappa - 1.0) * mu);
+  out[2] = 1.0 - 2.0 / (1.0 + kappa);
+}
+
+int32_t orc_pdhg_run(const orc_desc *d, const double *b, int32_t iters, double s, double t,
+                     double theta, double *x, double *xbar, double *y) {
+  const int64_t np = n_pix(d), m = n_meas(d);
+  if (!(s > 0.0) || !(t > 0.0)) return 1;
+  double *kx = dalloc(m), *kty = dalloc(np), *v = dalloc(np), *xn = dalloc(np);
+  for (int32_t it = 0; it < iters; ++it) {
+    apply_Kbar(d, xbar, kx);
+    for (int64_t q = 0; q < m; ++q) y[q] = (y[q] + s * kx[q] - s * b[q]) / (1.0 + s);
+    apply_KbarT(d, y, kty);
+    for (int64_t p = 0; p < np; ++p) v[p] = x[p] - t * kty[p];
+    orc_prox(d, t, v, xn);
+    for (int64_t p = 0; p < np; ++p) {
+      xbar[p] = xn[p] + theta * (xn[p] - x[p]);
+      x[p] = xn[p];
+    }
+  }
+  free(kx);
+  free(kty);
+  free(v);
+  free(xn);
   return 0;
 }
 

@@ -41,7 +41,8 @@ typedef struct {
   double det_dist;      /* fan: centre to detector */
   int32_t levels;       /* r */
   const double *probs;  /* p_ell, ell = 0..r-1; NULL selects uniform 1/r */
-  int32_t reg;          /* 0: R = mu/2 |x|^2; 1: plus lambda * smoothed TV */
+  int32_t reg;          /* 0: R = mu/2 |x|^2; 1: plus lambda * smoothed TV;
+                           2: lambda * TV with x >= 0 (no quadratic term) */
   double mu;            /* strong convexity of R */
   double tv_lambda;     /* smoothed-TV weight */
   double tv_eps;        /* smoothed-TV epsilon */
@@ -106,6 +107,11 @@ int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const d
                               uint64_t seed, int64_t k0, int32_t iters, double *x, double *xbar,
                               double *y, double *phi, double *psi, double *snap,
                               double *psi_mean, int32_t *levels_dual, int32_t *levels_primal);
+
+/* ---- PDHG (Sec. 5.4 comparison, x_nat generator) on Kbar = sum_l p_l K_l ---- */
+void orc_pdhg_params(double norm_K, double mu, double rho, double out[3]);
+int32_t orc_pdhg_run(const orc_desc *d, const double *b, int32_t iters, double s, double t,
+                     double theta, double *x, double *xbar, double *y);
 
 /* ---- step-size theory (Sec. 3.4-3.6, Thm. 3) ---- */
 /* Power method on sum_l w_l K_l^T K_l (transposed=0, size d) or
