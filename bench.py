@@ -280,22 +280,27 @@ def variant_params(variant: str, dual_tables: int, draws: int) -> dict:
 
 
 VARIANT_SET = {
-    "alg7_seq": ("seq", 0, 0),
-    "snapshot_tables": ("alg1", 1, 0),
-    "independent_draws": ("alg1", 0, 1),
-    "alg7_seq_snapshot_tables": ("seq", 1, 0),
+    "alg7_seq": ("seq", 0, 0, {}),
+    "snapshot_tables": ("alg1", 1, 0, {}),
+    "independent_draws": ("alg1", 0, 1, {}),
+    "alg7_seq_snapshot_tables": ("seq", 1, 0, {}),
+    # TV with nonnegativity (Sec. 5.3), prox by 20 dual-FISTA steps
+    "tv_nonneg": ("alg1", 0, 0, {"reg": 2, "tv_inner": 20}),
 }
 
 
 def time_variants(imask, p, bt, info, iters, stream, flush, x, steps=3):
     """solves/s of each variant over `steps` solves (after one warm-up solve),
-    same workload, mu and (Alg. 1) sigma; Alg. 7 takes sigma = 0.05."""
+    same workload, mu and (Alg. 1) sigma; Alg. 7 takes sigma = 0.05; then the
+    per-iteration time of PDHG on the same sketched problem."""
     import torch
     out = {}
-    for name, (v, dt, dr) in VARIANT_SET.items():
+    for name, (v, dt, dr, extra) in VARIANT_SET.items():
         sigma = 0.05 if v == "seq" else info["sigma"]
+        if extra.get("reg") == 2:
+            extra = dict(extra, tv_lambda=0.02 * info["mu"])
         plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=sigma,
-                               **variant_params(v, dt, dr)))
+                               **variant_params(v, dt, dr), **extra))
         with torch.cuda.stream(stream):
             plan.solve(bt, 777, iters, out=x, stream=stream)
         ms = []
@@ -312,6 +317,20 @@ def time_variants(imask, p, bt, info, iters, stream, flush, x, steps=3):
         out[name] = {"solves_per_s": 1e3 * steps / float(sum(ms)), "sigma": sigma,
                      "ms_per_solve": float(np.mean(ms))}
         plan.close()
+    # PDHG (every level's K and K^T per iteration), printed parameters
+    plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
+    s_, t_, th_ = imask.imask_pdhg_params(info["L"] * math.sqrt(info["mu"]), info["mu"], 0.99)
+    n_it = 20
+    with torch.cuda.stream(stream):
+        plan.pdhg(bt, 2, s_, t_, th_, out=x, stream=stream)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.pdhg(bt, n_it, s_, t_, th_, out=x, stream=stream)
+        e.record(stream)
+    torch.cuda.synchronize()
+    out["pdhg"] = {"ms_per_iteration": a.elapsed_time(e) / n_it, "s": s_, "t": t_,
+                   "theta": th_, "note": "includes the per-call work-buffer allocation"}
+    plan.close()
     return out
 
 

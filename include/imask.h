@@ -65,7 +65,11 @@ typedef struct imask_state_s *imask_state_t; /* one solve: x, y, SAGA tables, co
  * source src_dist (cos, sin) to the bin centre -det_dist (cos, sin) +
  * offset (-sin, cos).  probs[ell] (NULL: uniform) are the p_ell of Alg. 1.
  * R(x) = mu/2 |x|^2 (reg 0) or mu/2 |x|^2 + tv_lambda sum sqrt(|grad x|^2 +
- * tv_eps^2) with forward differences (reg 1, prox by tv_inner FISTA steps).
+ * tv_eps^2) with forward differences (reg 1, prox by tv_inner FISTA steps),
+ * or tv_lambda sum |grad x| restricted to x >= 0 (reg 2, the non-smooth TV
+ * with nonnegativity of Sec. 5.3; prox by tv_inner steps of the fast gradient
+ * projection on the dual; no quadratic term, mu only scales the primal step
+ * sigma/mu -- the paper uses the TV weight itself there).
  * mu <= 0 picks mu = |K|^2 / 2.46^2; sigma <= 0 picks a step from power-method
  * estimates of L, Lbar, Lbar_p (Sec. 3.4-3.6) by step_rule: 0 the Thm. 3
  * optimum sigma*, 1 half of sigma*, 2 sigma_B = 1/(L^2 + 3 Lbar^2) (the comparison
@@ -94,7 +98,7 @@ typedef struct {
   double fov, det_spacing, angle_start, angle_span, src_dist, det_dist;
   int32_t levels;                        /* r, 1..8 */
   const double *probs;                   /* host array of r entries, or NULL */
-  int32_t reg;                           /* 0 quadratic, 1 quadratic + smoothed TV */
+  int32_t reg;                           /* 0 quadratic, 1 + smoothed TV, 2 TV, x >= 0 */
   double mu, tv_lambda, tv_eps;
   int32_t tv_inner;
   double sigma;
@@ -195,6 +199,22 @@ imask_status imask_state_destroy(imask_state_t state);
 /* Whole solve: state_create, iters steps, copy x to x_dev, destroy. */
 imask_status imask_solve(imask_plan_t plan, const float *b_dev, uint64_t seed, int32_t iters,
                          float *x_dev, void *stream);
+
+/* PDHG (Chambolle & Pock 2011), the comparison method of Sec. 5.4 and a
+ * generator of reference solutions, on the plan's sketched problem
+ * min_x 1/2 |Kbar x - b|^2 + R(x), Kbar = sum_l p_l K_l (= K for one level):
+ *   y+ = (y + s (Kbar xbar - b)) / (1 + s);  x+ = prox_{t R}(x - t Kbar^T y+);
+ *   xbar = x+ + theta (x+ - x), from x = xbar = y = 0.
+ * Every iteration applies every level's projector and back-projector.
+ * x_dev[n*n] receives x after iters iterations.  Allocates its work buffers
+ * with cudaMallocAsync on stream.  Errors: INVALID, OOM, CUDA. */
+imask_status imask_pdhg(imask_plan_t plan, const float *b_dev, int32_t iters, double s,
+                        double t, double theta, float *x_dev, void *stream);
+/* The PDHG parameters printed with that comparison (for a mu-strongly convex
+ * R): kappa = sqrt(1 + norm_K^2 / (mu rho^2)), s = 1/(kappa - 1),
+ * t = 1/((kappa - 1) mu), theta = 1 - 2/(1 + kappa); the paper uses rho = 0.99.
+ * out = {s, t, theta}.  Host only. */
+imask_status imask_pdhg_params(double norm_K, double mu, double rho, double out[3]);
 
 /* Metrics in FP64 on the device (synchronise; results on the host).
  * Objective of eq. min_obj_new: 1/2 |sum_l p_l K_l x - b|^2 + R(x). */

@@ -177,9 +177,11 @@ imask_status validate(const imask_desc *d) {
     }
     if (fabs(s - 1.0) > 1e-9) return fail(IMASK_ERR_INVALID, "probs sum to %.17g, not 1", s);
   }
-  if (d->reg != 0 && d->reg != 1) return fail(IMASK_ERR_INVALID, "reg must be 0 or 1");
+  if (d->reg < 0 || d->reg > 2) return fail(IMASK_ERR_INVALID, "reg must be 0, 1 or 2");
   if (d->reg == 1 && (!(d->tv_eps > 0.0) || d->tv_lambda < 0.0 || d->tv_inner < 0))
     return fail(IMASK_ERR_INVALID, "smoothed TV needs tv_eps > 0, tv_lambda >= 0, tv_inner >= 0");
+  if (d->reg == 2 && (!(d->tv_lambda >= 0.0) || d->tv_inner < 0))
+    return fail(IMASK_ERR_INVALID, "TV with nonnegativity needs tv_lambda >= 0, tv_inner >= 0");
   if (d->storage != 0) return fail(IMASK_ERR_INVALID, "only fp32 storage (0) is implemented");
   if (d->variant != 0 && d->variant != 1)
     return fail(IMASK_ERR_INVALID, "variant must be 0 (Alg. 1) or 1 (Alg. 7)");
@@ -359,6 +361,17 @@ DualArgs no_dual() {
   DualArgs d{};
   d.on = 0;
   return d;
+}
+
+// x <- prox_{tau R}(x) for the TV regularisers (x holds the prox input v);
+// work: 5 n^2 floats.
+cudaError_t launch_reg_prox(const imask_plan_s *p, float tau, float *x, float *work,
+                            cudaStream_t st) {
+  if (p->desc.reg == 1)
+    return launch_tv_prox(p->dp, tau, (float)p->mu, (float)p->desc.tv_lambda,
+                          (float)p->desc.tv_eps, p->desc.tv_inner, x, work, st);
+  return launch_tv_nonneg_prox(p->dp, tau * (float)p->desc.tv_lambda, p->desc.tv_inner, x, work,
+                               st);
 }
 
 // K_ell x -> sino using scratch pads (level index ell + 1 allocated).
@@ -970,14 +983,14 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
       const size_t nl = (size_t)p->dp.lg[l + 1].nl;
       o_snap[l] = cv.take(nl * nl);
     }
-  size_t o_xprev = (seq && p->desc.reg == 1) ? cv.take(d) : 0;
+  size_t o_xprev = (seq && p->desc.reg != 0) ? cv.take(d) : 0;
   size_t o_g = cv.take(p->gcap);
   size_t o_phic[IMASK_MAX_LEVELS] = {0};
   for (int l = 1; l < r; ++l) {
     const size_t nl = (size_t)p->dp.lg[l + 1].nl;
     o_phic[l] = cv.take(nl * nl);
   }
-  size_t o_tv = p->desc.reg == 1 ? cv.take(5 * d) : 0;
+  size_t o_tv = p->desc.reg != 0 ? cv.take(5 * d) : 0;
   size_t o_T[IMASK_MAX_LEVELS + 1] = {0}, o_R[IMASK_MAX_LEVELS + 1] = {0};
   for (int li = 1; li <= r; ++li) {
     o_T[li] = cv.take(pad_floats(p->dp.lg[li]));
@@ -1008,7 +1021,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   s->g = B + o_g;
   s->phic = B;
   for (int l = 1; l < r; ++l) s->phic_off[l] = (long long)o_phic[l];
-  s->tv = p->desc.reg == 1 ? B + o_tv : nullptr;
+  s->tv = p->desc.reg != 0 ? B + o_tv : nullptr;
   for (int li = 1; li <= r; ++li) {
     s->pads.T[li] = B + o_T[li];
     s->pads.R[li] = B + o_R[li];
@@ -1085,10 +1098,8 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
       ProfScope ps(2, lvl_x, st, prof);
       CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
     }
-    if (p->desc.reg == 1) {
-      CK(launch_tv_prox(P, tau, (float)p->mu, (float)p->desc.tv_lambda, (float)p->desc.tv_eps,
-                        p->desc.tv_inner, s->x, s->tv, st),
-         "TV prox launch");
+    if (p->desc.reg != 0) {
+      CK(launch_reg_prox(p, tau, s->x, s->tv, st), "TV prox launch");
       LevelSel nxt = sel;
       nxt.k = s->k + 1;
       ExtrapArgs ex{};
@@ -1165,6 +1176,82 @@ imask_status imask_rel_distance(int64_t n, const float *a_dev, const float *b_de
   return IMASK_OK;
 }
 
+imask_status imask_pdhg_params(double norm_K, double mu, double rho, double out[3]) {
+  if (!out) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (!(norm_K > 0.0) || !(mu > 0.0) || !(rho > 0.0 && rho <= 1.0))
+    return fail(IMASK_ERR_INVALID, "need norm_K > 0, mu > 0, 0 < rho <= 1");
+  const double kappa = sqrt(1.0 + norm_K * norm_K / (mu * rho * rho));
+  out[0] = 1.0 / (kappa - 1.0);
+  out[1] = 1.0 / ((kappa - 1.0) * mu);
+  out[2] = 1.0 - 2.0 / (1.0 + kappa);
+  return IMASK_OK;
+}
+
+imask_status imask_pdhg(imask_plan_t p, const float *b_dev, int32_t iters, double s_step,
+                        double t_step, double theta, float *x_dev, void *stream) {
+  if (!p || !b_dev || !x_dev) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (iters < 0) return fail(IMASK_ERR_INVALID, "iters < 0");
+  if (!(s_step > 0.0) || !(t_step > 0.0) || !isfinite(theta))
+    return fail(IMASK_ERR_INVALID, "PDHG needs s > 0, t > 0 and a finite theta");
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long d = p->dp.d, m = p->dp.m;
+  const int r = p->desc.levels;
+  Scratch sc;
+  unsigned mask = 0;
+  for (int li = 1; li <= r; ++li) mask |= 1u << li;
+  imask_status rc = scratch_alloc(p, mask, true, st, sc);
+  if (rc != IMASK_OK) return rc;
+  Carve cv;
+  const size_t o_x = cv.take(d), o_xb = cv.take(d), o_xn = cv.take(d), o_kty = cv.take(d),
+               o_ti = cv.take(d), o_y = cv.take(m), o_kx = cv.take(m), o_tm = cv.take(m),
+               o_tv = p->desc.reg != 0 ? cv.take(5 * d) : 0;
+  void *mem = nullptr;
+  cudaError_t e = cudaMallocAsync(&mem, cv.off * sizeof(float), st);
+  if (e != cudaSuccess) {
+    scratch_free(sc);
+    return cuda_fail(e, "cudaMallocAsync(pdhg)");
+  }
+  float *B = (float *)mem;
+  float *x = B + o_x, *xb = B + o_xb, *xn = B + o_xn, *kty = B + o_kty, *ti = B + o_ti;
+  float *y = B + o_y, *kx = B + o_kx, *tm = B + o_tm, *tv = p->desc.reg != 0 ? B + o_tv : nullptr;
+  const float s = (float)s_step, t = (float)t_step, th = (float)theta;
+  // quadratic prox folded into the extrapolation kernel's scale
+  const float scale = p->desc.reg == 0 ? (float)(1.0 / (1.0 + t_step * p->mu)) : 1.0f;
+  do {
+    if ((e = cudaMemsetAsync(mem, 0, cv.off * sizeof(float), st)) != cudaSuccess) break;
+    for (int it = 0; it < iters && rc == IMASK_OK && e == cudaSuccess; ++it) {
+      // y <- (y + s (Kbar xbar - b)) / (1 + s)
+      for (int l = 0; l < r && rc == IMASK_OK && e == cudaSuccess; ++l) {
+        rc = apply_K(p, l, xb, l == 0 ? kx : tm, sc, st);
+        if (rc != IMASK_OK) break;
+        e = l == 0 ? launch_scale(m, (float)p->probs[0], kx, st)
+                   : launch_axpy(m, (float)p->probs[l], tm, kx, st);
+      }
+      if (rc != IMASK_OK || e != cudaSuccess) break;
+      if ((e = launch_pdhg_dual(m, kx, b_dev, s, y, st)) != cudaSuccess) break;
+      // x+ = prox_{t R}(x - t Kbar^T y), xbar = x+ + theta (x+ - x)
+      for (int l = 0; l < r && rc == IMASK_OK && e == cudaSuccess; ++l) {
+        rc = apply_KT(p, l, y, l == 0 ? kty : ti, sc, st);
+        if (rc != IMASK_OK) break;
+        e = l == 0 ? launch_scale(d, (float)p->probs[0], kty, st)
+                   : launch_axpy(d, (float)p->probs[l], ti, kty, st);
+      }
+      if (rc != IMASK_OK || e != cudaSuccess) break;
+      if ((e = launch_copy(d, x, xn, st)) != cudaSuccess) break;
+      if ((e = launch_axpy(d, -t, kty, xn, st)) != cudaSuccess) break;
+      if (p->desc.reg != 0 && (e = launch_reg_prox(p, t, xn, tv, st)) != cudaSuccess) break;
+      e = launch_pdhg_primal(d, scale, th, xn, x, xb, st);
+    }
+    if (rc == IMASK_OK && e == cudaSuccess)
+      e = cudaMemcpyAsync(x_dev, x, d * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  } while (false);
+  cudaFreeAsync(mem, st);
+  scratch_free(sc);
+  if (rc != IMASK_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "pdhg");
+  return IMASK_OK;
+}
+
 imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_dev, double *out,
                              void *stream) {
   if (!p || !x_dev || !b_dev || !out) return fail(IMASK_ERR_INVALID, "NULL argument");
@@ -1195,9 +1282,9 @@ imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_
     if (rc != IMASK_OK || e != cudaSuccess) break;
     if ((e = launch_diff64(m, kx, b_dev, part, res, st)) != cudaSuccess) break;
     if ((e = launch_dot64(d, x_dev, x_dev, part, res + 2, st)) != cudaSuccess) break;
-    if (p->desc.reg == 1 &&
-        (e = launch_tv_value64(p->dp, x_dev, (float)p->desc.tv_eps, part, res + 3, st)) !=
-            cudaSuccess)
+    if (p->desc.reg != 0 &&
+        (e = launch_tv_value64(p->dp, x_dev, p->desc.reg == 1 ? (float)p->desc.tv_eps : 0.0f,
+                               part, res + 3, st)) != cudaSuccess)
       break;
     e = cudaMemcpyAsync(h, res, sizeof h, cudaMemcpyDeviceToHost, st);
   } while (false);
@@ -1206,8 +1293,9 @@ imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_
   if (rc != IMASK_OK) return rc;
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "objective");
-  double obj = 0.5 * h[0] + 0.5 * p->mu * h[2];
-  if (p->desc.reg == 1) obj += p->desc.tv_lambda * h[3];
+  // reg 2 has no quadratic term; its nonnegativity indicator is not evaluated
+  double obj = 0.5 * h[0] + (p->desc.reg == 2 ? 0.0 : 0.5 * p->mu * h[2]);
+  if (p->desc.reg != 0) obj += p->desc.tv_lambda * h[3];
   if (!isfinite(obj)) return fail(IMASK_ERR_NONFINITE, "objective is not finite");
   *out = obj;
   return IMASK_OK;

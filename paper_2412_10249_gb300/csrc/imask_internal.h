@@ -149,6 +149,12 @@ cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int wri
                           PadSet pads, cudaStream_t st);
 cudaError_t launch_tv_prox(const DevPlan &P, float tau, float mu, float lam, float eps, int inner,
                            float *x, float *work, cudaStream_t st);
+cudaError_t launch_tv_nonneg_prox(const DevPlan &P, float alpha, int inner, float *x, float *work,
+                                  cudaStream_t st);
+cudaError_t launch_pdhg_dual(long long m, const float *kx, const float *b, float s, float *y,
+                             cudaStream_t st);
+cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn, float *x,
+                               float *xbar, cudaStream_t st);
 cudaError_t launch_axpy(long long n, float alpha, const float *x, float *y, cudaStream_t st);
 cudaError_t launch_scale(long long n, float alpha, float *x, cudaStream_t st);
 cudaError_t launch_fill(long long n, float v, float *x, cudaStream_t st);

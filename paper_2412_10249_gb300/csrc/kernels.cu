@@ -873,6 +873,76 @@ __global__ void k_tv_step(int n, const float *__restrict__ v, float *__restrict_
 }
 
 // ---------------------------------------------------------------------------------
+// TV prox with nonnegativity: fast gradient projection on the dual (fixed step
+// count).  argmin_{x >= 0} 1/2|x - v|^2 + alpha |grad x|_{1,2};
+// x(r) = max(0, v - alpha grad^T r); p <- P_{|.|<=1}(r + grad x / (8 alpha));
+// r <- p + beta (p - p_old).
+// ---------------------------------------------------------------------------------
+__global__ void k_fgp_primal(int n, const float *__restrict__ v, const float *__restrict__ r1,
+                             const float *__restrict__ r2, float alpha, float *__restrict__ x) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)n * n) return;
+  const int i = (int)(p / n), j = (int)(p % n);
+  // transpose of the forward differences applied to (r1, r2)
+  float dt = 0.0f;
+  if (i + 1 < n) dt -= r1[p];
+  if (i >= 1) dt += r1[p - n];
+  if (j + 1 < n) dt -= r2[p];
+  if (j >= 1) dt += r2[p - 1];
+  x[p] = fmaxf(0.0f, fmaf(-alpha, dt, v[p]));
+}
+
+__global__ void k_fgp_dual(int n, const float *__restrict__ x, float inv8a, float beta,
+                           float *__restrict__ p1, float *__restrict__ p2, float *__restrict__ r1,
+                           float *__restrict__ r2) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)n * n) return;
+  const int i = (int)(p / n), j = (int)(p % n);
+  const float xp = x[p];
+  const float g1 = (i + 1 < n) ? x[p + n] - xp : 0.0f;
+  const float g2 = (j + 1 < n) ? x[p + 1] - xp : 0.0f;
+  const float a = fmaf(g1, inv8a, r1[p]);
+  const float b = fmaf(g2, inv8a, r2[p]);
+  const float nrm = sqrtf(fmaf(a, a, b * b));
+  const float sc = nrm > 1.0f ? 1.0f / nrm : 1.0f;
+  const float n1 = a * sc, n2 = b * sc;
+  const float o1 = p1[p], o2 = p2[p];
+  p1[p] = n1;
+  p2[p] = n2;
+  r1[p] = fmaf(beta, n1 - o1, n1);
+  r2[p] = fmaf(beta, n2 - o2, n2);
+}
+
+__global__ void k_relu(long long n, float *x) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] = fmaxf(0.0f, x[t]);
+}
+
+// ---------------------------------------------------------------------------------
+// PDHG helpers: dual prox of f = 1/2|. - b|^2 and the primal extrapolation.
+// ---------------------------------------------------------------------------------
+__global__ void k_pdhg_dual(long long m, const float *__restrict__ kx, const float *__restrict__ b,
+                            float s, float inv_1ps, float *__restrict__ y) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < m;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = fmaf(s, kx[t] - b[t], y[t]) * inv_1ps;
+}
+
+// xn holds x - t Kbar^T y on entry for the quadratic prox (scaled here) or
+// the prox result already; xbar = xn + theta (xn - x); x = xn.
+__global__ void k_pdhg_primal(long long d, float scale, float theta, float *__restrict__ xn,
+                              float *__restrict__ x, float *__restrict__ xbar) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < d;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float v = xn[t] * scale;
+    const float xo = x[t];
+    xbar[t] = fmaf(theta, v - xo, v);
+    x[t] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Elementwise helpers and FP64 reductions
 // ---------------------------------------------------------------------------------
 __global__ void k_levels(DevPlan P, unsigned long long seed, long long k0, long long n, int *out) {
@@ -1130,6 +1200,50 @@ cudaError_t launch_tv_prox(const DevPlan &P, float tau, float mu, float lam, flo
     count_launch();
     k_copy<<<grid_for(d, 256), 256, 0, st>>>(d, v, x);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tv_nonneg_prox(const DevPlan &P, float alpha, int inner, float *x, float *work,
+                                  cudaStream_t st) {
+  const long long d = (long long)P.n * P.n;
+  if (!(alpha > 0.0f) || inner <= 0) {
+    count_launch();
+    k_relu<<<grid_for(d, 256), 256, 0, st>>>(d, x);
+    return cudaGetLastError();
+  }
+  float *v = work, *p1 = work + d, *p2 = work + 2 * d, *r1 = work + 3 * d, *r2 = work + 4 * d;
+  const int blocks = (int)((d + 255) / 256);
+  count_launch();
+  k_copy<<<grid_for(d, 256), 256, 0, st>>>(d, x, v);
+  cudaError_t e = cudaMemsetAsync(p1, 0, 4 * d * sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  const float inv8a = 1.0f / (8.0f * alpha);
+  double t = 1.0;
+  for (int it = 0; it < inner; ++it) {
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const float beta = (float)((t - 1.0) / tn);
+    t = tn;
+    count_launch();
+    k_fgp_primal<<<blocks, 256, 0, st>>>(P.n, v, r1, r2, alpha, x);
+    count_launch();
+    k_fgp_dual<<<blocks, 256, 0, st>>>(P.n, x, inv8a, beta, p1, p2, r1, r2);
+  }
+  count_launch();
+  k_fgp_primal<<<blocks, 256, 0, st>>>(P.n, v, p1, p2, alpha, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pdhg_dual(long long m, const float *kx, const float *b, float s, float *y,
+                             cudaStream_t st) {
+  count_launch();
+  k_pdhg_dual<<<grid_for(m, 256), 256, 0, st>>>(m, kx, b, s, 1.0f / (1.0f + s), y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn, float *x,
+                               float *xbar, cudaStream_t st) {
+  count_launch();
+  k_pdhg_primal<<<grid_for(d, 256), 256, 0, st>>>(d, scale, theta, xn, x, xbar);
   return cudaGetLastError();
 }
 

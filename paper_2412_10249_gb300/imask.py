@@ -87,6 +87,9 @@ SIGNATURES = {
     "imask_solve": (_I32, [_VP, _VP, _U64, _I32, _VP, _VP]),
     "imask_objective": (_I32, [_VP, _VP, _VP, _DP, _VP]),
     "imask_rel_distance": (_I32, [_I64, _VP, _VP, _DP, _VP]),
+    "imask_pdhg": (_I32, [_VP, _VP, _I32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                          _VP, _VP]),
+    "imask_pdhg_params": (_I32, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]),
     "imask_profile_enable": (_I32, [_I32]),
     "imask_profile_read": (_I32, [_DP, _I64P, _I32]),
     "imask_launch_count": (_I64, []),
@@ -235,6 +238,12 @@ def imask_solve(plan, b, seed, iters, x, n, m, stream=None):
                              _stream(stream)))
 
 
+def imask_pdhg_params(norm_K: float, mu: float, rho: float = 0.99):
+    out = (ctypes.c_double * 3)()
+    _check(lib().imask_pdhg_params(norm_K, mu, rho, out))
+    return tuple(out)
+
+
 def imask_rel_distance(a, b, stream=None) -> float:
     out = ctypes.c_double()
     n = a.numel()
@@ -327,6 +336,14 @@ class Plan:
                                      _ptr(b, self.m, name="b"), ctypes.byref(out),
                                      _stream(stream)))
         return out.value
+
+    def pdhg(self, b: torch.Tensor, iters: int, s: float, t: float, theta: float,
+             out: torch.Tensor | None = None, stream=None):
+        if out is None:
+            out = torch.empty(self.n * self.n, device=b.device, dtype=torch.float32)
+        _check(lib().imask_pdhg(self.handle, _ptr(b, self.m, name="b"), iters, s, t, theta,
+                                _ptr(out, self.n * self.n, name="x"), _stream(stream)))
+        return out
 
     def state(self, b: torch.Tensor, seed: int, stream=None) -> "State":
         return State(self, b, seed, stream)

@@ -45,7 +45,7 @@ def test_every_declared_symbol_is_exported(imask):
     (dict(probs=[0.5, 0.6]), 1), (dict(geometry=2), 1), (dict(storage=1), 1),
     (dict(fov=-1.0), 1), (dict(n=4096), 2), (dict(variant=2), 1),
     (dict(variant=1, theta=float("nan")), 1), (dict(dual_tables=2), 1), (dict(draws=-1), 1),
-    (dict(step_rule=3), 1),
+    (dict(step_rule=3), 1), (dict(reg=3), 1), (dict(reg=2, tv_inner=-1), 1),
 ])
 def test_descriptor_validation_without_device(imask, bad, status):
     p = dict(n=64, n_angles=10, n_det=20, levels=2)
@@ -89,3 +89,12 @@ def test_host_step_solver_matches_oracle(imask, consts):
     got = imask.imask_optimal_step(*consts, 200)
     ref = Oracle.optimal_step(*consts, 200)
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0)
+
+
+def test_pdhg_params_match_oracle(imask):
+    for nk, mu, rho in ((2.46, 1.0, 0.99), (17.3, 0.4, 0.99), (1.0, 3.0, 0.5)):
+        got = imask.imask_pdhg_params(nk, mu, rho)
+        ref = Oracle.pdhg_params(nk, mu, rho)
+        np.testing.assert_allclose(got, ref, rtol=1e-15)
+    with pytest.raises(imask.ImaskError):
+        imask.imask_pdhg_params(1.0, 0.0, 0.99)
