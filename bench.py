@@ -426,6 +426,133 @@ def run_ablation(args):
 
 
 # ---------------------------------------------------------------------------------
+# batched solves (mixed slice sizes) through captured CUDA graphs
+# ---------------------------------------------------------------------------------
+def _sinogram_job(args):
+    p, seed = args
+    return inputs.sinogram(p, seed).ravel().astype(np.float32)
+
+
+def batch_sigma():
+    """Thm. 3 step for the normalised constants every slice shares (mu chosen so
+    that L = 2.46; uniform 4 levels give Lbar = L/2, Lbar_p = L)."""
+    from paper_2412_10249_gb300 import imask
+    return imask.imask_optimal_step(2.46, 1.23, 2.46, 0.25)[0]
+
+
+def run_batch(args):
+    """Mixed-size slices (side 256..1024, 180..1440 views, 1.5x side bins, fan
+    beam, 4 levels, 500 iterations, quadratic R): every slice solved one after
+    the other with plain launches, then all slices at once as one batch
+    (graph-captured pairs of iterations, one branch per slice)."""
+    import multiprocessing as mp
+    probs = inputs.slice_mix(args.batch_slices, seed=0)
+    # host-side inputs first, in a spawn pool (no CUDA context in the workers)
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 1)) as pool:
+        sinos = pool.map(_sinogram_job, [(p, 1000 + i) for i, p in enumerate(probs)])
+    import torch
+    from paper_2412_10249_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask
+    sigma = batch_sigma()
+    plans = {}
+    t0 = time.perf_counter()
+    for p in probs:
+        key = (p.n, p.n_angles)
+        if key not in plans:
+            plans[key] = imask.Plan(dict(p.params(), mu=0.0, sigma=sigma))
+    t_plans = time.perf_counter() - t0
+    bs = [torch.as_tensor(b, device="cuda") for b in sinos]
+    xs_plain = [torch.empty(p.d, device="cuda") for p in probs]
+    samples = 0.0
+    for i, p in enumerate(probs):
+        lv = plans[(p.n, p.n_angles)].levels(i, 0, args.iters).cpu().numpy()
+        samples += float(samples_per_iteration(p, lv).sum())
+    stream = torch.cuda.Stream()
+    # warm-up: one short solve per plan
+    with torch.cuda.stream(stream):
+        for key, pl in plans.items():
+            b = bs[[k for k, p in enumerate(probs) if (p.n, p.n_angles) == key][0]]
+            pl.solve(b, 0, 4, stream=stream)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with torch.cuda.stream(stream):
+        e[0].record(stream)
+        for i, p in enumerate(probs):
+            plans[(p.n, p.n_angles)].solve(bs[i], i, args.iters, out=xs_plain[i], stream=stream)
+        e[1].record(stream)
+    torch.cuda.synchronize()
+    states = [plans[(p.n, p.n_angles)].state(bs[i], i, stream=stream)
+              for i, p in enumerate(probs)]
+    batch = imask.Batch(states)
+    torch.cuda.synchronize()
+    launches0 = imask.imask_launch_count()
+    with torch.cuda.stream(stream):
+        e[2].record(stream)
+        batch.step(args.iters, stream=stream)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    launches = imask.imask_launch_count() - launches0
+    clk = clocks.stop()
+    t_plain = e[0].elapsed_time(e[1]) / 1e3
+    t_batch = e[2].elapsed_time(e[3]) / 1e3
+    worst = 0.0
+    for i, s in enumerate(states):
+        worst = max(worst, imask.imask_rel_distance(s.get(s.X), xs_plain[i]))
+    batch.close()
+    n = len(probs)
+    line = {"metric": "batched ImaSk solves/s (mixed slice sizes)", "unit": "solves/s",
+            "slices": n, "iters_per_solve": args.iters, "sigma": sigma,
+            "plain": {"value": n / t_plain, "seconds": t_plain,
+                      "gsamples_per_s": samples / t_plain / 1e9},
+            "batched": {"value": n / t_batch, "seconds": t_batch,
+                        "gsamples_per_s": samples / t_batch / 1e9,
+                        "includes": "graph capture and instantiation in the first call",
+                        "gpu_launches": int(launches)},
+            "speedup": t_plain / t_batch,
+            "max_rel_dist_sq_batched_vs_plain": worst,
+            "plan_setup_s": t_plans, "distinct_plans": len(plans),
+            "clocks": clk,
+            "config": {"workload": "mixed slices: side {256,384,512,768,1024}, views "
+                                   "{180,360,720,1080,1440}, bins 1.5 x side, fan beam, r=4, "
+                                   "K=500, quadratic R, mu = |K|^2/2.46^2 per plan"}}
+    print(json.dumps(line))
+    return 0
+
+
+def time_batch_fan512(imask, p, bt, info, iters, stream, n_states=8):
+    """n_states copies of the headline solve advanced as one batch."""
+    import torch
+    plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
+    warm = [plan.state(bt, 900 + i, stream=stream) for i in range(n_states)]
+    wb = imask.Batch(warm)
+    wb.step(4, stream=stream)
+    torch.cuda.synchronize()
+    wb.close()
+    for w in warm:
+        w.close()
+    states = [plan.state(bt, 950 + i, stream=stream) for i in range(n_states)]
+    batch = imask.Batch(states)
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        batch.step(iters, stream=stream)
+        e.record(stream)
+    torch.cuda.synchronize()
+    t = a.elapsed_time(e) / 1e3
+    batch.close()
+    for s in states:
+        s.close()
+    plan.close()
+    return {"states": n_states, "solves_per_s": n_states / t, "seconds": t,
+            "includes": "graph capture and instantiation"}
+
+
+# ---------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------# ---------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------
 def run_ours(args):
@@ -525,6 +652,7 @@ def run_ours(args):
     variants = None
     if not args.no_variants:
         variants = time_variants(imask, p, bt, info, args.iters, stream, flush, x)
+        variants["batch_fan512"] = time_batch_fan512(imask, p, bt, info, args.iters, stream)
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
@@ -589,6 +717,9 @@ def main():
     ap.add_argument("--ablation", action="store_true",
                     help="distance to the fixed point for the step sizes of Sec. 3.6 and Alg. 7")
     ap.add_argument("--ablation-seeds", type=int, default=3)
+    ap.add_argument("--batch", action="store_true",
+                    help="mixed-size slices: one after the other vs one graph-captured batch")
+    ap.add_argument("--batch-slices", type=int, default=64)
     ap.add_argument("--profile-period", type=int, default=8,
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
@@ -609,6 +740,8 @@ def main():
         return run_probe(args)
     if args.ablation:
         return run_ablation(args)
+    if args.batch:
+        return run_batch(args)
     return run_ours(args)
 
 

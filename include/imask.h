@@ -56,6 +56,7 @@ typedef enum {
 
 typedef struct imask_plan_s *imask_plan_t;   /* immutable geometry, levels, step size */
 typedef struct imask_state_s *imask_state_t; /* one solve: x, y, SAGA tables, counter */
+typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA graphs */
 
 /* Problem description.  Geometry (Sec. 4.1-4.2): parallel beam, or fan beam
  * with a flat detector.  View a is at angle angle_start + angle_span*a/n_angles.
@@ -185,8 +186,28 @@ imask_status imask_levels(imask_plan_t plan, uint64_t seed, int64_t k0, int64_t 
  * and copies b_dev[n_angles*n_det].  Allocates with cudaMallocAsync on stream. */
 imask_status imask_state_create(imask_plan_t plan, const float *b_dev, uint64_t seed,
                                 imask_state_t *state_out, void *stream);
-/* Advances the state by n_iters iterations of Alg. 1 on stream. */
+/* Advances the state by n_iters iterations (Alg. 1, or the plan's variant) on
+ * stream, one launch per kernel. */
 imask_status imask_step(imask_state_t state, int32_t n_iters, void *stream);
+
+/* Batches of independent solves (the paper has no counterpart; this is the
+ * batched form of the same iteration).  A batch holds n_states distinct
+ * states, of the same or of different plans.  imask_batch_step advances every
+ * state by n_iters iterations with the same result as imask_step on each:
+ * pairs of iterations of all states are captured once as one CUDA graph, each
+ * state on its own branch so that the solves overlap on the device, and the
+ * graph is replayed n_iters / 2 times on stream (the iteration counter is read
+ * from a device copy held by each state); an odd last iteration runs with
+ * plain launches.  The graph is captured again when a state's dual ping-pong
+ * parity differs from the captured one (after an odd number of steps).
+ * Capture happens inside the call, on a stream the batch owns (relaxed
+ * capture mode); the graph is then launched on `stream`, which may be the
+ * legacy default stream.  Profiling events are not recorded in graphs.
+ * Destroy a batch before its states.  Errors: INVALID, OOM, CUDA. */
+imask_status imask_batch_create(const imask_state_t *states, int32_t n_states,
+                                imask_batch_t *batch_out);
+imask_status imask_batch_step(imask_batch_t batch, int32_t n_iters, void *stream);
+imask_status imask_batch_destroy(imask_batch_t batch);
 /* Iteration counter k of the state (host value, no synchronisation). */
 int64_t imask_state_iteration(imask_state_t state);
 /* Copies a part of the state into dst_dev (float): what = 0 x[n*n], 1 y[m],

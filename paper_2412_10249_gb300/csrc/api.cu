@@ -139,6 +139,20 @@ struct imask_state_s {
   long long phic_off[IMASK_MAX_LEVELS] = {0};
   SnapArgs snap{};   // dual_tables = 1: sketched projector inputs per level
   PadSet pads{};
+  long long *k_dev = nullptr;   // device copy of k for graph replays
+  bool k_dev_stale = true;      // k advanced by eager launches since the last sync
+};
+
+struct imask_batch_s {
+  std::vector<imask_state_s *> states;
+  cudaStream_t origin = nullptr;       // capture origin (the legacy stream cannot capture)
+  std::vector<cudaStream_t> streams;   // capture branches, one per state
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> cur_at_capture;     // ping-pong parity the graph was captured for
+  int unroll = 0;                      // iterations per replay (even)
+  int64_t kernels_per_replay = 0;
 };
 
 namespace {
@@ -984,6 +998,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
       o_snap[l] = cv.take(nl * nl);
     }
   size_t o_xprev = (seq && p->desc.reg != 0) ? cv.take(d) : 0;
+  size_t o_kdev = cv.take(2);   // one 64-bit counter
   size_t o_g = cv.take(p->gcap);
   size_t o_phic[IMASK_MAX_LEVELS] = {0};
   for (int l = 1; l < r; ++l) {
@@ -1016,6 +1031,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
     for (int l = 0; l < r; ++l) s->snap.snap_off[l] = (long long)o_snap[l];
   }
   s->x_prev = o_xprev ? B + o_xprev : nullptr;
+  s->k_dev = (long long *)(B + o_kdev);
   s->phi0 = B + o_phi0;
   s->phi_mean = B + o_phim;
   s->g = B + o_g;
@@ -1037,11 +1053,14 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   return IMASK_OK;
 }
 
-imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
-  if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
-  if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
-  cudaStream_t st = (cudaStream_t)stream;
-  s->stream = st;
+namespace {
+
+// Enqueues one iteration of the state's algorithm on stream st, reading and
+// writing the dual iterate pair selected by `cur`.  graph: the kernels take the
+// iteration counter from the state's device counter plus k_add (for captured
+// graphs) and no profiling events are recorded; otherwise the counter is k.
+imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur, long long k,
+                               bool graph, int k_add) {
   const imask_plan_s *p = s->plan;
   const DevPlan &P = p->dp;
   const bool seq = p->desc.variant == 1;
@@ -1049,69 +1068,219 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
   const float inv_1ps = (float)(1.0 / (1.0 + p->sigma));
   const float tau = (float)(p->sigma / p->mu);
   const float theta = (float)p->desc.theta;
+  LevelSel sel{};
+  sel.fixed = -2;
+  sel.seed = s->seed;
+  sel.seed_x = s->seed_x;
+  sel.k = k;
+  sel.k_dev = graph ? s->k_dev : nullptr;
+  sel.k_add = k_add;
+  const bool prof = !graph && g_prof.on && g_prof.period > 0 && k % g_prof.period == 0;
+  const int lvl = prof ? lvl_host_draw(P, s->seed, k) : 0;
+  const int lvl_x = prof ? lvl_host_draw(P, s->seed_x, k) : 0;
+  // dual half: projector on the sketch of x^k (Alg. 1) or xbar^k (Alg. 7)
+  // prepared by the previous iteration, fused with the zeta and y updates
+  DualArgs D{};
+  D.on = 1;
+  D.y_in = s->y[cur];
+  D.y_out = s->y[1 - cur];
+  D.b = s->b;
+  D.psi = s->psi;
+  D.psi_mean = s->psi_mean;
+  D.sigma = sigma;
+  D.inv_1ps = inv_1ps;
+  {
+    ProfScope ps(0, lvl, st, prof);
+    CK(launch_fp(P, sel, s->pads, nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, st),
+       "projector launch");
+  }
+  // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
+  {
+    ProfScope ps(1, lvl_x, st, prof);
+    CK(launch_bp(P, sel, seq ? s->y[1 - cur] : s->y[cur], s->g, p->d_err, st),
+       "back-projector launch");
+  }
+  PrimalArgs A{};
+  A.g = s->g;
+  A.x = s->x;
+  A.phi0 = s->phi0;
+  A.phic = s->phic;
+  for (int l = 0; l < IMASK_MAX_LEVELS; ++l) A.phic_off[l] = s->phic_off[l];
+  A.phi_mean = s->phi_mean;
+  A.tau = tau;
+  A.inv_1ps = inv_1ps;
+  A.prox_in_place = p->desc.reg == 0 ? 1 : 0;
+  A.x_prev = p->desc.reg == 0 ? nullptr : s->x_prev;
+  A.extrapolate = seq ? 1 : 0;
+  A.theta = theta;
+  A.snap = s->snap;
+  {
+    ProfScope ps(2, lvl_x, st, prof);
+    CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
+  }
+  if (p->desc.reg != 0) {
+    CK(launch_reg_prox(p, tau, s->x, s->tv, st), "TV prox launch");
+    LevelSel nxt = sel;
+    nxt.k = k + 1;
+    nxt.k_add = k_add + 1;
+    ExtrapArgs ex{};
+    if (seq) {
+      ex.x_prev = s->x_prev;
+      ex.theta = theta;
+    }
+    CK(launch_sketch(P, nxt, s->x, s->pads, ex, s->snap, st), "sketch launch");
+  }
+  return IMASK_OK;
+}
+
+void batch_release_graph(imask_batch_s *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->cur_at_capture.clear();
+}
+
+// Captures `unroll` iterations of every state of the batch, each state on its
+// own branch, as one CUDA graph.
+imask_status batch_capture(imask_batch_s *b, int unroll) {
+  batch_release_graph(b);
+  cudaStream_t origin = b->origin;
+  const int64_t c0 = launch_counter();
+  CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed), "begin capture");
+  imask_status rc = IMASK_OK;
+  cudaError_t e = cudaEventRecord(b->fork, origin);
+  for (size_t i = 0; i < b->states.size() && e == cudaSuccess && rc == IMASK_OK; ++i) {
+    imask_state_s *s = b->states[i];
+    cudaStream_t bs = b->streams[i];
+    if ((e = cudaStreamWaitEvent(bs, b->fork, 0)) != cudaSuccess) break;
+    int cur = s->cur;
+    for (int u = 0; u < unroll && rc == IMASK_OK; ++u) {
+      rc = enqueue_iteration(s, bs, cur, 0, true, u);
+      cur = 1 - cur;
+    }
+    if (rc != IMASK_OK) break;
+    if ((e = launch_counter(s->k_dev, unroll, 0, bs)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(b->joins[i], bs)) != cudaSuccess) break;
+    e = cudaStreamWaitEvent(origin, b->joins[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+  const int64_t captured = launch_counter() - c0;
+  add_launches(-captured);   // captured, not run
+  if (rc != IMASK_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "graph capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_fail(e, "graph instantiate");
+  }
+  b->unroll = unroll;
+  b->kernels_per_replay = captured;
+  b->cur_at_capture.clear();
+  for (auto *s : b->states) b->cur_at_capture.push_back(s->cur);
+  return IMASK_OK;
+}
+
+}  // namespace
+
+imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
+  if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
+  if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  s->stream = st;
   for (int it = 0; it < n_iters; ++it) {
-    LevelSel sel{};
-    sel.fixed = -2;
-    sel.seed = s->seed;
-    sel.seed_x = s->seed_x;
-    sel.k = s->k;
-    const bool prof = g_prof.on && g_prof.period > 0 && s->k % g_prof.period == 0;
-    const int lvl = prof ? lvl_host_draw(P, s->seed, s->k) : 0;
-    const int lvl_x = prof ? lvl_host_draw(P, s->seed_x, s->k) : 0;
-    // dual half: projector on the sketch of x^k (Alg. 1) or xbar^k (Alg. 7)
-    // prepared by the previous iteration, fused with the zeta and y updates
-    DualArgs D{};
-    D.on = 1;
-    D.y_in = s->y[s->cur];
-    D.y_out = s->y[1 - s->cur];
-    D.b = s->b;
-    D.psi = s->psi;
-    D.psi_mean = s->psi_mean;
-    D.sigma = sigma;
-    D.inv_1ps = inv_1ps;
-    {
-      ProfScope ps(0, lvl, st, prof);
-      CK(launch_fp(P, sel, s->pads, nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, st),
-         "projector launch");
-    }
-    // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
-    {
-      ProfScope ps(1, lvl_x, st, prof);
-      CK(launch_bp(P, sel, seq ? s->y[1 - s->cur] : s->y[s->cur], s->g, p->d_err, st),
-         "back-projector launch");
-    }
-    PrimalArgs A{};
-    A.g = s->g;
-    A.x = s->x;
-    A.phi0 = s->phi0;
-    A.phic = s->phic;
-    for (int l = 0; l < IMASK_MAX_LEVELS; ++l) A.phic_off[l] = s->phic_off[l];
-    A.phi_mean = s->phi_mean;
-    A.tau = tau;
-    A.inv_1ps = inv_1ps;
-    A.prox_in_place = p->desc.reg == 0 ? 1 : 0;
-    A.x_prev = p->desc.reg == 0 ? nullptr : s->x_prev;
-    A.extrapolate = seq ? 1 : 0;
-    A.theta = theta;
-    A.snap = s->snap;
-    {
-      ProfScope ps(2, lvl_x, st, prof);
-      CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
-    }
-    if (p->desc.reg != 0) {
-      CK(launch_reg_prox(p, tau, s->x, s->tv, st), "TV prox launch");
-      LevelSel nxt = sel;
-      nxt.k = s->k + 1;
-      ExtrapArgs ex{};
-      if (seq) {
-        ex.x_prev = s->x_prev;
-        ex.theta = theta;
-      }
-      CK(launch_sketch(P, nxt, s->x, s->pads, ex, s->snap, st), "sketch launch");
-    }
+    imask_status rc = enqueue_iteration(s, st, s->cur, s->k, false, 0);
+    if (rc != IMASK_OK) return rc;
     s->cur = 1 - s->cur;
     s->k += 1;
+    s->k_dev_stale = true;
   }
+  return IMASK_OK;
+}
+
+imask_status imask_batch_create(const imask_state_t *states, int32_t n_states,
+                                imask_batch_t *batch_out) {
+  if (!states || !batch_out || n_states < 1) return fail(IMASK_ERR_INVALID, "bad argument");
+  *batch_out = nullptr;
+  for (int i = 0; i < n_states; ++i) {
+    if (!states[i]) return fail(IMASK_ERR_INVALID, "state %d is NULL", i);
+    for (int j = 0; j < i; ++j)
+      if (states[j] == states[i]) return fail(IMASK_ERR_INVALID, "state %d appears twice", i);
+  }
+  imask_batch_s *b = new (std::nothrow) imask_batch_s();
+  if (!b) return fail(IMASK_ERR_OOM, "host allocation");
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int i = 0; i < n_states && e == cudaSuccess; ++i) {
+    b->states.push_back(states[i]);
+    cudaStream_t bs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking)) != cudaSuccess) break;
+    b->streams.push_back(bs);
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) break;
+    b->joins.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    imask_batch_destroy(b);
+    return cuda_fail(e, "batch streams");
+  }
+  *batch_out = b;
+  return IMASK_OK;
+}
+
+imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
+  if (!b) return fail(IMASK_ERR_INVALID, "NULL batch");
+  if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int unroll = 2;
+  const int replays = n_iters / unroll;
+  if (replays > 0) {
+    // bring the device counters up to date with eager steps taken meanwhile
+    for (auto *s : b->states)
+      if (s->k_dev_stale) {
+        CK(launch_counter(s->k_dev, s->k, 1, st), "counter set");
+        s->k_dev_stale = false;
+      }
+    bool match = b->exec && b->unroll == unroll && b->cur_at_capture.size() == b->states.size();
+    for (size_t i = 0; match && i < b->states.size(); ++i)
+      match = b->cur_at_capture[i] == b->states[i]->cur;
+    if (!match) {
+      imask_status rc = batch_capture(b, unroll);
+      if (rc != IMASK_OK) return rc;
+    }
+    for (int r = 0; r < replays; ++r) {
+      CK(cudaGraphLaunch(b->exec, st), "graph launch");
+      add_launches(b->kernels_per_replay);
+    }
+    for (auto *s : b->states) {
+      s->k += (long long)replays * unroll;   // unroll is even: cur is unchanged
+      s->stream = st;
+    }
+  }
+  // the odd remainder runs eagerly, state by state
+  for (int it = replays * unroll; it < n_iters; ++it)
+    for (auto *s : b->states) {
+      imask_status rc = imask_step(s, 1, stream);
+      if (rc != IMASK_OK) return rc;
+    }
+  return IMASK_OK;
+}
+
+imask_status imask_batch_destroy(imask_batch_t b) {
+  if (!b) return IMASK_OK;
+  batch_release_graph(b);
+  for (auto st : b->streams) cudaStreamDestroy(st);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  for (auto ev : b->joins) cudaEventDestroy(ev);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
   return IMASK_OK;
 }
 

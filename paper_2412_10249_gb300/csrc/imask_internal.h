@@ -77,11 +77,15 @@ struct PadSet {
 // level is drawn on the device from (seed, k) for the projector side and from
 // (seed_x, k) for the back-projector / image side (seed_x = seed unless the
 // primal and dual levels are drawn independently).
+// The iteration counter is k, or *k_dev + k_add when k_dev is set (a
+// device-resident counter, so that captured CUDA graphs can be replayed).
 struct LevelSel {
   int fixed;
   unsigned long long seed;
   unsigned long long seed_x;
   long long k;
+  const long long *k_dev;
+  int k_add;
 };
 
 // Snapshot form of the measurement-side tables: per level the sketched
@@ -156,6 +160,8 @@ cudaError_t launch_pdhg_dual(long long m, const float *kx, const float *b, float
 cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn, float *x,
                                float *xbar, cudaStream_t st);
 cudaError_t launch_axpy(long long n, float alpha, const float *x, float *y, cudaStream_t st);
+// *k_dev += delta (one thread), or *k_dev = value when set_value != 0
+cudaError_t launch_counter(long long *k_dev, long long delta, int set_value, cudaStream_t st);
 cudaError_t launch_scale(long long n, float alpha, float *x, cudaStream_t st);
 cudaError_t launch_fill(long long n, float v, float *x, cudaStream_t st);
 cudaError_t launch_copy(long long n, const float *x, float *y, cudaStream_t st);
@@ -170,4 +176,5 @@ int reduce_blocks();
 long long fp_smem_bytes();
 int64_t launch_counter();
 void count_launch();
+void add_launches(int64_t n);   // may be negative (captured launches that did not run)
 }

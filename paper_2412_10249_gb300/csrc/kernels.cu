@@ -46,14 +46,19 @@ __host__ __device__ __forceinline__ int draw_level(const DevPlan &P, unsigned lo
   return l;
 }
 
+// Iteration counter of a launch.
+__device__ __forceinline__ long long sel_k(const LevelSel &s) {
+  return s.k_dev ? *s.k_dev + s.k_add : s.k;
+}
+
 // Projector-side (dual) level of a launch.
 __device__ __forceinline__ int sel_level(const DevPlan &P, const LevelSel &s) {
-  return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed, s.k);
+  return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed, sel_k(s));
 }
 
 // Back-projector / image-side (primal) level of a launch.
 __device__ __forceinline__ int sel_level_x(const DevPlan &P, const LevelSel &s) {
-  return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed_x, s.k);
+  return s.fixed >= -1 ? s.fixed : draw_level(P, s.seed_x, sel_k(s));
 }
 
 // ---------------------------------------------------------------------------------
@@ -828,7 +833,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
   }
   if (!write_sketch) return;
   __syncthreads();
-  const int elln = draw_level(P, sel.seed, sel.k + 1);
+  const int elln = draw_level(P, sel.seed, sel_k(sel) + 1);
   float *S = A.snap.snap ? A.snap.snap + A.snap.snap_off[elln] : nullptr;
   sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0, S);
 }
@@ -951,6 +956,10 @@ __global__ void k_levels(DevPlan P, unsigned long long seed, long long k0, long 
     out[t] = draw_level(P, seed, k0 + t);
 }
 
+__global__ void k_counter(long long *k, long long delta, int set_value) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *k = set_value ? delta : *k + delta;
+}
+
 __global__ void k_axpy(long long n, float a, const float *__restrict__ x, float *__restrict__ y) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
        t += (long long)gridDim.x * blockDim.x)
@@ -1061,6 +1070,7 @@ inline int upd_smem_bytes(const DevPlan &P) {
 // ===================================================================================
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 int64_t launch_counter() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int reduce_blocks() { return kRedBlocks; }
 long long fp_smem_bytes() { return (long long)FP_STAGES * FP_STAGE_FLOATS * (long long)sizeof(float); }
 
@@ -1244,6 +1254,12 @@ cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn,
                                float *xbar, cudaStream_t st) {
   count_launch();
   k_pdhg_primal<<<grid_for(d, 256), 256, 0, st>>>(d, scale, theta, xn, x, xbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counter(long long *k_dev, long long delta, int set_value, cudaStream_t st) {
+  count_launch();
+  k_counter<<<1, 32, 0, st>>>(k_dev, delta, set_value);
   return cudaGetLastError();
 }
 

@@ -87,6 +87,9 @@ SIGNATURES = {
     "imask_solve": (_I32, [_VP, _VP, _U64, _I32, _VP, _VP]),
     "imask_objective": (_I32, [_VP, _VP, _VP, _DP, _VP]),
     "imask_rel_distance": (_I32, [_I64, _VP, _VP, _DP, _VP]),
+    "imask_batch_create": (_I32, [_VP, _I32, _VP]),
+    "imask_batch_step": (_I32, [_VP, _I32, _VP]),
+    "imask_batch_destroy": (_I32, [_VP]),
     "imask_pdhg": (_I32, [_VP, _VP, _I32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                           _VP, _VP]),
     "imask_pdhg_params": (_I32, [ctypes.c_double, ctypes.c_double, ctypes.c_double, _DP]),
@@ -378,6 +381,32 @@ class State:
     def close(self):
         if self.handle:
             _check(lib().imask_state_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent states advanced together through captured CUDA graphs."""
+
+    def __init__(self, states):
+        self.states = list(states)
+        arr = (ctypes.c_void_p * len(self.states))(*[st.handle.value for st in self.states])
+        h = ctypes.c_void_p()
+        _check(lib().imask_batch_create(arr, len(self.states), ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, n_iters: int, stream=None):
+        _check(lib().imask_batch_step(self.handle, n_iters, _stream(stream)))
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().imask_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -205,6 +205,35 @@ def poisson_log(b: np.ndarray, i0: float, seed: int) -> np.ndarray:
     return -np.log(np.maximum(counts, 1) / i0)
 
 
+def sinogram(p: Problem, seed: int, noise: str = "auto") -> np.ndarray:
+    """The noisy sinogram of ``measurements`` without rasterising the phantom."""
+    n_e = 16 if p.n >= 1024 else 10
+    clean = ellipse_sinogram(random_ellipses(seed, n_e, p.fov), p)
+    if noise == "auto":
+        noise = "gauss" if p.geometry == 0 else "poisson"
+    if noise == "gauss":
+        return gaussian_noise(clean, 0.01, seed + 1)
+    if noise == "poisson":
+        return poisson_log(clean, 1e4, seed + 1)
+    return clean
+
+
+def slice_mix(n_slices: int, seed: int):
+    """Mixed-size fan-beam slices: side from {256, 384, 512, 768, 1024}, view
+    count from {180, 360, 720, 1080, 1440} (uniform draws), 1.5 x side bins,
+    geometry as the 512x512 workload (source 2W, detector 1W, 2 pi), 4 levels."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sides = [256, 384, 512, 768, 1024]
+    views = [180, 360, 720, 1080, 1440]
+    out = []
+    for _ in range(n_slices):
+        n = int(sides[rng.integers(len(sides))])
+        na = int(views[rng.integers(len(views))])
+        out.append(Problem(n=n, n_angles=na, n_det=3 * n // 2, geometry=1,
+                           angle_span=2 * math.pi, src_dist=2.0, det_dist=1.0, levels=4))
+    return out
+
+
 def measurements(p: Problem, seed: int, noise: str = "auto"):
     """(phantom image, noisy sinogram b, clean sinogram) for problem ``p``."""
     e, img = phantom(seed, p.n, p.fov)

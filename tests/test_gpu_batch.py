@@ -1,0 +1,117 @@
+"""Batched stepping through captured CUDA graphs: identical to plain stepping,
+state by state, for mixed plans, variants, odd counts and interleaved calls."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle
+from paper_2412_10249_gb300 import build as pkg_build
+from paper_2412_10249_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def imask():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask as m
+    m.lib()
+    return m
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32).ravel(), device="cuda")
+
+
+FAN64 = inputs.Problem(n=64, n_angles=90, n_det=96, geometry=1, angle_span=2 * math.pi,
+                       levels=4)
+PAR40 = inputs.Problem(n=40, n_angles=36, n_det=61, geometry=0, angle_span=math.pi, levels=3)
+TV64 = inputs.small_problem()
+
+
+def _setups(imask):
+    """(plan, b) pairs covering Alg. 1, Alg. 7, snapshot tables, independent
+    draws and a TV prox (extra launches inside the iteration)."""
+    out = []
+    for prob, extra in ((FAN64, {}), (PAR40, dict(variant=1, theta=1.0, dual_tables=1)),
+                        (FAN64, dict(draws=1, dual_tables=1)),
+                        (TV64, dict(reg=1, tv_lambda=0.02, variant=1, theta=0.7))):
+        plan = imask.Plan(dict(prob.params(), mu=0.1, sigma=0.04, **extra))
+        _, b, _ = inputs.measurements(prob, seed=len(out), noise="none")
+        out.append((plan, cuda(b)))
+    return out
+
+
+def test_batch_equals_plain_steps(imask):
+    setups = _setups(imask)
+    ref = []
+    for i, (plan, b) in enumerate(setups):
+        s = plan.state(b, 100 + i)
+        s.step(20)
+        ref.append(s.get(s.X))
+    states = [plan.state(b, 100 + i) for i, (plan, b) in enumerate(setups)]
+    batch = imask.Batch(states)
+    batch.step(20)
+    torch.cuda.synchronize()
+    for s, r in zip(states, ref):
+        assert s.k == 20
+        assert torch.equal(s.get(s.X), r)
+    batch.close()
+
+
+def test_batch_mixed_with_plain_and_odd_counts(imask):
+    setups = _setups(imask)[:3]
+    ref = []
+    for i, (plan, b) in enumerate(setups):
+        s = plan.state(b, 7 + i)
+        s.step(31)
+        ref.append((s.get(s.X), s.get(s.Y)))
+    states = [plan.state(b, 7 + i) for i, (plan, b) in enumerate(setups)]
+    states[0].step(3)          # parities differ across the batch
+    batch = imask.Batch(states)
+    batch.step(9)              # 4 replays + one plain iteration each
+    for s in states[1:]:
+        s.step(3)
+    batch.step(16)
+    states[0].step(3)
+    for s in states[1:]:
+        s.step(3)
+    torch.cuda.synchronize()
+    for s, (rx, ry) in zip(states, ref):
+        assert s.k == 31
+        assert torch.equal(s.get(s.X), rx)
+        assert torch.equal(s.get(s.Y), ry)
+    batch.close()
+
+
+def test_batch_matches_oracle(imask):
+    prob = FAN64
+    params = dict(prob.params(), mu=0.1, sigma=0.04, variant=1, theta=1.0)
+    _, b, _ = inputs.measurements(prob, seed=3, noise="none")
+    o = Oracle(**dict(prob.params(), mu=0.1, sigma=0.04))
+    st, _, _ = o.run_variant(b.ravel(), 5, 24, sequential=True)
+    plan = imask.Plan(params)
+    s = plan.state(cuda(b), 5)
+    batch = imask.Batch([s])
+    batch.step(24)
+    x = s.get(s.X).double().cpu().numpy()
+    assert np.linalg.norm(x - st["x"]) / np.linalg.norm(st["x"]) <= 1e-4
+    batch.close()
+
+
+def test_batch_counts_replayed_launches(imask):
+    plan = imask.Plan(dict(FAN64.params(), mu=0.1, sigma=0.04))
+    _, b, _ = inputs.measurements(FAN64, seed=1, noise="none")
+    states = [plan.state(cuda(b), i) for i in range(3)]
+    batch = imask.Batch(states)
+    batch.step(2)     # capture
+    torch.cuda.synchronize()
+    c0 = imask.imask_launch_count()
+    batch.step(10)
+    torch.cuda.synchronize()
+    # per state and pair of iterations: 2 x (projector, back-projector, update) + counter
+    assert imask.imask_launch_count() - c0 == 5 * 3 * 7
+    batch.close()
