@@ -551,6 +551,63 @@ def time_batch_fan512(imask, p, bt, info, iters, stream, n_states=8):
 
 
 # ---------------------------------------------------------------------------------
+# serving: Poisson arrivals, continuous batching under a device-memory budget
+# ---------------------------------------------------------------------------------
+def run_serve(args):
+    import torch
+    from paper_2412_10249_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2412_10249_gb300 import serve
+    reqs = []
+    problems = {}
+    offered = 0.0
+    for i, (t, p, iters, seed) in enumerate(inputs.serving_requests(args.serve_seconds,
+                                                                     args.serve_rate, seed=0)):
+        problems[i] = p
+        def make_b(p=p, seed=seed):
+            return inputs.poisson_log(inputs.disk_sinogram(p), 1e4, seed)
+        reqs.append(serve.Request(rid=i, params=p.params(), b=make_b, iters=iters,
+                                  seed=seed, arrival=t))
+        offered += expected_samples_per_solve(p, iters)
+    srv = serve.Server(budget_bytes=int(args.serve_budget_gb * (1 << 30)),
+                       max_active=args.serve_slots, max_queue=args.serve_queue,
+                       quantum=10, power_iters=20)
+    clocks = ClockSampler(0)
+    clocks.start()
+    st = srv.run(reqs, duration=args.serve_seconds, drain=False)
+    clk = clocks.stop()
+    done = [r for r in reqs if r.status == "done"]
+    achieved = sum(expected_samples_per_solve(problems[r.rid], r.iters) for r in done)
+    lat = np.array(st.latencies) * 1e3
+    wait = np.array(st.waits) * 1e3
+    T = args.serve_seconds
+    line = {"metric": "served ImaSk solves/s (Poisson arrivals, continuous batching)",
+            "unit": "solves/s", "value": len(done) / T, "seconds": T,
+            "offered": {"requests": len(reqs), "rate_per_s": args.serve_rate,
+                        "gsamples_per_s": offered / T / 1e9},
+            "achieved_gsamples_per_s": achieved / T / 1e9,
+            "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
+            "queue_wait_p50_ms": float(np.percentile(wait, 50)) if wait.size else None,
+            "completed": st.completed, "admitted": st.admitted,
+            "rejected_queue_full": st.rejected_queue_full,
+            "rejected_too_large": st.rejected_too_large,
+            "unfinished_at_end": len(srv.active) + len(srv.queue),
+            "failed": st.failed, "failed_plans": [[list(k), e] for k, e in st.failed_plans[:5]],
+            "max_active": st.max_active, "peak_gb": st.peak_bytes / (1 << 30),
+            "plans_built": st.plans_built, "plan_seconds": st.plan_seconds,
+            "clocks": clk,
+            "config": {"workload": "serving: Poisson arrivals, r in {2..6}, side log-uniform "
+                                   "[128, 2048], views [180, 2048], bins 1.5 x side, fan beam, "
+                                   "K in [100, 1000]; centred-disk sinograms with Poisson "
+                                   "noise", "budget_gb": args.serve_budget_gb,
+                       "slots": args.serve_slots, "queue": args.serve_queue, "quantum": 10}}
+    srv.close()
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------# ---------------------------------------------------------------------------------
 # our arm
@@ -720,6 +777,13 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="mixed-size slices: one after the other vs one graph-captured batch")
     ap.add_argument("--batch-slices", type=int, default=64)
+    ap.add_argument("--serve", action="store_true",
+                    help="Poisson-arrival serving run with continuous batching")
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=64.0)
+    ap.add_argument("--serve-slots", type=int, default=16)
+    ap.add_argument("--serve-queue", type=int, default=64)
     ap.add_argument("--profile-period", type=int, default=8,
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
@@ -742,6 +806,8 @@ def main():
         return run_ablation(args)
     if args.batch:
         return run_batch(args)
+    if args.serve:
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -109,6 +109,7 @@ typedef struct {
   int32_t dual_tables;                   /* 0 K_l x tables, 1 input snapshots */
   int32_t draws;                         /* 0 common level, 1 independent primal/dual */
   int32_t step_rule;                     /* sigma <= 0: 0 sigma*, 1 half, 2 sigma_B */
+  int32_t power_iters;                   /* power-method iterations; 0 picks 100 */
 } imask_desc;
 
 /* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,
@@ -119,6 +120,8 @@ typedef struct {
   int64_t n_meas, n_pix;
   int32_t levels, n_xmajor_views_split; /* views whose rays change major axis */
   int64_t n_xmajor_rays;
+  int64_t state_bytes;                  /* device bytes one imask_state_create allocates */
+  int64_t plan_bytes;                   /* device bytes the plan holds */
 } imask_plan_info;
 
 /* Creates a plan: validates the descriptor, builds the per-ray geometry tables

@@ -206,6 +206,8 @@ imask_status validate(const imask_desc *d) {
   if (d->draws != 0 && d->draws != 1) return fail(IMASK_ERR_INVALID, "draws must be 0 or 1");
   if (d->step_rule < 0 || d->step_rule > 2)
     return fail(IMASK_ERR_INVALID, "step_rule must be 0, 1 or 2");
+  if (d->power_iters < 0 || d->power_iters > 100000)
+    return fail(IMASK_ERR_INVALID, "power_iters must be in [0, 100000]");
   if (d->geometry == 1) {
     if (!(d->src_dist > 0.5 * d->fov * 1.4142135623730951))
       return fail(IMASK_ERR_INVALID, "fan source must lie outside the field of view");
@@ -496,7 +498,7 @@ imask_status plan_constants(imask_plan_s *p, cudaStream_t st) {
   if (p->desc.variant == 1 && !(p->sigma > 0.0)) p->sigma = 0.05;
   const bool need_sigma = !(p->sigma > 0.0);
   if (!need_mu && !need_sigma) return IMASK_OK;
-  const int iters = 100;
+  const int iters = p->desc.power_iters > 0 ? p->desc.power_iters : 100;
   const long long d = p->dp.d, m = p->dp.m;
   Scratch s;
   unsigned mask = 0;
@@ -569,6 +571,54 @@ imask_status plan_constants(imask_plan_s *p, cudaStream_t st) {
   }
   if (rc == IMASK_OK && !(p->sigma > 0.0)) rc = fail(IMASK_ERR_INVALID, "no admissible step size");
   return rc;
+}
+
+}  // namespace
+
+namespace {
+
+// Float offsets of the parts of a state's single device allocation.
+struct StateLayout {
+  size_t x = 0, y0 = 0, y1 = 0, b = 0, psi = 0, psim = 0, phi0 = 0, phim = 0, xprev = 0, kdev = 0,
+         g = 0, tv = 0, total = 0;
+  size_t snap[IMASK_MAX_LEVELS] = {0}, phic[IMASK_MAX_LEVELS] = {0};
+  size_t T[IMASK_MAX_LEVELS + 1] = {0}, R[IMASK_MAX_LEVELS + 1] = {0};
+};
+
+StateLayout state_layout(const imask_plan_s *p) {
+  StateLayout L;
+  const int r = p->desc.levels;
+  const size_t d = p->dp.d, m = p->dp.m;
+  const bool snapshots = p->desc.dual_tables == 1;
+  const bool seq = p->desc.variant == 1;
+  Carve cv;
+  L.x = cv.take(d);   // first: offset 0 marks "absent" for the optional parts below
+  L.y0 = cv.take(m);
+  L.y1 = cv.take(m);
+  L.b = cv.take(m);
+  L.psi = snapshots ? 0 : cv.take(m * r);
+  L.psim = cv.take(m);
+  L.phi0 = cv.take(d);
+  L.phim = cv.take(d);
+  if (snapshots)
+    for (int l = 0; l < r; ++l) {
+      const size_t nl = (size_t)p->dp.lg[l + 1].nl;
+      L.snap[l] = cv.take(nl * nl);
+    }
+  L.xprev = (seq && p->desc.reg != 0) ? cv.take(d) : 0;
+  L.kdev = cv.take(2);   // one 64-bit counter
+  L.g = cv.take(p->gcap);
+  for (int l = 1; l < r; ++l) {
+    const size_t nl = (size_t)p->dp.lg[l + 1].nl;
+    L.phic[l] = cv.take(nl * nl);
+  }
+  L.tv = p->desc.reg != 0 ? cv.take(5 * d) : 0;
+  for (int li = 1; li <= r; ++li) {
+    L.T[li] = cv.take(pad_floats(p->dp.lg[li]));
+    L.R[li] = cv.take(pad_floats(p->dp.lg[li]));
+  }
+  L.total = cv.off;
+  return L;
 }
 
 }  // namespace
@@ -808,13 +858,26 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
     imask_plan_destroy(p);
     return cuda_fail(e, "cudaMalloc(plan)");
   }
-  if ((e = cudaMemcpy(p->d_rays, rays.data(), rays.size() * sizeof(float4),
-                      cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(p->d_rays_lo, rays_lo.data(), rays_lo.size() * sizeof(float2),
-                      cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(p->d_views, views.data(), views.size() * sizeof(ViewInfo),
-                      cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemset(p->d_err, 0, sizeof(unsigned int))) != cudaSuccess) {
+  // Every upload and every launch of the plan's set-up goes to one
+  // non-blocking stream, which is synchronised before the plan is returned:
+  // a copy on the legacy stream would not be ordered before work on a
+  // non-blocking stream, and a pageable cudaMemcpy may return before its
+  // transfer has landed.
+  cudaStream_t st = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
+    imask_plan_destroy(p);
+    return cuda_fail(e, "cudaStreamCreate");
+  }
+  if ((e = cudaMemcpyAsync(p->d_rays, rays.data(), rays.size() * sizeof(float4),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p->d_rays_lo, rays_lo.data(), rays_lo.size() * sizeof(float2),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p->d_views, views.data(), views.size() * sizeof(ViewInfo),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), st)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
     imask_plan_destroy(p);
     return cuda_fail(e, "upload plan");
   }
@@ -822,14 +885,10 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.rays_lo = p->d_rays_lo;
   dp.views = p->d_views;
 
-  cudaStream_t st = nullptr;
-  if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess) {
-    imask_plan_destroy(p);
-    return cuda_fail(e, "cudaStreamCreate");
-  }
   rc = plan_constants(p, st);
-  cudaStreamSynchronize(st);
+  e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
+  if (rc == IMASK_OK && e != cudaSuccess) rc = cuda_fail(e, "plan set-up");
   if (rc != IMASK_OK) {
     imask_plan_destroy(p);
     return rc;
@@ -864,6 +923,9 @@ imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
   info->levels = p->desc.levels;
   info->n_xmajor_views_split = p->n_split_views;
   info->n_xmajor_rays = p->dp.m_x;
+  info->state_bytes = (int64_t)(state_layout(p).total * sizeof(float));
+  info->plan_bytes = (int64_t)(p->dp.m * (sizeof(float4) + sizeof(float2)) +
+                               p->dp.n_angles * sizeof(ViewInfo) + sizeof(unsigned int));
   return IMASK_OK;
 }
 
@@ -882,7 +944,9 @@ imask_status imask_plan_check(imask_plan_t p) {
   unsigned int flag = 0;
   CK(cudaMemcpy(&flag, p->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
   if (flag) {
+    // cleared before returning, so no later launch can race with the reset
     cudaMemset(p->d_err, 0, sizeof flag);
+    cudaDeviceSynchronize();
     return fail(IMASK_ERR_TIMEOUT, "a projector launch gave up waiting for its image strips");
   }
   return IMASK_OK;
@@ -984,33 +1048,15 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   s->seed = seed;
   s->stream = st;
   const int r = p->desc.levels;
-  const size_t d = p->dp.d, m = p->dp.m;
-  Carve cv;
+  const size_t m = p->dp.m;
   const bool snapshots = p->desc.dual_tables == 1;
-  const bool seq = p->desc.variant == 1;
-  size_t o_x = cv.take(d), o_y0 = cv.take(m), o_y1 = cv.take(m), o_b = cv.take(m);
-  size_t o_psi = snapshots ? 0 : cv.take(m * r);
-  size_t o_psim = cv.take(m), o_phi0 = cv.take(d), o_phim = cv.take(d);
-  size_t o_snap[IMASK_MAX_LEVELS] = {0};
-  if (snapshots)
-    for (int l = 0; l < r; ++l) {
-      const size_t nl = (size_t)p->dp.lg[l + 1].nl;
-      o_snap[l] = cv.take(nl * nl);
-    }
-  size_t o_xprev = (seq && p->desc.reg != 0) ? cv.take(d) : 0;
-  size_t o_kdev = cv.take(2);   // one 64-bit counter
-  size_t o_g = cv.take(p->gcap);
-  size_t o_phic[IMASK_MAX_LEVELS] = {0};
-  for (int l = 1; l < r; ++l) {
-    const size_t nl = (size_t)p->dp.lg[l + 1].nl;
-    o_phic[l] = cv.take(nl * nl);
-  }
-  size_t o_tv = p->desc.reg != 0 ? cv.take(5 * d) : 0;
-  size_t o_T[IMASK_MAX_LEVELS + 1] = {0}, o_R[IMASK_MAX_LEVELS + 1] = {0};
-  for (int li = 1; li <= r; ++li) {
-    o_T[li] = cv.take(pad_floats(p->dp.lg[li]));
-    o_R[li] = cv.take(pad_floats(p->dp.lg[li]));
-  }
+  const StateLayout L = state_layout(p);
+  const size_t o_x = L.x, o_y0 = L.y0, o_y1 = L.y1, o_b = L.b, o_psi = L.psi, o_psim = L.psim,
+               o_phi0 = L.phi0, o_phim = L.phim, o_xprev = L.xprev, o_kdev = L.kdev, o_g = L.g,
+               o_tv = L.tv;
+  const size_t *o_snap = L.snap, *o_phic = L.phic, *o_T = L.T, *o_R = L.R;
+  Carve cv;
+  cv.off = L.total;
   void *mem = nullptr;
   cudaError_t e = cudaMallocAsync(&mem, cv.off * sizeof(float), st);
   if (e != cudaSuccess) {

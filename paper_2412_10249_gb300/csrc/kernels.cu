@@ -14,6 +14,9 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "imask_internal.h"
 
@@ -1095,9 +1098,21 @@ cudaError_t launch_levels(const DevPlan &P, unsigned long long seed, long long k
   return cudaGetLastError();
 }
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`.  The
+// limit is process-wide and only ever raised, so that plans of different sizes
+// launching from several threads never see it lowered under them.
 static cudaError_t set_smem(const void *fn, int bytes) {
-  static_assert(sizeof(int) == 4, "");
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, int> limit;   // (device, kernel) -> bytes
+  int dev = 0;
+  const cudaError_t ed = cudaGetDevice(&dev);
+  if (ed != cudaSuccess) return ed;
+  std::lock_guard<std::mutex> lk(mu);
+  int &cur = limit[std::make_pair(dev, fn)];
+  if (bytes <= cur) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet pads,

@@ -43,7 +43,7 @@ class Desc(ctypes.Structure):
         ("storage", ctypes.c_int32),
         ("variant", ctypes.c_int32), ("theta", ctypes.c_double),
         ("dual_tables", ctypes.c_int32), ("draws", ctypes.c_int32),
-        ("step_rule", ctypes.c_int32),
+        ("step_rule", ctypes.c_int32), ("power_iters", ctypes.c_int32),
     ]
 
 
@@ -53,7 +53,8 @@ class PlanInfo(ctypes.Structure):
         ("L", ctypes.c_double), ("Lbar", ctypes.c_double), ("Lbar_p", ctypes.c_double),
         ("norm_K", ctypes.c_double), ("n_meas", ctypes.c_int64), ("n_pix", ctypes.c_int64),
         ("levels", ctypes.c_int32), ("n_xmajor_views_split", ctypes.c_int32),
-        ("n_xmajor_rays", ctypes.c_int64),
+        ("n_xmajor_rays", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
+        ("plan_bytes", ctypes.c_int64),
     ]
 
 
@@ -174,6 +175,7 @@ def make_desc(params: dict):
     d.dual_tables = int(params.get("dual_tables", 0))
     d.draws = int(params.get("draws", 0))
     d.step_rule = int(params.get("step_rule", 0))
+    d.power_iters = int(params.get("power_iters", 0))
     return d, keep
 
 

@@ -1,0 +1,80 @@
+"""The continuous-batching loop: every result equals the same solve run alone;
+admission respects the device-memory budget; oversize requests are rejected."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_10249_gb300 import build as pkg_build
+from paper_2412_10249_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask, serve
+    imask.lib()
+    return imask, serve
+
+
+def _requests(serve):
+    specs = [(64, 90, 2, 40, 0.0), (96, 120, 3, 60, 0.0), (128, 200, 4, 30, 0.0),
+             (64, 90, 2, 50, 0.02), (160, 150, 2, 40, 0.05), (96, 120, 3, 20, 0.05)]
+    out = []
+    for i, (n, na, r, iters, t) in enumerate(specs):
+        p = inputs.Problem(n=n, n_angles=na, n_det=3 * n // 2, geometry=1,
+                           angle_span=2 * math.pi, levels=r)
+        b = inputs.sinogram(p, 50 + i).ravel().astype(np.float32)
+        out.append(serve.Request(rid=i, params=p.params(), b=b, iters=iters, seed=7 + i,
+                                 arrival=t))
+    return out
+
+
+def _alone(imask, serve, req):
+    plan = imask.Plan(dict(req.params, mu=0.0, sigma=serve.normalised_sigma(req.params["levels"]),
+                           power_iters=20))
+    x = plan.solve(torch.as_tensor(req.b, device="cuda"), req.seed, req.iters)
+    return x.cpu()
+
+
+def test_results_equal_solves_alone(mods):
+    imask, serve = mods
+    reqs = _requests(serve)
+    srv = serve.Server(budget_bytes=8 << 30, max_active=4, quantum=7)
+    st = srv.run(reqs)
+    srv.close()
+    assert st.completed == len(reqs) and st.max_active >= 2
+    for r in reqs:
+        assert r.status == "done"
+        assert torch.equal(r.x, _alone(imask, serve, r)), r.rid
+
+
+def test_admission_respects_the_budget(mods):
+    imask, serve = mods
+    reqs = _requests(serve)
+    # room for the plans and about two states at a time
+    infos = []
+    for r in reqs:
+        plan = imask.Plan(dict(r.params, mu=0.3, sigma=0.03))
+        infos.append((plan.info["plan_bytes"], plan.info["state_bytes"]))
+        plan.close()
+    budget = sum(pb for pb, _ in set(infos)) + 2 * max(sb for _, sb in infos) + (4 << 20)
+    srv = serve.Server(budget_bytes=budget, max_active=6, quantum=5)
+    st = srv.run(reqs)
+    srv.close()
+    assert st.completed == len(reqs)
+    assert st.peak_bytes <= budget
+    assert st.max_active <= 3
+
+
+def test_oversize_request_is_rejected(mods):
+    imask, serve = mods
+    reqs = _requests(serve)[:2]
+    srv = serve.Server(budget_bytes=1 << 20, max_active=2)
+    st = srv.run(reqs)
+    srv.close()
+    assert st.rejected_too_large == 2 and st.completed == 0
