@@ -110,6 +110,8 @@ typedef struct {
   int32_t draws;                         /* 0 common level, 1 independent primal/dual */
   int32_t step_rule;                     /* sigma <= 0: 0 sigma*, 1 half, 2 sigma_B */
   int32_t power_iters;                   /* power-method iterations; 0 picks 100 */
+  int32_t autotune;                      /* 1: time the back-projector's view-group
+                                            split per level at plan time */
 } imask_desc;
 
 /* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,
@@ -122,6 +124,8 @@ typedef struct {
   int64_t n_xmajor_rays;
   int64_t state_bytes;                  /* device bytes one imask_state_create allocates */
   int64_t plan_bytes;                   /* device bytes the plan holds */
+  int32_t autotuned;                    /* 1 when the split below was measured */
+  int32_t bp_view_groups[8];            /* back-projector view groups per level */
 } imask_plan_info;
 
 /* Creates a plan: validates the descriptor, builds the per-ray geometry tables

@@ -123,6 +123,7 @@ struct imask_plan_s {
   int n_cta_x = 0, n_cta_y = 0;
   int n_split_views = 0;
   double mu = 0, sigma = 0, theta = 0, L = 0, Lbar = 0, Lbar_p = 0, norm_K = 0;
+  bool autotuned = false;
 };
 
 struct imask_state_s {
@@ -206,6 +207,7 @@ imask_status validate(const imask_desc *d) {
   if (d->draws != 0 && d->draws != 1) return fail(IMASK_ERR_INVALID, "draws must be 0 or 1");
   if (d->step_rule < 0 || d->step_rule > 2)
     return fail(IMASK_ERR_INVALID, "step_rule must be 0, 1 or 2");
+  if (d->autotune != 0 && d->autotune != 1) return fail(IMASK_ERR_INVALID, "autotune must be 0 or 1");
   if (d->power_iters < 0 || d->power_iters > 100000)
     return fail(IMASK_ERR_INVALID, "power_iters must be in [0, 100000]");
   if (d->geometry == 1) {
@@ -411,6 +413,80 @@ imask_status apply_KT(const imask_plan_s *p, int ell, const float *y, float *img
     CK(launch_bp(p->dp, sel, y, s.g, p->d_err, st), "back-projector launch");
   }
   CK(launch_adjsketch(p->dp, ell, s.g, img, st), "adjoint sketch launch");
+  return IMASK_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Plan-time autotuning of the back-projector's view-group split: for every
+// level, K_ell^T (back-projector and the partial-image sum that consumes its
+// output) is timed with CUDA events for split counts around the occupancy
+// heuristic's choice, and the fastest is kept.
+// ---------------------------------------------------------------------------------
+imask_status autotune_bp(imask_plan_s *p, cudaStream_t st) {
+  DevPlan &dp = p->dp;
+  const int r = p->desc.levels, na = p->desc.n_angles;
+  std::vector<int> cand[IMASK_MAX_LEVELS + 1];
+  size_t gmax = p->gcap;
+  for (int li = 0; li <= r; ++li) {
+    const int base = dp.lg[li].bp_vgo;
+    for (int v : {base, std::max(1, base / 2), std::max(1, (2 * base) / 3), (3 * base + 1) / 2,
+                  2 * base}) {
+      v = std::min(v, na);
+      if (std::find(cand[li].begin(), cand[li].end(), v) == cand[li].end()) cand[li].push_back(v);
+      gmax = std::max(gmax, (size_t)2 * v * dp.lg[li].nl * dp.lg[li].nl);
+    }
+  }
+  const size_t d = dp.d, m = dp.m;
+  Scratch sc;
+  sc.st = st;
+  Carve cv;
+  const size_t o_g = cv.take(gmax), o_y = cv.take(m), o_img = cv.take(d);
+  void *mem = nullptr;
+  CK(cudaMallocAsync(&mem, cv.off * sizeof(float), st), "cudaMallocAsync(autotune)");
+  float *B = (float *)mem;
+  sc.g = B + o_g;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  imask_status rc = IMASK_OK;
+  cudaError_t e = cudaMemsetAsync(mem, 0, cv.off * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  for (int li = 1; li <= r && e == cudaSuccess && rc == IMASK_OK; ++li) {
+    const int ell = li - 1;
+    float best_ms = 1e30f;
+    int best_v = dp.lg[li].bp_vgo;
+    for (int v : cand[li]) {
+      LevelGeom &g = dp.lg[li];
+      g.bp_vgo = v;
+      g.bp_nv = (na + v - 1) / v;
+      if (bp_smem_bytes(dp) > 160 * 1024) continue;
+      float ms = 0.0f, tot = 0.0f;
+      for (int rep = 0; rep < 4 && rc == IMASK_OK && e == cudaSuccess; ++rep) {
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        rc = apply_KT(p, ell, B + o_y, B + o_img, sc, st);
+        if (rc != IMASK_OK) break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        if (rep > 0) tot += ms;   // the first launch warms up
+      }
+      if (rc != IMASK_OK || e != cudaSuccess) break;
+      if (tot < best_ms) {
+        best_ms = tot;
+        best_v = v;
+      }
+    }
+    dp.lg[li].bp_vgo = best_v;
+    dp.lg[li].bp_nv = (na + best_v - 1) / best_v;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(mem, st);
+  if (rc != IMASK_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  p->gcap = 0;
+  for (int li = 0; li <= r; ++li)
+    p->gcap = std::max(p->gcap, (size_t)2 * dp.lg[li].bp_vgo * dp.lg[li].nl * dp.lg[li].nl);
+  p->autotuned = true;
   return IMASK_OK;
 }
 
@@ -885,7 +961,8 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.rays_lo = p->d_rays_lo;
   dp.views = p->d_views;
 
-  rc = plan_constants(p, st);
+  rc = p->desc.autotune ? autotune_bp(p, st) : IMASK_OK;
+  if (rc == IMASK_OK) rc = plan_constants(p, st);
   e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
   if (rc == IMASK_OK && e != cudaSuccess) rc = cuda_fail(e, "plan set-up");
@@ -924,6 +1001,9 @@ imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
   info->n_xmajor_views_split = p->n_split_views;
   info->n_xmajor_rays = p->dp.m_x;
   info->state_bytes = (int64_t)(state_layout(p).total * sizeof(float));
+  info->autotuned = p->autotuned ? 1 : 0;
+  for (int l = 0; l < IMASK_MAX_LEVELS; ++l)
+    info->bp_view_groups[l] = l < p->desc.levels ? p->dp.lg[l + 1].bp_vgo : 0;
   info->plan_bytes = (int64_t)(p->dp.m * (sizeof(float4) + sizeof(float2)) +
                                p->dp.n_angles * sizeof(ViewInfo) + sizeof(unsigned int));
   return IMASK_OK;

@@ -18,7 +18,9 @@
 #define BP_THREADS 256         // back-projector: threads per CTA
 #define BP_W 16                // back-projector tile: lines along the major axis
 #define BP_SEG 32              // back-projector tile: lines across (one owner segment)
+#ifndef BP_SLOTS
 #define BP_SLOTS 256           // back-projector: ray slots per staged chunk
+#endif
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin);
                                // equal to BP_W so a back-projector tile is one block
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA

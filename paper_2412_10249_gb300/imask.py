@@ -18,7 +18,9 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libimask.so")
+# IMASK_LIBRARY selects another build of the same library (e.g. one compiled
+# with different tile constants); the default is the in-tree build.
+LIB_PATH = os.environ.get("IMASK_LIBRARY") or os.path.join(_HERE, "_build", "libimask.so")
 
 STATUS = {0: "IMASK_OK", 1: "IMASK_ERR_INVALID", 2: "IMASK_ERR_SHAPE", 3: "IMASK_ERR_OOM",
           4: "IMASK_ERR_CUDA", 5: "IMASK_ERR_TIMEOUT", 6: "IMASK_ERR_NONFINITE"}
@@ -44,6 +46,7 @@ class Desc(ctypes.Structure):
         ("variant", ctypes.c_int32), ("theta", ctypes.c_double),
         ("dual_tables", ctypes.c_int32), ("draws", ctypes.c_int32),
         ("step_rule", ctypes.c_int32), ("power_iters", ctypes.c_int32),
+        ("autotune", ctypes.c_int32),
     ]
 
 
@@ -54,7 +57,8 @@ class PlanInfo(ctypes.Structure):
         ("norm_K", ctypes.c_double), ("n_meas", ctypes.c_int64), ("n_pix", ctypes.c_int64),
         ("levels", ctypes.c_int32), ("n_xmajor_views_split", ctypes.c_int32),
         ("n_xmajor_rays", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
-        ("plan_bytes", ctypes.c_int64),
+        ("plan_bytes", ctypes.c_int64), ("autotuned", ctypes.c_int32),
+        ("bp_view_groups", ctypes.c_int32 * 8),
     ]
 
 
@@ -176,6 +180,7 @@ def make_desc(params: dict):
     d.draws = int(params.get("draws", 0))
     d.step_rule = int(params.get("step_rule", 0))
     d.power_iters = int(params.get("power_iters", 0))
+    d.autotune = int(params.get("autotune", 0))
     return d, keep
 
 
@@ -196,7 +201,9 @@ def imask_plan_destroy(plan):
 def imask_plan_get_info(plan) -> dict:
     info = PlanInfo()
     _check(lib().imask_plan_get_info(plan, ctypes.byref(info)))
-    return {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+    out = {k: getattr(info, k) for k, _ in PlanInfo._fields_}
+    out["bp_view_groups"] = list(info.bp_view_groups)
+    return out
 
 
 def imask_plan_check(plan):

@@ -1,0 +1,54 @@
+"""Plan-time autotuning of the back-projector split: the tuned plan keeps
+parity with the oracle (the split only changes the order of the partial-image
+sum) and reports what it chose."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import Oracle
+from paper_2412_10249_gb300 import build as pkg_build
+from paper_2412_10249_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def imask():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask as m
+    m.lib()
+    return m
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prob", [
+    inputs.Problem(n=64, n_angles=90, n_det=96, geometry=1, angle_span=2 * math.pi, levels=4),
+    inputs.Problem(n=48, n_angles=37, n_det=75, geometry=1, angle_span=2 * math.pi,
+                   angle_start=0.3, levels=4, probs=[0.3, 0.3, 0.2, 0.2]),
+], ids=["fan64_r4", "fan48_p3322"])
+def test_autotuned_plan_keeps_parity(imask, prob):
+    params = dict(prob.params(), mu=0.1, sigma=0.04)
+    plan = imask.Plan(dict(params, autotune=1))
+    info = plan.info
+    assert info["autotuned"] == 1
+    assert all(v >= 1 for v in info["bp_view_groups"][:prob.levels])
+    o = Oracle(**params)
+    rng = np.random.default_rng(0)
+    y = rng.standard_normal(o.m)
+    yt = torch.as_tensor(y.astype(np.float32), device="cuda")
+    for ell in range(prob.levels):
+        got = plan.backproject(ell, yt).double().cpu().numpy()
+        assert rel(got, o.KT(ell, y)) <= 1e-5, ell
+    _, b, _ = inputs.measurements(prob, seed=1, noise="none")
+    st, _ = o.run(b.ravel(), 3, 30)
+    s = plan.state(torch.as_tensor(b.ravel().astype(np.float32), device="cuda"), 3)
+    s.step(30)
+    assert rel(s.get(s.X).double().cpu().numpy(), st["x"]) <= 1e-4
