@@ -580,6 +580,11 @@ def run_serve(args):
     clk = clocks.stop()
     done = [r for r in reqs if r.status == "done"]
     achieved = sum(expected_samples_per_solve(problems[r.rid], r.iters) for r in done)
+    # work launched in the window, unfinished solves included (iterations
+    # launched; an upper bound on the iterations executed)
+    launched = achieved + sum(expected_samples_per_solve(problems[a.req.rid],
+                                                         a.req.iters - a.remaining)
+                              for a in srv.active)
     lat = np.array(st.latencies) * 1e3
     wait = np.array(st.waits) * 1e3
     T = args.serve_seconds
@@ -588,6 +593,7 @@ def run_serve(args):
             "offered": {"requests": len(reqs), "rate_per_s": args.serve_rate,
                         "gsamples_per_s": offered / T / 1e9},
             "achieved_gsamples_per_s": achieved / T / 1e9,
+            "launched_gsamples_per_s": launched / T / 1e9,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
             "p99_ms": float(np.percentile(lat, 99)) if lat.size else None,
             "queue_wait_p50_ms": float(np.percentile(wait, 50)) if wait.size else None,
