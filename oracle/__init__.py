@@ -61,7 +61,8 @@ def _dp(a: np.ndarray):
 
 class OrcVariant(ctypes.Structure):
     _fields_ = [("sequential", ctypes.c_int32), ("theta", ctypes.c_double),
-                ("snapshots", ctypes.c_int32), ("independent", ctypes.c_int32)]
+                ("snapshots", ctypes.c_int32), ("independent", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
 
 
 class Oracle:
@@ -109,6 +110,8 @@ class Oracle:
                                                        ctypes.c_double, _D, _D, _D, _D, _D,
                                                        _I32]),
                 "orc_primal_seed": (ctypes.c_uint64, [ctypes.c_uint64]),
+                "orc_round_format": (ctypes.c_double, [ctypes.c_double, ctypes.c_int32,
+                                                       ctypes.c_int32]),
                 "orc_imask_variant_run": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_void_p, _D,
                                                            ctypes.c_uint64, ctypes.c_int64,
                                                            ctypes.c_int32] + [_D] * 7
@@ -329,6 +332,12 @@ class Oracle:
         state["k"] += iters
         return state, lv[:iters]
 
+    @classmethod
+    def round_format(cls, v: float, fmt: int) -> float:
+        """bfloat16 (fmt 1) or binary16 (fmt 2) rounding of v, RNE."""
+        bits, emin = (8, -126) if fmt == 1 else (11, -14)
+        return float(cls.lib().orc_round_format(float(v), bits, emin))
+
     def primal_seed(self, seed: int) -> int:
         return int(self.L.orc_primal_seed(seed))
 
@@ -345,14 +354,14 @@ class Oracle:
         return st
 
     def run_variant(self, b: np.ndarray, seed: int, iters: int, sequential=False, theta=1.0,
-                    snapshots=False, independent=False, state=None):
+                    snapshots=False, independent=False, storage=0, state=None):
         """Alg. 1 / Alg. 7 with the snapshot tables and independent-draw options.
 
         Returns (state, dual levels, primal levels)."""
         if state is None:
             state = self.new_variant_state(snapshots)
         var = OrcVariant(int(bool(sequential)), float(theta), int(bool(snapshots)),
-                         int(bool(independent)))
+                         int(bool(independent)), int(storage))
         b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
         ld = np.zeros(max(1, iters), dtype=np.int32)
         lp = np.zeros(max(1, iters), dtype=np.int32)

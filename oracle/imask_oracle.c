@@ -627,6 +627,26 @@ int32_t orc_imask_seq_run(const orc_desc *d, const double *b, uint64_t seed, int
 /*    in the concluding section).                                             */
 /* ------------------------------------------------------------------------ */
 
+/* Nearest representable value with RNE: the quantum is 2^(e - bits + 1) for a
+ * value in [2^e, 2^(e+1)), with e clamped below at emin (subnormals); ties go
+ * to the even multiple (nearbyint in the default rounding mode).  Overflow is
+ * not modelled (the tables stay far below both formats' largest values). */
+double orc_round_format(double v, int32_t bits, int32_t emin) {
+  if (v == 0.0 || !isfinite(v)) return v;
+  int e2 = 0;
+  frexp(v, &e2);          /* |v| = f 2^e2, f in [0.5, 1) */
+  int ex = e2 - 1;        /* |v| in [2^ex, 2^(ex+1)) */
+  if (ex < emin) ex = emin;
+  const double q = ldexp(1.0, ex - (bits - 1));
+  return nearbyint(v / q) * q;
+}
+
+static double store_table(const orc_variant *var, double v) {
+  if (var->storage == 1) return orc_round_format(v, 8, -126);
+  if (var->storage == 2) return orc_round_format(v, 11, -14);
+  return v;
+}
+
 uint64_t orc_primal_seed(uint64_t seed) {
   /* the SplitMix64 finaliser applied to the seed itself */
   uint64_t z = seed;
@@ -670,6 +690,9 @@ int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const d
         delta[q] = kx[q] - psi[(int64_t)ld * m + q];
         zeta[q] = delta[q] + s;
       }
+      /* 16-bit tables: the refreshed entry is stored rounded (the sum above
+       * always runs over the stored values) */
+      for (int64_t q = 0; q < m; ++q) kx[q] = store_table(var, kx[q]);
     }
     /* Alg. 1 back-projects y^k; Alg. 7 back-projects y^{k+1} */
     for (int64_t q = 0; q < m; ++q) yn[q] = (y[q] + sigma * zeta[q] - sigma * b[q]) / (1.0 + sigma);

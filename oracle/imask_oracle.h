@@ -96,7 +96,12 @@ typedef struct {
   double theta;        /* Alg. 7 extrapolation weight */
   int32_t snapshots;   /* 1: dual tables kept as projector-input snapshots */
   int32_t independent; /* 1: primal level drawn from the stream of orc_primal_seed(seed) */
+  int32_t storage;     /* measurement-side tables held as 0 FP64, 1 bfloat16, 2 binary16 */
 } orc_variant;
+
+/* Round-to-nearest-even of v to a binary format with `bits` significant bits
+ * and minimum normal exponent emin (bfloat16: 8, -126; binary16: 11, -14). */
+double orc_round_format(double v, int32_t bits, int32_t emin);
 
 uint64_t orc_primal_seed(uint64_t seed);
 /* State: x[d], xbar[d] (sequential), y[m], phi[r*d], and either psi[r*m]
