@@ -553,6 +553,109 @@ def time_batch_fan512(imask, p, bt, info, iters, stream, n_states=8):
 
 
 # ---------------------------------------------------------------------------------
+# 16-bit table storage with an fp32 refinement sweep (1024x1024 fan workload)
+# ---------------------------------------------------------------------------------
+def run_precision(args):
+    """1024x1024 fan beam, 1440 views x 1024 bins (bin pitch 1.5 W / 1024 so the
+    magnified field of view stays covered), 5 levels, 500 iterations: the plain
+    fp32 form (one solve at a time) against bf16 / fp16 measurement-side tables,
+    alone and as a graph-captured batch, each followed by an fp32 refinement
+    sweep in steps of 10 iterations while its error against the plain fp32
+    result exceeds 1e-3 (at most 100 iterations).  Errors are also given
+    against the fixed point of eq. min_obj_new (CG)."""
+    import torch
+    from paper_2412_10249_gb300 import build as pkg_build
+    pkg_build.build()
+    from paper_2412_10249_gb300 import imask
+    p = inputs.Problem(n=1024, n_angles=1440, n_det=1024, geometry=1, angle_span=2 * math.pi,
+                       src_dist=2.0, det_dist=1.0, det_spacing=1.5 / 1024, levels=5)
+    b = inputs.sinogram(p, 0)
+    bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
+    base = imask.Plan(dict(p.params(), mu=0.0, sigma=0.0, autotune=1))
+    info = base.info
+    xnat, cg_res = cg_fixed_point(base, p, bt, info["mu"])
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+    stream = torch.cuda.Stream()
+    K = args.iters
+    B = args.precision_batch
+
+    def timed(fn):
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            fn()
+            e.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(e) / 1e3
+
+    def refine(states, x_ref):
+        """fp32 sweep until every state is within 1e-3 of x_ref; device seconds."""
+        t, its = 0.0, 0
+        errs = [math.sqrt(imask.imask_rel_distance(s.get(s.X), x_ref)) for s in states]
+        first = list(errs)
+        while max(errs) > 1e-3 and its < 100:
+            if its == 0:
+                for s in states:
+                    s.set_storage(0, stream=stream)
+            t += timed(lambda: [s.step(10, stream=stream) for s in states])
+            its += 10
+            errs = [math.sqrt(imask.imask_rel_distance(s.get(s.X), x_ref)) for s in states]
+        return t, its, first, errs
+
+    plans = {fmt: imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"], storage=fmt,
+                                  autotune=1)) for fmt in (0, 1, 2)}
+    # warm-up
+    for fmt, plan in plans.items():
+        w = plan.state(bt, 99, stream=stream)
+        timed(lambda: w.step(10, stream=stream))
+        w.close()
+    out = {}
+    # plain fp32, one solve at a time
+    s = plans[0].state(bt, 0, stream=stream)
+    flush.fill_(1.0)
+    t = timed(lambda: s.step(K, stream=stream))
+    x_plain = s.get(s.X)
+    out["fp32_plain"] = {"solves_per_s": 1.0 / t, "ms_per_solve": 1e3 * t,
+                         "rel_err_vs_fixed_point": math.sqrt(imask.imask_rel_distance(x_plain, xnat)),
+                         "state_mb": plans[0].info["state_bytes"] / 2 ** 20}
+    for name, fmt in (("bf16", 1), ("fp16", 2)):
+        s = plans[fmt].state(bt, 0, stream=stream)
+        flush.fill_(1.0)
+        t = timed(lambda: s.step(K, stream=stream))
+        tr, its, e0, e1 = refine([s], x_plain)
+        x = s.get(s.X)
+        out[name] = {"solves_per_s": 1.0 / (t + tr), "ms_per_solve": 1e3 * (t + tr),
+                     "rel_err_vs_plain_fp32_before_refinement": e0[0],
+                     "refine_iters": its, "rel_err_vs_plain_fp32": e1[0],
+                     "rel_err_vs_fixed_point": math.sqrt(imask.imask_rel_distance(x, xnat)),
+                     "state_mb": plans[fmt].info["state_bytes"] / 2 ** 20}
+        s.close()
+    # batched bf16: B solves (seeds 0..B-1; seed 0 is compared with the plain result)
+    states = [plans[1].state(bt, i, stream=stream) for i in range(B)]
+    batch = imask.Batch(states)
+    flush.fill_(1.0)
+    t = timed(lambda: batch.step(K, stream=stream))
+    batch.close()
+    tr, its, e0, e1 = refine(states[:1], x_plain)
+    if its:
+        tr = timed(lambda: [st.step(its, stream=stream) for st in states[1:]]) + tr
+    out[f"bf16_batch{B}"] = {"solves_per_s": B / (t + tr), "ms_per_solve": 1e3 * (t + tr) / B,
+                             "rel_err_vs_plain_fp32_before_refinement": e0[0],
+                             "refine_iters": its, "rel_err_vs_plain_fp32": e1[0],
+                             "includes": "graph capture and instantiation"}
+    for st in states:
+        st.close()
+    line = {"metric": "ImaSk solves/s at rel.err<=1e-3 vs plain FP32: 16-bit tables, batched",
+            "unit": "solves/s", "iters": K,
+            "config": {"workload": "1024x1024 fan 1440x1024 (pitch 1.5W/1024), r=5, K=500, "
+                                   "quadratic R", "batch": B},
+            "mu": info["mu"], "sigma": info["sigma"], "cg_rel_residual": cg_res,
+            "forms": out}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------
 # serving: Poisson arrivals, continuous batching under a device-memory budget
 # ---------------------------------------------------------------------------------
 def run_serve(args):
@@ -798,6 +901,9 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="mixed-size slices: one after the other vs one graph-captured batch")
     ap.add_argument("--batch-slices", type=int, default=64)
+    ap.add_argument("--precision", action="store_true",
+                    help="1024x1024: bf16/fp16 tables with an fp32 refinement sweep vs fp32")
+    ap.add_argument("--precision-batch", type=int, default=4)
     ap.add_argument("--serve", action="store_true",
                     help="Poisson-arrival serving run with continuous batching")
     ap.add_argument("--serve-seconds", type=float, default=20.0)
@@ -829,6 +935,8 @@ def main():
         return run_batch(args)
     if args.serve:
         return run_serve(args)
+    if args.precision:
+        return run_precision(args)
     return run_ours(args)
 
 

@@ -88,6 +88,13 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               last refresh (n^2 + sum_{l>=1} (n/2^l)^2 floats; the remark
  *               after Alg. 3), the projector then applies K_l to the
  *               difference.  Same iterates up to rounding.
+ *  storage      format of the measurement-side tables psi_l (dual_tables 0),
+ *               the largest arrays of a solve: 0 fp32, 1 bfloat16, 2 binary16
+ *               (round to nearest even on store; all arithmetic in fp32; the
+ *               running mean follows the stored values).  Rounded tables move
+ *               the fixed point by about the format's precision;
+ *               imask_state_set_storage(state, 0, ...) switches a state to
+ *               fp32 tables for a refinement sweep.
  *  draws        0: one level per iteration (Alg. 1); 1: the primal level
  *               (back-projector, image-side tables) is drawn from a second
  *               SplitMix64 stream whose seed is the SplitMix64 finaliser of
@@ -103,7 +110,7 @@ typedef struct {
   double mu, tv_lambda, tv_eps;
   int32_t tv_inner;
   double sigma;
-  int32_t storage;                       /* 0: fp32 (the only storage implemented) */
+  int32_t storage;                       /* tables: 0 fp32, 1 bf16, 2 fp16 (see below) */
   int32_t variant;                       /* 0 Alg. 1, 1 Alg. 7 */
   double theta;                          /* Alg. 7 extrapolation */
   int32_t dual_tables;                   /* 0 K_l x tables, 1 input snapshots */
@@ -221,6 +228,13 @@ int64_t imask_state_iteration(imask_state_t state);
  * 2 the running mean sum_l p_l phi_l [n*n], 3 the running mean sum_l p_l psi_l [m]. */
 imask_status imask_state_get(imask_state_t state, int32_t what, float *dst_dev, void *stream);
 imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
+/* Converts the state's measurement-side tables to another storage format
+ * (0 fp32, 1 bf16, 2 fp16) and re-forms their running mean from the converted
+ * tables; later iterations use the new format (widening to fp32 is exact: the
+ * refinement sweep of a 16-bit solve).  Allocates the new tables with
+ * cudaMallocAsync on stream.  INVALID for a state without such tables unless
+ * storage is 0.  Not to be called while a batch holding the state is replayed. */
+imask_status imask_state_set_storage(imask_state_t state, int32_t storage, void *stream);
 /* Frees the state's buffers (stream-ordered on the stream last used). */
 imask_status imask_state_destroy(imask_state_t state);
 

@@ -134,7 +134,10 @@ struct imask_state_s {
   cudaStream_t stream = nullptr;
   float *block = nullptr;
   unsigned long long seed_x = 0;   // primal level stream (= seed unless draws = 1)
-  float *x = nullptr, *y[2] = {nullptr, nullptr}, *b = nullptr, *psi = nullptr,
+  void *psi = nullptr;        // measurement-side tables (format psi_fmt), or nullptr
+  int psi_fmt = 0;            // 0 float, 1 bfloat16, 2 binary16
+  void *psi_block = nullptr;  // separate table allocation after a storage change
+  float *x = nullptr, *y[2] = {nullptr, nullptr}, *b = nullptr,
         *psi_mean = nullptr, *phi0 = nullptr, *phic = nullptr, *phi_mean = nullptr, *g = nullptr,
         *tv = nullptr, *x_prev = nullptr;
   long long phic_off[IMASK_MAX_LEVELS] = {0};
@@ -197,7 +200,11 @@ imask_status validate(const imask_desc *d) {
     return fail(IMASK_ERR_INVALID, "smoothed TV needs tv_eps > 0, tv_lambda >= 0, tv_inner >= 0");
   if (d->reg == 2 && (!(d->tv_lambda >= 0.0) || d->tv_inner < 0))
     return fail(IMASK_ERR_INVALID, "TV with nonnegativity needs tv_lambda >= 0, tv_inner >= 0");
-  if (d->storage != 0) return fail(IMASK_ERR_INVALID, "only fp32 storage (0) is implemented");
+  if (d->storage < 0 || d->storage > 2)
+    return fail(IMASK_ERR_INVALID, "storage must be 0 (fp32), 1 (bf16) or 2 (fp16)");
+  if (d->storage != 0 && d->dual_tables == 1)
+    return fail(IMASK_ERR_INVALID, "16-bit storage applies to the measurement-side tables, "
+                                   "which the snapshot form does not keep");
   if (d->variant != 0 && d->variant != 1)
     return fail(IMASK_ERR_INVALID, "variant must be 0 (Alg. 1) or 1 (Alg. 7)");
   if (d->variant == 1 && !isfinite(d->theta))
@@ -672,7 +679,8 @@ StateLayout state_layout(const imask_plan_s *p) {
   L.y0 = cv.take(m);
   L.y1 = cv.take(m);
   L.b = cv.take(m);
-  L.psi = snapshots ? 0 : cv.take(m * r);
+  const size_t esize = p->desc.storage != 0 ? 2 : 4;   // bytes per table entry
+  L.psi = snapshots ? 0 : cv.take((m * r * esize + 3) / 4);
   L.psim = cv.take(m);
   L.phi0 = cv.take(d);
   L.phim = cv.take(d);
@@ -1149,7 +1157,8 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   s->y[0] = B + o_y0;
   s->y[1] = B + o_y1;
   s->b = B + o_b;
-  s->psi = snapshots ? nullptr : B + o_psi;
+  s->psi = snapshots ? nullptr : (void *)(B + o_psi);
+  s->psi_fmt = p->desc.storage;
   s->psi_mean = B + o_psim;
   s->seed_x = p->desc.draws == 1 ? primal_seed(seed) : seed;
   if (snapshots) {
@@ -1212,6 +1221,7 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   D.y_out = s->y[1 - cur];
   D.b = s->b;
   D.psi = s->psi;
+  D.psi_fmt = s->psi_fmt;
   D.psi_mean = s->psi_mean;
   D.sigma = sigma;
   D.inv_1ps = inv_1ps;
@@ -1433,8 +1443,42 @@ imask_status imask_state_get_x(imask_state_t s, float *x_dev, void *stream) {
   return imask_state_get(s, 0, x_dev, stream);
 }
 
+imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *stream) {
+  if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
+  if (storage < 0 || storage > 2) return fail(IMASK_ERR_INVALID, "storage must be 0, 1 or 2");
+  if (!s->psi || storage == s->psi_fmt) {
+    if (!s->psi && storage != 0)
+      return fail(IMASK_ERR_INVALID, "the snapshot form keeps no measurement-side tables");
+    return IMASK_OK;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const imask_plan_s *p = s->plan;
+  const long long n = (long long)p->dp.m * p->desc.levels;
+  void *mem = nullptr;
+  CK(cudaMallocAsync(&mem, (size_t)n * (storage != 0 ? 2 : 4), st), "cudaMallocAsync(tables)");
+  cudaError_t e = launch_convert(n, s->psi, s->psi_fmt, mem, storage, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, st);
+    return cuda_fail(e, "table conversion");
+  }
+  // the running mean is re-formed from the converted tables so that it stays
+  // their p-weighted sum
+  e = launch_table_mean(p->dp, mem, storage, s->psi_mean, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(mem, st);
+    return cuda_fail(e, "table mean");
+  }
+  if (s->psi_block) cudaFreeAsync(s->psi_block, st);
+  s->psi_block = mem;
+  s->psi = mem;
+  s->psi_fmt = storage;
+  s->stream = st;
+  return IMASK_OK;
+}
+
 imask_status imask_state_destroy(imask_state_t s) {
   if (!s) return IMASK_OK;
+  if (s->psi_block) cudaFreeAsync(s->psi_block, s->stream);
   if (s->block) cudaFreeAsync(s->block, s->stream);
   delete s;
   return IMASK_OK;

@@ -112,8 +112,9 @@ struct DualArgs {
   const float *y_in;
   float *y_out;
   const float *b;
-  float *psi;        // table base, level ell at psi + ell * m; nullptr: the
+  void *psi;         // table base, level ell at entry ell * m; nullptr: the
                      // projector output is already the table difference
+  int psi_fmt;       // table entries: 0 float, 1 bfloat16, 2 binary16
   float *psi_mean;   // sum_l p_l psi_l
   float sigma, inv_1ps;
 };
@@ -164,6 +165,12 @@ cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn,
 cudaError_t launch_axpy(long long n, float alpha, const float *x, float *y, cudaStream_t st);
 // *k_dev += delta (one thread), or *k_dev = value when set_value != 0
 cudaError_t launch_counter(long long *k_dev, long long delta, int set_value, cudaStream_t st);
+// dst[i] = src[i] converted between the table formats (0 float, 1 bfloat16, 2 binary16)
+cudaError_t launch_convert(long long n, const void *src, int src_fmt, void *dst, int dst_fmt,
+                           cudaStream_t st);
+// psi_mean = sum_l p_l psi_l over the level tables
+cudaError_t launch_table_mean(const DevPlan &P, const void *psi, int fmt, float *psi_mean,
+                              cudaStream_t st);
 cudaError_t launch_scale(long long n, float alpha, float *x, cudaStream_t st);
 cudaError_t launch_fill(long long n, float v, float *x, cudaStream_t st);
 cudaError_t launch_copy(long long n, const float *x, float *y, cudaStream_t st);

@@ -10,6 +10,8 @@
 //             update and prox, and the image-side sketch T_ell' / S_r of the
 //             new iterate for the next drawn level (fused "sketch on load").
 // The level of every launch is drawn on the device from (seed, k).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -311,16 +313,38 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
       // the running mean and the table entry take the refreshed value.  With
       // snapshot tables the projector already applied K_l to the input
       // difference, so v is psi_new - psi_l itself.
-      float delta = v;
+      // With 16-bit tables the refreshed entry is stored rounded and the
+      // running mean moves by the stored change, so that it stays the
+      // p-weighted sum of the stored tables.
+      float delta = v, dmean = v;
       if (D.psi) {
-        float *psil = D.psi + (size_t)ell * P.m;
-        delta = v - psil[q];
-        psil[q] = v;
+        const size_t qi = (size_t)ell * P.m + q;
+        float old, stored;
+        if (D.psi_fmt == 1) {
+          __nv_bfloat16 *t = (__nv_bfloat16 *)D.psi;
+          old = __bfloat162float(t[qi]);
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          t[qi] = h;
+          stored = __bfloat162float(h);
+        } else if (D.psi_fmt == 2) {
+          __half *t = (__half *)D.psi;
+          old = __half2float(t[qi]);
+          const __half h = __float2half_rn(v);
+          t[qi] = h;
+          stored = __half2float(h);
+        } else {
+          float *t = (float *)D.psi;
+          old = t[qi];
+          t[qi] = v;
+          stored = v;
+        }
+        delta = v - old;
+        dmean = stored - old;
       }
       const float pm = D.psi_mean[q];
       const float zeta = delta + pm;
       D.y_out[q] = fmaf(D.sigma, zeta - D.b[q], D.y_in[q]) * D.inv_1ps;
-      D.psi_mean[q] = fmaf(P.probs[ell], delta, pm);
+      D.psi_mean[q] = fmaf(P.probs[ell], dmean, pm);
     }
   }
 }
@@ -966,6 +990,35 @@ __global__ void k_levels(DevPlan P, unsigned long long seed, long long k0, long 
     out[t] = draw_level(P, seed, k0 + t);
 }
 
+__device__ __forceinline__ float load_fmt(const void *p, long long i, int fmt) {
+  if (fmt == 1) return __bfloat162float(((const __nv_bfloat16 *)p)[i]);
+  if (fmt == 2) return __half2float(((const __half *)p)[i]);
+  return ((const float *)p)[i];
+}
+
+__global__ void k_convert(long long n, const void *src, int sf, void *dst, int df) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const float v = load_fmt(src, t, sf);
+    if (df == 1)
+      ((__nv_bfloat16 *)dst)[t] = __float2bfloat16_rn(v);
+    else if (df == 2)
+      ((__half *)dst)[t] = __float2half_rn(v);
+    else
+      ((float *)dst)[t] = v;
+  }
+}
+
+// psi_mean[q] = sum_l p_l psi_l[q], levels in order
+__global__ void k_table_mean(DevPlan P, const void *psi, int fmt, float *psi_mean) {
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < P.m;
+       q += (long long)gridDim.x * blockDim.x) {
+    float s = 0.0f;
+    for (int l = 0; l < P.levels; ++l) s = fmaf(P.probs[l], load_fmt(psi, (long long)l * P.m + q, fmt), s);
+    psi_mean[q] = s;
+  }
+}
+
 __global__ void k_counter(long long *k, long long delta, int set_value) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *k = set_value ? delta : *k + delta;
 }
@@ -1282,6 +1335,21 @@ cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn,
 cudaError_t launch_counter(long long *k_dev, long long delta, int set_value, cudaStream_t st) {
   count_launch();
   k_counter<<<1, 32, 0, st>>>(k_dev, delta, set_value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert(long long n, const void *src, int src_fmt, void *dst, int dst_fmt,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  count_launch();
+  k_convert<<<grid_for(n, 256), 256, 0, st>>>(n, src, src_fmt, dst, dst_fmt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_mean(const DevPlan &P, const void *psi, int fmt, float *psi_mean,
+                              cudaStream_t st) {
+  count_launch();
+  k_table_mean<<<grid_for(P.m, 256), 256, 0, st>>>(P, psi, fmt, psi_mean);
   return cudaGetLastError();
 }
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "imask_solve": (_I32, [_VP, _VP, _U64, _I32, _VP, _VP]),
     "imask_objective": (_I32, [_VP, _VP, _VP, _DP, _VP]),
     "imask_rel_distance": (_I32, [_I64, _VP, _VP, _DP, _VP]),
+    "imask_state_set_storage": (_I32, [_VP, _I32, _VP]),
     "imask_batch_create": (_I32, [_VP, _I32, _VP]),
     "imask_batch_step": (_I32, [_VP, _I32, _VP]),
     "imask_batch_destroy": (_I32, [_VP]),
@@ -375,6 +376,10 @@ class State:
 
     def step(self, n_iters: int, stream=None):
         _check(lib().imask_step(self.handle, n_iters, _stream(stream)))
+
+    def set_storage(self, storage: int, stream=None):
+        """Converts the measurement-side tables (0 fp32, 1 bf16, 2 fp16)."""
+        _check(lib().imask_state_set_storage(self.handle, storage, _stream(stream)))
 
     @property
     def k(self) -> int:

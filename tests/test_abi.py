@@ -42,7 +42,8 @@ def test_every_declared_symbol_is_exported(imask):
 
 @pytest.mark.parametrize("bad,status", [
     (dict(n=0), 2), (dict(levels=9), 1), (dict(n=60, levels=4), 2),
-    (dict(probs=[0.5, 0.6]), 1), (dict(geometry=2), 1), (dict(storage=1), 1),
+    (dict(probs=[0.5, 0.6]), 1), (dict(geometry=2), 1), (dict(storage=3), 1),
+    (dict(storage=1, dual_tables=1), 1),
     (dict(fov=-1.0), 1), (dict(n=4096), 2), (dict(variant=2), 1),
     (dict(variant=1, theta=float("nan")), 1), (dict(dual_tables=2), 1), (dict(draws=-1), 1),
     (dict(step_rule=3), 1), (dict(reg=3), 1), (dict(reg=2, tv_inner=-1), 1),
