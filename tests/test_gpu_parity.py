@@ -284,3 +284,19 @@ def test_fan512_iterates(imask, fan512):
     s.step(6)
     assert rel(host(s.get(s.X)), st["x"]) <= TOL_ITER
     assert rel(host(s.get(s.Y)), st["y"]) <= TOL_ITER
+
+
+def test_fan512_autotuned_launch_configuration(imask, fan512):
+    # the benchmark's plan: back-projector splits measured at plan time
+    params, b, _, o = fan512
+    plan = imask.Plan(dict(params, autotune=1))
+    assert plan.info["autotuned"] == 1
+    yv = np.random.default_rng(2).standard_normal(o.m)
+    y = cuda(yv)
+    for ell in (1, 2):
+        assert rel(host(plan.backproject(ell, y)), o.KT(ell, yv).ravel()) <= TOL_OP, ell
+    seed = 33
+    st, _ = o.run(b, seed, 6)
+    s = plan.state(cuda(b), seed)
+    s.step(6)
+    assert rel(host(s.get(s.X)), st["x"]) <= TOL_ITER
