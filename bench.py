@@ -235,7 +235,15 @@ def _dram_traffic(kname: str, level: int):
         return None
 
 
-def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops, period=1):
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops, period=1, smem_probe=None):
     """Dominant (kernel, level) by total event time; its average launch against
     the FP32 CUDA-core peak (bound "alu": the projectors are limited by issue
     slots and the shared-memory pipe, not by DRAM), plus the shared-memory
@@ -262,7 +270,14 @@ def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops, period=1):
                                 "flops_per_sample": FLOPS_PER_SAMPLE[kind],
                                 "smem_bytes_per_sample": SMEM_BYTES_PER_SAMPLE[kind]},
                    smem={"achieved_gbs": smem, "peak_gbs": SMEM_PEAK_GBS,
+                         "peak_source": "derived: 152 SMs x 128 B x 2070 MHz",
                          "frac": smem / SMEM_PEAK_GBS})
+        if smem_probe is not None:
+            # measured ceiling of the access pattern: loads (projector) or
+            # private read-modify-writes (back-projector)
+            ceil_gbs = smem_probe[1] if kind == 1 else smem_probe[0]
+            rep["smem"].update(measured_peak_gbs=ceil_gbs, measured_frac=smem / ceil_gbs,
+                               measured_pattern="read-modify-write" if kind == 1 else "load")
     else:
         rep.update(achieved=None, frac=None, traffic=None)
     total = max(1e-12, float(sum(prof_ms)))
@@ -824,8 +839,19 @@ def run_ours(args):
     e2e_value = total_solves / T_e2e
 
     # ---- roofline of the dominant kernel (kind, level) ----
+    smem_probe = imask.imask_probe_smem()
     roofline = roofline_report(p, prof_ms, prof_cnt, args.alu_peak_tflops,
-                               args.profile_period)
+                               args.profile_period, smem_probe)
+    # the fused epilogues' algorithmic traffic (7 m + 5 d floats per
+    # iteration: y in/out, b, psi_l in/out, psi_mean in/out; x, phi_0 in/out,
+    # phi_mean in/out) against the measured HBM copy bandwidth
+    bytes_it = 4.0 * (7 * p.m + 5 * p.d)
+    mem_gbs = bytes_it * args.iters * args.steps / T_max / 1e9
+    hbm = measured_peaks().get("hbm_gbs")
+    memory = {"algorithmic_bytes_per_iteration": bytes_it, "achieved_gbs": mem_gbs,
+              "hbm_peak_gbs": hbm, "frac_of_hbm": (mem_gbs / hbm) if hbm else None,
+              "note": "the solve state (about 22 MB) stays in L2; memory is not the bound",
+              "smem_probe_gbs": {"load": smem_probe[0], "read_modify_write": smem_probe[1]}}
 
     # ---- the other iteration variants on the same workload (short runs) ----
     variants = None
@@ -869,6 +895,7 @@ def run_ours(args):
             "launches_plan": int(n_launch_plan),
             "clocks": clk,
             "roofline": roofline,
+            "memory": memory,
             "cpu_baseline": cpu,
             "variants": variants,
         }

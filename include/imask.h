@@ -277,6 +277,13 @@ imask_status imask_rel_distance(int64_t n, const float *a_dev, const float *b_de
  * reset: ms[kind*8 + level], count[kind*8 + level]. */
 imask_status imask_profile_enable(int32_t period);
 imask_status imask_profile_read(double ms[24], int64_t count[24], int32_t reset);
+/* Measured shared-memory ceilings of the current GPU, for roofline reports
+ * (the paper has no counterpart): out[0] = GB/s of conflict-free 32-bit loads,
+ * out[1] = GB/s (read + write bytes) of read-modify-writes of private slots,
+ * the back-projector's access pattern; every SM runs 8 CTAs of 256 threads
+ * with 8 independent access chains each, best of 3 timed launches.
+ * Synchronises.  Errors: INVALID, CUDA. */
+imask_status imask_probe_smem(double out[2], void *stream);
 /* Number of kernels this library has launched in the process so far. */
 int64_t imask_launch_count(void);
 

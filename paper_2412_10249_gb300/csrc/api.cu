@@ -1640,6 +1640,40 @@ imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_
   return IMASK_OK;
 }
 
+imask_status imask_probe_smem(double out[2], void *stream) {
+  if (!out) return fail(IMASK_ERR_INVALID, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int dev = 0, n_sm = 0;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  CK(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "SM count");
+  const int blocks = 8 * n_sm, iters = 4096;
+  void *mem = nullptr;
+  CK(cudaMallocAsync(&mem, 256, st), "cudaMallocAsync(probe)");
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  for (int rmw = 0; rmw < 2 && e == cudaSuccess; ++rmw) {
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+      float ms = 0.0f;
+      if ((e = cudaEventRecord(a, st)) != cudaSuccess) break;
+      if ((e = launch_probe_smem(blocks, iters, rmw, (float *)mem, st)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(b, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+      if ((e = cudaEventElapsedTime(&ms, a, b)) != cudaSuccess) break;
+      if (rep > 0 && ms < best) best = ms;   // the first launch warms up
+    }
+    // bytes moved through shared memory: 4 per load, 8 per read-modify-write
+    const double bytes = (double)blocks * 256 * iters * 8 * (rmw ? 8.0 : 4.0);
+    out[rmw] = bytes / (best * 1e-3) / 1e9;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFreeAsync(mem, st);
+  if (e != cudaSuccess) return cuda_fail(e, "shared-memory probe");
+  return IMASK_OK;
+}
+
 imask_status imask_profile_enable(int32_t period) {
   if (period < 0) return fail(IMASK_ERR_INVALID, "profile period must be >= 0");
   std::lock_guard<std::mutex> lk(g_prof.mu);

@@ -1009,6 +1009,38 @@ __global__ void k_convert(long long n, const void *src, int sf, void *dst, int d
   }
 }
 
+// Shared-memory ceilings for roofline reports: conflict-free 32-bit loads
+// (every warp reads 32 consecutive words) and read-modify-writes of private
+// slots (the back-projector's access pattern).  Eight independent chains per
+// thread; volatile keeps every access.
+constexpr int kProbeWords = 8192;
+__global__ void __launch_bounds__(256) k_probe_smem(int iters, int rmw, float *sink) {
+  __shared__ float buf[kProbeWords];
+  for (int i = threadIdx.x; i < kProbeWords; i += blockDim.x) buf[i] = (float)i;
+  __syncthreads();
+  volatile float *vb = buf;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float acc[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) acc[u] = 0.0f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      // word (row, lane): rows cycle through the array, 32 consecutive words per warp
+      const int row = (w * 8 + u + it * 3) & (kProbeWords / 32 - 1);
+      const int a = row * 32 + lane;
+      if (rmw)
+        vb[a] = vb[a] + 1.0f;
+      else
+        acc[u] += vb[a];
+    }
+  }
+  float t = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) t += acc[u];
+  if (t == -1.0f) sink[0] = t;   // never true; keeps the loads
+}
+
 // psi_mean[q] = sum_l p_l psi_l[q], levels in order
 __global__ void k_table_mean(DevPlan P, const void *psi, int fmt, float *psi_mean) {
   for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < P.m;
@@ -1343,6 +1375,12 @@ cudaError_t launch_convert(long long n, const void *src, int src_fmt, void *dst,
   if (n <= 0) return cudaSuccess;
   count_launch();
   k_convert<<<grid_for(n, 256), 256, 0, st>>>(n, src, src_fmt, dst, dst_fmt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probe_smem(int blocks, int iters, int rmw, float *sink, cudaStream_t st) {
+  count_launch();
+  k_probe_smem<<<blocks, 256, 0, st>>>(iters, rmw, sink);
   return cudaGetLastError();
 }
 

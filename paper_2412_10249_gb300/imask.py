@@ -93,6 +93,7 @@ SIGNATURES = {
     "imask_objective": (_I32, [_VP, _VP, _VP, _DP, _VP]),
     "imask_rel_distance": (_I32, [_I64, _VP, _VP, _DP, _VP]),
     "imask_state_set_storage": (_I32, [_VP, _I32, _VP]),
+    "imask_probe_smem": (_I32, [_DP, _VP]),
     "imask_batch_create": (_I32, [_VP, _I32, _VP]),
     "imask_batch_step": (_I32, [_VP, _I32, _VP]),
     "imask_batch_destroy": (_I32, [_VP]),
@@ -275,6 +276,14 @@ def imask_profile_read(reset: bool = False):
     cnt = (ctypes.c_int64 * 24)()
     _check(lib().imask_profile_read(ms, cnt, 1 if reset else 0))
     return list(ms), list(cnt)
+
+
+def imask_probe_smem(stream=None):
+    """Measured shared-memory ceilings (GB/s): conflict-free loads, private
+    read-modify-writes."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().imask_probe_smem(out, _stream(stream)))
+    return tuple(out)
 
 
 def imask_launch_count() -> int:

@@ -52,3 +52,13 @@ def test_autotuned_plan_keeps_parity(imask, prob):
     s = plan.state(torch.as_tensor(b.ravel().astype(np.float32), device="cuda"), 3)
     s.step(30)
     assert rel(s.get(s.X).double().cpu().numpy(), st["x"]) <= 1e-4
+
+
+def test_shared_memory_probe(imask):
+    # ceilings of the roofline report: positive, below the unit-count bound
+    # (SMs x 128 B per clock at the maximum clock) with some slack
+    load, rmw = imask.imask_probe_smem()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    bound = n_sm * 128 * 2.2e9 / 1e9
+    assert 0.2 * bound < load < 1.1 * bound
+    assert 0.1 * bound < rmw < 1.1 * bound
