@@ -201,7 +201,13 @@ imask_status imask_levels(imask_plan_t plan, uint64_t seed, int64_t k0, int64_t 
 imask_status imask_state_create(imask_plan_t plan, const float *b_dev, uint64_t seed,
                                 imask_state_t *state_out, void *stream);
 /* Advances the state by n_iters iterations (Alg. 1, or the plan's variant) on
- * stream, one launch per kernel. */
+ * stream.  Runs of 8 or more iterations replay a captured CUDA graph of two
+ * iterations (as imask_batch_step does for a batch of this state alone; the
+ * first such call captures it).  With kernel profiling at a period of 4 or
+ * more, the profiled iterations are launched kernel by kernel (so that their
+ * events are recorded) and the pairs between them replay the graph; at
+ * periods 1 to 3 every iteration is launched kernel by kernel.  Results are
+ * the same either way. */
 imask_status imask_step(imask_state_t state, int32_t n_iters, void *stream);
 
 /* Batches of independent solves (the paper has no counterpart; this is the
@@ -213,7 +219,8 @@ imask_status imask_step(imask_state_t state, int32_t n_iters, void *stream);
  * graph is replayed n_iters / 2 times on stream (the iteration counter is read
  * from a device copy held by each state); an odd last iteration runs with
  * plain launches.  The graph is captured again when a state's dual ping-pong
- * parity differs from the captured one (after an odd number of steps).
+ * parity differs from the captured one (after an odd number of steps) or its
+ * buffers moved (imask_state_set_storage).
  * Capture happens inside the call, on a stream the batch owns (relaxed
  * capture mode); the graph is then launched on `stream`, which may be the
  * legacy default stream.  Profiling events are not recorded in graphs.
@@ -233,7 +240,9 @@ imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
  * tables; later iterations use the new format (widening to fp32 is exact: the
  * refinement sweep of a 16-bit solve).  Allocates the new tables with
  * cudaMallocAsync on stream.  INVALID for a state without such tables unless
- * storage is 0.  Not to be called while a batch holding the state is replayed. */
+ * storage is 0.  Graphs captured for the state (its own, or a batch's) are
+ * captured again at their next step.  Not to be called while a batch holding
+ * the state is being stepped from another thread. */
 imask_status imask_state_set_storage(imask_state_t state, int32_t storage, void *stream);
 /* Frees the state's buffers (stream-ordered on the stream last used). */
 imask_status imask_state_destroy(imask_state_t state);

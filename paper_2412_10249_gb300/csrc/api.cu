@@ -145,6 +145,8 @@ struct imask_state_s {
   PadSet pads{};
   long long *k_dev = nullptr;   // device copy of k for graph replays
   bool k_dev_stale = true;      // k advanced by eager launches since the last sync
+  struct imask_batch_s *self_batch = nullptr;   // graph replays of this state alone
+  int gen = 0;                  // bumped when buffers move; captured graphs go stale
 };
 
 struct imask_batch_s {
@@ -155,6 +157,7 @@ struct imask_batch_s {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cur_at_capture;     // ping-pong parity the graph was captured for
+  std::vector<int> gen_at_capture;     // state buffer generations it was captured with
   int unroll = 0;                      // iterations per replay (even)
   int64_t kernels_per_replay = 0;
 };
@@ -1273,6 +1276,7 @@ void batch_release_graph(imask_batch_s *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
   b->cur_at_capture.clear();
+  b->gen_at_capture.clear();
 }
 
 // Captures `unroll` iterations of every state of the batch, each state on its
@@ -1320,7 +1324,11 @@ imask_status batch_capture(imask_batch_s *b, int unroll) {
   b->unroll = unroll;
   b->kernels_per_replay = captured;
   b->cur_at_capture.clear();
-  for (auto *s : b->states) b->cur_at_capture.push_back(s->cur);
+  b->gen_at_capture.clear();
+  for (auto *s : b->states) {
+    b->cur_at_capture.push_back(s->cur);
+    b->gen_at_capture.push_back(s->gen);
+  }
   return IMASK_OK;
 }
 
@@ -1331,6 +1339,51 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
   if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
   cudaStream_t st = (cudaStream_t)stream;
   s->stream = st;
+  // Runs of several iterations replay a captured two-iteration graph (same
+  // kernels, fewer launch gaps).  With kernel profiling every period-th
+  // iteration is launched on its own so that its events are recorded, and the
+  // pairs in between still replay the graph.
+  bool prof_on;
+  int period;
+  {
+    std::lock_guard<std::mutex> lk(g_prof.mu);
+    prof_on = g_prof.on;
+    period = g_prof.period;
+  }
+  if (n_iters >= 8 && (!prof_on || period >= 4)) {
+    if (!s->self_batch) {
+      imask_state_t one[1] = {s};
+      imask_status rc = imask_batch_create(one, 1, &s->self_batch);
+      if (rc != IMASK_OK) return rc;
+    }
+    if (!prof_on) return imask_batch_step(s->self_batch, n_iters, stream);
+    int left = n_iters;
+    while (left > 0) {
+      const int into = (int)(s->k % period);
+      int run = into == 0 ? 1 : std::min(left, period - into);   // up to the next profiled k
+      imask_status rc = IMASK_OK;
+      if (into == 0) {
+        rc = enqueue_iteration(s, st, s->cur, s->k, false, 0);
+        if (rc == IMASK_OK) {
+          s->cur = 1 - s->cur;
+          s->k += 1;
+          s->k_dev_stale = true;
+        }
+      } else {
+        const int pairs = run / 2;
+        if (pairs > 0) rc = imask_batch_step(s->self_batch, 2 * pairs, stream);
+        for (int i = 2 * pairs; i < run && rc == IMASK_OK; ++i) {
+          rc = enqueue_iteration(s, st, s->cur, s->k, false, 0);
+          s->cur = 1 - s->cur;
+          s->k += 1;
+          s->k_dev_stale = true;
+        }
+      }
+      if (rc != IMASK_OK) return rc;
+      left -= run;
+    }
+    return IMASK_OK;
+  }
   for (int it = 0; it < n_iters; ++it) {
     imask_status rc = enqueue_iteration(s, st, s->cur, s->k, false, 0);
     if (rc != IMASK_OK) return rc;
@@ -1386,7 +1439,8 @@ imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
       }
     bool match = b->exec && b->unroll == unroll && b->cur_at_capture.size() == b->states.size();
     for (size_t i = 0; match && i < b->states.size(); ++i)
-      match = b->cur_at_capture[i] == b->states[i]->cur;
+      match = b->cur_at_capture[i] == b->states[i]->cur &&
+              b->gen_at_capture[i] == b->states[i]->gen;
     if (!match) {
       imask_status rc = batch_capture(b, unroll);
       if (rc != IMASK_OK) return rc;
@@ -1473,11 +1527,13 @@ imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *str
   s->psi = mem;
   s->psi_fmt = storage;
   s->stream = st;
+  s->gen += 1;   // graphs captured with the old tables are captured again
   return IMASK_OK;
 }
 
 imask_status imask_state_destroy(imask_state_t s) {
   if (!s) return IMASK_OK;
+  if (s->self_batch) imask_batch_destroy(s->self_batch);
   if (s->psi_block) cudaFreeAsync(s->psi_block, s->stream);
   if (s->block) cudaFreeAsync(s->block, s->stream);
   delete s;

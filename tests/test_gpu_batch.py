@@ -115,3 +115,50 @@ def test_batch_counts_replayed_launches(imask):
     # per state and pair of iterations: 2 x (projector, back-projector, update) + counter
     assert imask.imask_launch_count() - c0 == 5 * 3 * 7
     batch.close()
+
+
+def test_graphs_follow_storage_changes(imask):
+    # a state's own graph and a batch's graph are captured again after its
+    # tables moved (16-bit -> fp32); plain single-iteration steps are the reference
+    plan = imask.Plan(dict(FAN64.params(), mu=0.1, sigma=0.04, storage=2))
+    _, b, _ = inputs.measurements(FAN64, seed=4, noise="none")
+    bt = cuda(b)
+    ref = plan.state(bt, 3)
+    for _ in range(12):
+        ref.step(1)
+    ref.set_storage(0)
+    for _ in range(12):
+        ref.step(1)
+    own = plan.state(bt, 3)
+    own.step(12)              # its own graph
+    own.set_storage(0)
+    own.step(12)
+    a, c = plan.state(bt, 3), plan.state(bt, 5)
+    batch = imask.Batch([a, c])
+    batch.step(12)
+    a.set_storage(0)
+    batch.step(12)
+    torch.cuda.synchronize()
+    assert torch.equal(own.get(own.X), ref.get(ref.X))
+    assert torch.equal(a.get(a.X), ref.get(ref.X))
+    batch.close()
+
+
+def test_profiled_steps_equal_graph_steps(imask):
+    # with profiling at period 8 the profiled iterations run kernel by kernel
+    # and the pairs between them replay the graph; the iterates are the same
+    plan = imask.Plan(dict(FAN64.params(), mu=0.1, sigma=0.04))
+    _, b, _ = inputs.measurements(FAN64, seed=6, noise="none")
+    bt = cuda(b)
+    x_graph = plan.solve(bt, 8, 37)
+    imask.imask_profile_read(reset=True)
+    imask.imask_profile_enable(8)
+    try:
+        x_prof = plan.solve(bt, 8, 37)
+        torch.cuda.synchronize()
+        ms, cnt = imask.imask_profile_read(reset=True)
+    finally:
+        imask.imask_profile_enable(0)
+    assert torch.equal(x_graph, x_prof)
+    # iterations 0, 8, 16, 24, 32 were profiled: 5 of each kind
+    assert sum(cnt[0:8]) == 5 and sum(cnt[8:16]) == 5 and sum(cnt[16:24]) == 5
