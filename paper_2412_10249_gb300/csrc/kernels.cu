@@ -431,19 +431,6 @@ __device__ __forceinline__ float *bp_y(float4 *raw, int b) {
 }
 __device__ __forceinline__ int2 *bp_vinfo(float4 *raw) { return (int2 *)bp_y(raw, 2); }
 
-// last index v in [0, n) with pref[v] <= e (pref non-decreasing, pref[0] = 0)
-__device__ __forceinline__ int find_view(const int *pref, int n, int e) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (pref[mid] <= e)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
-  return lo;
-}
-
 // Block-wide exclusive scan of n counters held in a[0..n) (in place); a[n]
 // receives the total, which is also returned.
 __device__ int scan_counts(int *a, int n) {
@@ -539,6 +526,10 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
   const int nch = (NR + BP_SLOTS - 1) / BP_SLOTS;
 
   // raw data of chunk k into buffer b
+  // view of a thread's current list entry: chunks are staged in order, so a
+  // thread's entries only move forward and the search starts from the last
+  // view found (galloping, then bisection)
+  int vs = 0;
   auto stage = [&](int k, int b) {
     float4 *win = bp_win(bp_raw, b);
     float2 *lo = bp_lo(bp_raw, b);
@@ -546,7 +537,21 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
     for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
       const int e = k * BP_SLOTS + sl;
       if (e >= NR) break;
-      const int v = find_view(pref, nv, e);
+      // gallop forward from the previous view, then bisect the last step
+      int step = 1;
+      while (vs + step < nv && pref[vs + step] <= e) {
+        vs += step;
+        step <<= 1;
+      }
+      int hi = min(vs + step, nv) - 1;   // pref[hi + 1] > e or hi = nv - 1
+      while (vs < hi) {
+        const int mid = (vs + hi + 1) >> 1;
+        if (pref[mid] <= e)
+          vs = mid;
+        else
+          hi = mid - 1;
+      }
+      const int v = vs;
       const int kk = e - pref[v];
       const int2 vi = vinfo[v];
       cp_async(win + sl, P.rays + vi.x + kk, 16);
