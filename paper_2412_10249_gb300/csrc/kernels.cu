@@ -593,8 +593,11 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
       const float4 e = win[sl];
       const float q = fmaf(dseg, e.y, e.x);
       const float tq = __fadd_rd(q, kMagic);
-      const int slot =
-          min(max(__float_as_int(tq) - kMagicBits + __float_as_int(e.w), 0), BP_ACC - 2);
+      // one unsigned clamp: rows off the segment on either side (negative
+      // slots wrap to large unsigned values) land in the top guard slots,
+      // which the epilogue never reads
+      const int slot = (int)min((unsigned)(__float_as_int(tq) - kMagicBits + __float_as_int(e.w)),
+                                (unsigned)(BP_ACC - 2));
       const float f = q - (tq - kMagic);
       const float w1 = f * e.z;
       // plain read-modify-writes: shared-memory atomic adds on the same
