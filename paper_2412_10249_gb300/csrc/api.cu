@@ -117,6 +117,7 @@ struct imask_plan_s {
   float4 *d_rays = nullptr;
   float2 *d_rays_lo = nullptr;
   ViewInfo *d_views = nullptr;
+  int *d_bp_order = nullptr;
   size_t gcap = 0;   // floats of the back-projector's partial-sum buffer
   unsigned int *d_err = nullptr;
   std::vector<int> split, first_x;
@@ -302,8 +303,20 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   const int sh = ell > 0 ? ell : 0;
   g.nl = d.n >> sh;
   g.ls = g.nl + IMASK_PAD + IMASK_PAD_END;
-  int tc = (FP_STAGE_FLOATS / g.ls) & ~3;
-  tc = std::min(32, std::max(4, tc));
+  // lines per TMA strip: a multiple of 4 that fits a stage buffer; among those,
+  // the one with the least padding (every padded line is a full line of
+  // samples for all rays) plus half a line per strip hand-over
+  const int tmax = std::min(32, std::max(4, (FP_STAGE_FLOATS / g.ls) & ~3));
+  int tc = tmax;
+  double best = 1e30;
+  for (int t = tmax; t >= 4; t -= 4) {
+    const int strips = (g.nl + t - 1) / t;
+    const double cost = (double)strips * t + 0.5 * strips;
+    if (cost < best - 1e-9) {
+      best = cost;
+      tc = t;
+    }
+  }
   g.tc = tc;
   g.lines = (g.nl + tc - 1) / tc * tc;
   g.inv2l = (float)ldexp(1.0, -sh);
@@ -710,6 +723,60 @@ StateLayout state_layout(const imask_plan_s *p) {
 
 }  // namespace
 
+namespace {
+
+// Back-projector CTA order per level (only the order changes, not the result):
+// every (role, tile) is weighted by the rays its windows hold over a sample of
+// the views, computed in FP64 with the kernel's window rule (bins of the tile
+// box's corners, widened by one pixel across), and sorted heaviest first.
+std::vector<int> bp_tile_order(const DevPlan &dp, const std::vector<ViewInfo> &views,
+                               const imask_desc &d) {
+  std::vector<int> all;
+  const int na = d.n_angles;
+  const int stride = std::max(1, na / 90);
+  const double pitch = 1.0 / (double)dp.inv_pitch, center = dp.center;
+  auto bin = [&](double c, double s, double x, double y) {
+    if (d.geometry == 0) return (x * c + y * s) / pitch + center;
+    const double num = -x * s + y * c, den = d.src_dist - (x * c + y * s);
+    return (d.src_dist + d.det_dist) * num / den / pitch + center;
+  };
+  for (int li = 0; li <= d.levels; ++li) {
+    const LevelGeom &g = dp.lg[li];
+    const int nm = g.bp_nm, nc = g.bp_nc, ntile = nm * nc;
+    const double W = d.fov, hl = W / (double)g.nl;
+    std::vector<std::pair<double, int>> wts;
+    for (int role = 0; role < 2; ++role)
+      for (int tile = 0; tile < ntile; ++tile) {
+        const int mb = tile % nm, cb = tile / nm;
+        const int m0 = mb * BP_W, m1 = std::min(m0 + BP_W, g.nl) - 1;
+        const int c0 = cb * BP_SEG, c1 = std::min(c0 + BP_SEG, g.nl) - 1;
+        const double mlo = -0.5 * W + (m0 + 0.5) * hl, mhi = -0.5 * W + (m1 + 0.5) * hl;
+        const double clo = -0.5 * W + (c0 + 0.5) * hl - hl, chi = -0.5 * W + (c1 + 0.5) * hl + hl;
+        double w = 0.0;
+        for (int a = 0; a < na; a += stride) {
+          const ViewInfo &V = views[a];
+          double mn = 1e30, mx = -1e30;
+          for (int k = 0; k < 4; ++k) {
+            const double mc = (k & 1) ? mhi : mlo, cc = (k & 2) ? chi : clo;
+            const double j = role == 0 ? bin(V.c, V.s, mc, cc) : bin(V.c, V.s, cc, mc);
+            mn = std::min(mn, j);
+            mx = std::max(mx, j);
+          }
+          const int j0 = role == 0 ? V.xj0 : V.yj0, j1 = role == 0 ? V.xj1 : V.yj1;
+          const double lo = std::max(std::ceil(mn), (double)j0);
+          const double hi = std::min(std::floor(mx), (double)(j1 - 1));
+          if (hi >= lo) w += hi - lo + 1.0;
+        }
+        wts.push_back(std::make_pair(-w, role * ntile + tile));
+      }
+    std::stable_sort(wts.begin(), wts.end());
+    for (auto &e : wts) all.push_back(e.second);
+  }
+  return all;
+}
+
+}  // namespace
+
 // ===================================================================================
 // C ABI
 // ===================================================================================
@@ -936,12 +1003,21 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
     imask_plan_destroy(p);
     return fail(IMASK_ERR_SHAPE, "too many views per back-projector CTA for shared memory");
   }
+  const std::vector<int> order = bp_tile_order(dp, views, *desc);
+  {
+    int off = 0;
+    for (int li = 0; li <= r; ++li) {
+      dp.lg[li].bp_order_off = off;
+      off += 2 * dp.lg[li].bp_nm * dp.lg[li].bp_nc;
+    }
+  }
 
   cudaError_t e;
   if ((e = cudaMalloc(&p->d_rays, rays.size() * sizeof(float4))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_rays_lo, rays_lo.size() * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_views, views.size() * sizeof(ViewInfo))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess) {
+      (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_bp_order, order.size() * sizeof(int))) != cudaSuccess) {
     imask_plan_destroy(p);
     return cuda_fail(e, "cudaMalloc(plan)");
   }
@@ -961,6 +1037,8 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(p->d_views, views.data(), views.size() * sizeof(ViewInfo),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p->d_bp_order, order.data(), order.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess) {
     cudaStreamSynchronize(st);
@@ -971,6 +1049,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.rays = p->d_rays;
   dp.rays_lo = p->d_rays_lo;
   dp.views = p->d_views;
+  dp.bp_order = p->d_bp_order;
 
   rc = p->desc.autotune ? autotune_bp(p, st) : IMASK_OK;
   if (rc == IMASK_OK) rc = plan_constants(p, st);
@@ -992,6 +1071,7 @@ imask_status imask_plan_destroy(imask_plan_t p) {
   if (p->d_rays_lo) cudaFree(p->d_rays_lo);
   if (p->d_views) cudaFree(p->d_views);
   if (p->d_err) cudaFree(p->d_err);
+  if (p->d_bp_order) cudaFree(p->d_bp_order);
   delete p;
   return IMASK_OK;
 }
@@ -1015,8 +1095,11 @@ imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
   info->autotuned = p->autotuned ? 1 : 0;
   for (int l = 0; l < IMASK_MAX_LEVELS; ++l)
     info->bp_view_groups[l] = l < p->desc.levels ? p->dp.lg[l + 1].bp_vgo : 0;
+  int64_t n_order = 0;
+  for (int li = 0; li <= p->desc.levels; ++li) n_order += 2 * p->dp.lg[li].bp_nm * p->dp.lg[li].bp_nc;
   info->plan_bytes = (int64_t)(p->dp.m * (sizeof(float4) + sizeof(float2)) +
-                               p->dp.n_angles * sizeof(ViewInfo) + sizeof(unsigned int));
+                               p->dp.n_angles * sizeof(ViewInfo) + sizeof(unsigned int)) +
+                     n_order * (int64_t)sizeof(int);
   return IMASK_OK;
 }
 

@@ -49,6 +49,7 @@ struct LevelGeom {
   int bp_nc;       // back-projector tiles across it (BP_SEG lines each)
   int bp_vgo;      // back-projector view groups per major axis (partial sums)
   int bp_nv;       // largest number of views handled by one CTA
+  int bp_order_off;  // this level's entries in DevPlan::bp_order
 };
 
 // Everything the kernels need about a plan (passed by value).
@@ -66,6 +67,9 @@ struct DevPlan {
   const float4 *rays;      // ray list: (a_hi, t_hi, g, sino index bits)
   const float2 *rays_lo;   // ray list: (a_lo, t_lo), the low words of a and t
   const ViewInfo *views;   // per view
+  // back-projector CTA order per level: (role * tiles + tile) codes, heaviest
+  // (most rays to apply) first; the view groups of one code are adjacent
+  const int *bp_order;
 };
 
 // Padded level images: for every level index li (0: level -1, ell + 1: ell),

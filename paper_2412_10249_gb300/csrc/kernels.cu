@@ -474,11 +474,12 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
   const LevelGeom G = P.lg[ell + 1];
   const int nm = G.bp_nm, nc = G.bp_nc, vgo = G.bp_vgo;
   const int ntile = nm * nc;
-  const int role = (int)blockIdx.x >= ntile * vgo ? 1 : 0;   // 0: x-major rays, 1: y-major
-  const int bid = (int)blockIdx.x - role * ntile * vgo;
-  const int vg = bid / ntile;
-  if (vg >= vgo) return;
-  const int tile = bid % ntile;
+  // CTAs go heaviest (role, tile) first so that light tiles fill the last wave
+  const int rank = (int)blockIdx.x / vgo, vg = (int)blockIdx.x % vgo;
+  if (rank >= 2 * ntile) return;
+  const int code = P.bp_order[G.bp_order_off + rank];
+  const int role = code >= ntile ? 1 : 0;   // 0: x-major rays, 1: y-major
+  const int tile = code - role * ntile;
   const int mb = tile % nm, cb = tile / nm;   // march block (BP_W lines), cross block (BP_SEG)
   const int tid = threadIdx.x;
   const int a0 = (int)(((long long)vg * P.n_angles) / vgo);

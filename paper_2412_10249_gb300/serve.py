@@ -138,9 +138,11 @@ class Server:
 
     @staticmethod
     def plan_bytes_estimate(params: dict) -> int:
-        # the plan's device tables: 24 bytes per ray, 32 per view, an error flag
+        # the plan's device tables: 24 bytes per ray, 32 per view, an error
+        # flag, and the back-projector's tile order (under 4 x 2 n^2/512 bytes)
         m = int(params["n_angles"]) * int(params["n_det"])
-        return 24 * m + 32 * int(params["n_angles"]) + 4
+        n = int(params["n"])
+        return 24 * m + 32 * int(params["n_angles"]) + 4 + 16 * (n // 16 + 1) * (n // 32 + 1)
 
     def _prepare(self, req: Request) -> bool:
         """Starts the plan build (memory permitting) and the sinogram; False
