@@ -329,9 +329,13 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
   return g;
 }
 
+#ifndef IMASK_UPD_TILE_CAP
+#define IMASK_UPD_TILE_CAP 32
+#endif
+
 int update_tile(int n, int levels) {
   const int blk = 1 << (levels - 1);
-  const int cap = std::max(32, blk);
+  const int cap = std::max(IMASK_UPD_TILE_CAP, blk);
   int best = blk;
   for (int k = 1; blk * k <= cap; ++k)
     if (n % (blk * k) == 0) best = blk * k;
