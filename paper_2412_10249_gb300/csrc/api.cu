@@ -143,7 +143,14 @@ struct imask_state_s {
         *tv = nullptr, *x_prev = nullptr;
   long long phic_off[IMASK_MAX_LEVELS] = {0};
   SnapArgs snap{};   // dual_tables = 1: sketched projector inputs per level
-  PadSet pads{};
+  // padded sketch images: the projector of iteration k reads pads[k % 2], the
+  // update writes the next sketch into pads[(k + 1) % 2] (one set, both
+  // entries equal, for Alg. 7, whose launches run in order anyway)
+  PadSet pads[2] = {};
+  // Alg. 1: the projector runs on aux, concurrently with the back-projector
+  // and the update on the caller's stream (fork / join events)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_fp = nullptr;
   long long *k_dev = nullptr;   // device copy of k for graph replays
   bool k_dev_stale = true;      // k advanced by eager launches since the last sync
   struct imask_batch_s *self_batch = nullptr;   // graph replays of this state alone
@@ -686,6 +693,7 @@ struct StateLayout {
          g = 0, tv = 0, total = 0;
   size_t snap[IMASK_MAX_LEVELS] = {0}, phic[IMASK_MAX_LEVELS] = {0};
   size_t T[IMASK_MAX_LEVELS + 1] = {0}, R[IMASK_MAX_LEVELS + 1] = {0};
+  size_t T2[IMASK_MAX_LEVELS + 1] = {0}, R2[IMASK_MAX_LEVELS + 1] = {0};   // Alg. 1 only
 };
 
 StateLayout state_layout(const imask_plan_s *p) {
@@ -720,6 +728,10 @@ StateLayout state_layout(const imask_plan_s *p) {
   for (int li = 1; li <= r; ++li) {
     L.T[li] = cv.take(pad_floats(p->dp.lg[li]));
     L.R[li] = cv.take(pad_floats(p->dp.lg[li]));
+    if (!seq) {
+      L.T2[li] = cv.take(pad_floats(p->dp.lg[li]));
+      L.R2[li] = cv.take(pad_floats(p->dp.lg[li]));
+    }
   }
   L.total = cv.off;
   return L;
@@ -1264,8 +1276,10 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   for (int l = 1; l < r; ++l) s->phic_off[l] = (long long)o_phic[l];
   s->tv = p->desc.reg != 0 ? B + o_tv : nullptr;
   for (int li = 1; li <= r; ++li) {
-    s->pads.T[li] = B + o_T[li];
-    s->pads.R[li] = B + o_R[li];
+    s->pads[0].T[li] = B + o_T[li];
+    s->pads[0].R[li] = B + o_R[li];
+    s->pads[1].T[li] = L.T2[li] ? B + L.T2[li] : s->pads[0].T[li];
+    s->pads[1].R[li] = L.R2[li] ? B + L.R2[li] : s->pads[0].R[li];
   }
   if ((e = cudaMemsetAsync(mem, 0, cv.off * sizeof(float), st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(s->b, b_dev, m * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
@@ -1273,6 +1287,13 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
     cudaFreeAsync(mem, st);
     delete s;
     return cuda_fail(e, "state init");
+  }
+  if (p->desc.variant == 0 &&
+      ((e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&s->ev_fp, cudaEventDisableTiming)) != cudaSuccess)) {
+    imask_state_destroy(s);
+    return cuda_fail(e, "state streams");
   }
   *state_out = s;
   return IMASK_OK;
@@ -1315,11 +1336,25 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   D.psi_mean = s->psi_mean;
   D.sigma = sigma;
   D.inv_1ps = inv_1ps;
+  // Alg. 1: the projector (writes y^{k+1}, the psi tables) and the
+  // back-projector (reads y^k) are independent; the projector runs on the
+  // state's second stream, forked after the previous update and joined at the
+  // end of the iteration.  Its sketch input sits in its own buffer set, so the
+  // update may write the next sketch meanwhile.
+  // (profiled iterations stay in order, so that each kernel's events time it
+  // alone rather than sharing the GPU with the other)
+  const bool fork = !seq && s->aux && !prof;
+  const cudaStream_t sfp = fork ? s->aux : st;
+  if (fork) {
+    CK(cudaEventRecord(s->ev_fork, st), "fork");
+    CK(cudaStreamWaitEvent(s->aux, s->ev_fork, 0), "fork");
+  }
   {
-    ProfScope ps(0, lvl, st, prof);
-    CK(launch_fp(P, sel, s->pads, nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, st),
+    ProfScope ps(0, lvl, sfp, prof);
+    CK(launch_fp(P, sel, s->pads[cur], nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, sfp),
        "projector launch");
   }
+  if (fork) CK(cudaEventRecord(s->ev_fp, s->aux), "join");
   // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
   {
     ProfScope ps(1, lvl_x, st, prof);
@@ -1342,7 +1377,8 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   A.snap = s->snap;
   {
     ProfScope ps(2, lvl_x, st, prof);
-    CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads, st), "update launch");
+    CK(launch_update(P, sel, A, p->desc.reg == 0 ? 1 : 0, s->pads[1 - cur], st),
+       "update launch");
   }
   if (p->desc.reg != 0) {
     CK(launch_reg_prox(p, tau, s->x, s->tv, st), "TV prox launch");
@@ -1354,8 +1390,9 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
       ex.x_prev = s->x_prev;
       ex.theta = theta;
     }
-    CK(launch_sketch(P, nxt, s->x, s->pads, ex, s->snap, st), "sketch launch");
+    CK(launch_sketch(P, nxt, s->x, s->pads[1 - cur], ex, s->snap, st), "sketch launch");
   }
+  if (fork) CK(cudaStreamWaitEvent(st, s->ev_fp, 0), "join");
   return IMASK_OK;
 }
 
@@ -1621,6 +1658,13 @@ imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *str
 imask_status imask_state_destroy(imask_state_t s) {
   if (!s) return IMASK_OK;
   if (s->self_batch) imask_batch_destroy(s->self_batch);
+  if (s->aux) {
+    // the last projector on aux is joined into s->stream, so the frees below,
+    // ordered on s->stream, come after it
+    cudaStreamDestroy(s->aux);
+  }
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_fp) cudaEventDestroy(s->ev_fp);
   if (s->psi_block) cudaFreeAsync(s->psi_block, s->stream);
   if (s->block) cudaFreeAsync(s->block, s->stream);
   delete s;
