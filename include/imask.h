@@ -140,6 +140,8 @@ typedef struct {
  * FP64 power method on the device and the Thm. 3 solver on the host.
  * Synchronises.  Errors: INVALID, SHAPE, OOM, CUDA. */
 imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out);
+/* Frees a plan.  Synchronises the device first (states of the plan may have
+ * work in flight on any stream); destroy the plan's states before it. */
 imask_status imask_plan_destroy(imask_plan_t plan);
 imask_status imask_plan_get_info(imask_plan_t plan, imask_plan_info *info);
 

@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <string>
@@ -61,8 +62,8 @@ struct ProfRec {
 
 struct Profiler {
   std::mutex mu;
-  bool on = false;
-  int period = 0;   // imask_step times the iterations with k % period == 0
+  std::atomic<bool> on{false};
+  std::atomic<int> period{0};   // imask_step times the iterations with k % period == 0
   std::vector<cudaEvent_t> pool;
   std::vector<ProfRec> pending;
   double ms[24] = {0};
@@ -1321,7 +1322,8 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   sel.k = k;
   sel.k_dev = graph ? s->k_dev : nullptr;
   sel.k_add = k_add;
-  const bool prof = !graph && g_prof.on && g_prof.period > 0 && k % g_prof.period == 0;
+  const int pp = g_prof.period.load();
+  const bool prof = !graph && g_prof.on.load() && pp > 0 && k % pp == 0;
   const int lvl = prof ? lvl_host_draw(P, s->seed, k) : 0;
   const int lvl_x = prof ? lvl_host_draw(P, s->seed_x, k) : 0;
   // dual half: projector on the sketch of x^k (Alg. 1) or xbar^k (Alg. 7)
@@ -1471,8 +1473,8 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
   int period;
   {
     std::lock_guard<std::mutex> lk(g_prof.mu);
-    prof_on = g_prof.on;
-    period = g_prof.period;
+    prof_on = g_prof.on.load();
+    period = g_prof.period.load();
   }
   if (n_iters >= 8 && (!prof_on || period >= 4)) {
     if (!s->self_batch) {
