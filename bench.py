@@ -155,13 +155,17 @@ def dist_barrier(world: int):
 # ---------------------------------------------------------------------------------
 # reference arm: the FP64 oracle on host cores
 # ---------------------------------------------------------------------------------
-def oracle_sample(p: inputs.Problem, params: dict, b: np.ndarray, seed: int, iters: int):
-    """Runs `iters` oracle iterations of the workload; returns (seconds, samples)."""
+def oracle_sample(p: inputs.Problem, params: dict, b: np.ndarray, seed: int, iters: int,
+                  want_x: bool = False):
+    """Runs `iters` oracle iterations of the workload; returns (seconds,
+    samples) and, with want_x, the oracle's iterate."""
     from oracle import Oracle
     o = Oracle(**params)
     t0 = time.perf_counter()
-    _, lv = o.run(b, seed, iters)
+    st, lv = o.run(b, seed, iters)
     dt = time.perf_counter() - t0
+    if want_x:
+        return dt, float(samples_per_iteration(p, lv).sum()), st["x"]
     return dt, float(samples_per_iteration(p, lv).sum())
 
 
@@ -861,9 +865,17 @@ def run_ours(args):
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
+    oracle_err = None
     if rank == 0 and not args.no_cpu_baseline:
         params = dict(p.params(), mu=info["mu"], sigma=info["sigma"])
-        dt, sm = oracle_sample(p, params, b.ravel(), 0, args.cpu_iters)
+        dt, sm, x_orc = oracle_sample(p, params, b.ravel(), 0, args.cpu_iters, want_x=True)
+        # the timed form against the FP64 oracle on the same seed and iterations
+        with torch.cuda.stream(stream):
+            x_gpu = plan.solve(bt, 0, args.cpu_iters, stream=stream)
+        torch.cuda.synchronize()
+        xg = x_gpu.double().cpu().numpy()
+        oracle_err = {"iters": args.cpu_iters, "seed": 0,
+                      "rel_l2": float(np.linalg.norm(xg - x_orc) / np.linalg.norm(x_orc))}
         per_solve = expected_samples_per_solve(p)
         cpu = {"value": sm / per_solve / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_iters} FP64 oracle iterations of the fan512 solve "
@@ -887,6 +899,7 @@ def run_ours(args):
             "gsamples_per_s": gs,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "rel_err_vs_plain_fp32": rel_err_plain,
+            "rel_err_vs_fp64_oracle": oracle_err,
             "wall_s": wall,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 4 * p.m,
                     "d2h_bytes_per_step": 4 * p.d},
