@@ -152,6 +152,12 @@ struct imask_state_s {
   // and the update on the caller's stream (fork / join events)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_fp = nullptr;
+  // Alg. 1 across iterations: the back-projector of k + 1 runs on aux2 as soon
+  // as the projector of k is done, beside the update of k; its partial images
+  // alternate between g and g2 so the update of k can still read its own
+  cudaStream_t aux2 = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_bp = nullptr, ev_upd[2] = {nullptr, nullptr};
+  float *g2 = nullptr;
   long long *k_dev = nullptr;   // device copy of k for graph replays
   bool k_dev_stale = true;      // k advanced by eager launches since the last sync
   struct imask_batch_s *self_batch = nullptr;   // graph replays of this state alone
@@ -691,7 +697,7 @@ namespace {
 // Float offsets of the parts of a state's single device allocation.
 struct StateLayout {
   size_t x = 0, y0 = 0, y1 = 0, b = 0, psi = 0, psim = 0, phi0 = 0, phim = 0, xprev = 0, kdev = 0,
-         g = 0, tv = 0, total = 0;
+         g = 0, g2 = 0, tv = 0, total = 0;
   size_t snap[IMASK_MAX_LEVELS] = {0}, phic[IMASK_MAX_LEVELS] = {0};
   size_t T[IMASK_MAX_LEVELS + 1] = {0}, R[IMASK_MAX_LEVELS + 1] = {0};
   size_t T2[IMASK_MAX_LEVELS + 1] = {0}, R2[IMASK_MAX_LEVELS + 1] = {0};   // Alg. 1 only
@@ -721,6 +727,7 @@ StateLayout state_layout(const imask_plan_s *p) {
   L.xprev = (seq && p->desc.reg != 0) ? cv.take(d) : 0;
   L.kdev = cv.take(2);   // one 64-bit counter
   L.g = cv.take(p->gcap);
+  L.g2 = seq ? 0 : cv.take(p->gcap);
   for (int l = 1; l < r; ++l) {
     const size_t nl = (size_t)p->dp.lg[l + 1].nl;
     L.phic[l] = cv.take(nl * nl);
@@ -1273,6 +1280,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   s->phi0 = B + o_phi0;
   s->phi_mean = B + o_phim;
   s->g = B + o_g;
+  s->g2 = L.g2 ? B + L.g2 : s->g;
   s->phic = B;
   for (int l = 1; l < r; ++l) s->phic_off[l] = (long long)o_phic[l];
   s->tv = p->desc.reg != 0 ? B + o_tv : nullptr;
@@ -1291,8 +1299,13 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   }
   if (p->desc.variant == 0 &&
       ((e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+       (e = cudaStreamCreateWithFlags(&s->aux2, cudaStreamNonBlocking)) != cudaSuccess ||
        (e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-       (e = cudaEventCreateWithFlags(&s->ev_fp, cudaEventDisableTiming)) != cudaSuccess)) {
+       (e = cudaEventCreateWithFlags(&s->ev_fp, cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&s->ev_start, cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&s->ev_bp, cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&s->ev_upd[0], cudaEventDisableTiming)) != cudaSuccess ||
+       (e = cudaEventCreateWithFlags(&s->ev_upd[1], cudaEventDisableTiming)) != cudaSuccess)) {
     imask_state_destroy(s);
     return cuda_fail(e, "state streams");
   }
@@ -1306,8 +1319,17 @@ namespace {
 // writing the dual iterate pair selected by `cur`.  graph: the kernels take the
 // iteration counter from the state's device counter plus k_add (for captured
 // graphs) and no profiling events are recorded; otherwise the counter is k.
+//
+// Alg. 1 runs on three streams of the state: the projector of k on aux, its
+// back-projector on aux2, the update on st.  Within a sequence of iterations
+// (pos 0 .. last) the projector of k waits for the update of k - 1 (its sketch),
+// the back-projector of k for the projector of k - 1 (y^k) and for the update
+// of k - 2 (which read the partial-image buffer it overwrites), the update of k
+// for the back-projector of k; the sequence starts after everything before it
+// on st and ends with st joined to both side streams.  Profiled iterations run
+// in order on st (one-iteration sequences).
 imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur, long long k,
-                               bool graph, int k_add) {
+                               bool graph, int k_add, int pos = 0, bool last = true) {
   const imask_plan_s *p = s->plan;
   const DevPlan &P = p->dp;
   const bool seq = p->desc.variant == 1;
@@ -1326,6 +1348,30 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   const bool prof = !graph && g_prof.on.load() && pp > 0 && k % pp == 0;
   const int lvl = prof ? lvl_host_draw(P, s->seed, k) : 0;
   const int lvl_x = prof ? lvl_host_draw(P, s->seed_x, k) : 0;
+  const bool fork = !seq && s->aux && !prof;
+  if (prof) {
+    pos = 0;
+    last = true;
+  }
+  const cudaStream_t sfp = fork ? s->aux : st, sbp = fork ? s->aux2 : st;
+  // partial images of this iteration's back-projection (alternating with the
+  // iteration parity, which equals cur, in Alg. 1)
+  float *g = cur != 0 ? s->g2 : s->g;
+  if (fork) {
+    if (pos == 0) {
+      CK(cudaEventRecord(s->ev_start, st), "fork");
+      CK(cudaStreamWaitEvent(s->aux, s->ev_start, 0), "fork");
+      CK(cudaStreamWaitEvent(s->aux2, s->ev_start, 0), "fork");
+    } else {
+      // projector of k - 1 done (y^k); update of k - 2 done with the buffer g
+      // (when k - 2 is in this sequence; earlier work is behind the start)
+      CK(cudaStreamWaitEvent(s->aux2, s->ev_fp, 0), "order");
+      if (pos >= 2) CK(cudaStreamWaitEvent(s->aux2, s->ev_upd[cur], 0), "order");
+      // update of k - 1 done (the sketch the projector reads)
+      CK(cudaEventRecord(s->ev_fork, st), "order");
+      CK(cudaStreamWaitEvent(s->aux, s->ev_fork, 0), "order");
+    }
+  }
   // dual half: projector on the sketch of x^k (Alg. 1) or xbar^k (Alg. 7)
   // prepared by the previous iteration, fused with the zeta and y updates
   DualArgs D{};
@@ -1338,33 +1384,24 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   D.psi_mean = s->psi_mean;
   D.sigma = sigma;
   D.inv_1ps = inv_1ps;
-  // Alg. 1: the projector (writes y^{k+1}, the psi tables) and the
-  // back-projector (reads y^k) are independent; the projector runs on the
-  // state's second stream, forked after the previous update and joined at the
-  // end of the iteration.  Its sketch input sits in its own buffer set, so the
-  // update may write the next sketch meanwhile.
-  // (profiled iterations stay in order, so that each kernel's events time it
-  // alone rather than sharing the GPU with the other)
-  const bool fork = !seq && s->aux && !prof;
-  const cudaStream_t sfp = fork ? s->aux : st;
-  if (fork) {
-    CK(cudaEventRecord(s->ev_fork, st), "fork");
-    CK(cudaStreamWaitEvent(s->aux, s->ev_fork, 0), "fork");
-  }
   {
     ProfScope ps(0, lvl, sfp, prof);
     CK(launch_fp(P, sel, s->pads[cur], nullptr, D, p->n_cta_x, p->n_cta_y, p->d_err, sfp),
        "projector launch");
   }
-  if (fork) CK(cudaEventRecord(s->ev_fp, s->aux), "join");
+  if (fork) CK(cudaEventRecord(s->ev_fp, s->aux), "order");
   // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
   {
-    ProfScope ps(1, lvl_x, st, prof);
-    CK(launch_bp(P, sel, seq ? s->y[1 - cur] : s->y[cur], s->g, p->d_err, st),
+    ProfScope ps(1, lvl_x, sbp, prof);
+    CK(launch_bp(P, sel, seq ? s->y[1 - cur] : s->y[cur], g, p->d_err, sbp),
        "back-projector launch");
   }
+  if (fork) {
+    CK(cudaEventRecord(s->ev_bp, s->aux2), "order");
+    CK(cudaStreamWaitEvent(st, s->ev_bp, 0), "order");
+  }
   PrimalArgs A{};
-  A.g = s->g;
+  A.g = g;
   A.x = s->x;
   A.phi0 = s->phi0;
   A.phic = s->phic;
@@ -1394,9 +1431,18 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
     }
     CK(launch_sketch(P, nxt, s->x, s->pads[1 - cur], ex, s->snap, st), "sketch launch");
   }
-  if (fork) CK(cudaStreamWaitEvent(st, s->ev_fp, 0), "join");
+  if (fork) {
+    CK(cudaEventRecord(s->ev_upd[cur], st), "order");
+    if (last) CK(cudaStreamWaitEvent(st, s->ev_fp, 0), "join");
+  }
   return IMASK_OK;
 }
+
+// Iterations per captured graph (even, so that the dual ping-pong returns to
+// its start).  Within a graph the back-projector of one iteration overlaps the
+// update of the previous one; replays are serialised, so longer graphs keep
+// that overlap for more of the iterations.
+constexpr int kGraphUnroll = 4;
 
 void batch_release_graph(imask_batch_s *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1420,7 +1466,7 @@ imask_status batch_capture(imask_batch_s *b, int unroll) {
     if ((e = cudaStreamWaitEvent(bs, b->fork, 0)) != cudaSuccess) break;
     int cur = s->cur;
     for (int u = 0; u < unroll && rc == IMASK_OK; ++u) {
-      rc = enqueue_iteration(s, bs, cur, 0, true, u);
+      rc = enqueue_iteration(s, bs, cur, 0, true, u, u, u == unroll - 1);
       cur = 1 - cur;
     }
     if (rc != IMASK_OK) break;
@@ -1496,9 +1542,9 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
           s->k_dev_stale = true;
         }
       } else {
-        const int pairs = run / 2;
-        if (pairs > 0) rc = imask_batch_step(s->self_batch, 2 * pairs, stream);
-        for (int i = 2 * pairs; i < run && rc == IMASK_OK; ++i) {
+        const int units = run / kGraphUnroll;
+        if (units > 0) rc = imask_batch_step(s->self_batch, kGraphUnroll * units, stream);
+        for (int i = kGraphUnroll * units; i < run && rc == IMASK_OK; ++i) {
           rc = enqueue_iteration(s, st, s->cur, s->k, false, 0);
           s->cur = 1 - s->cur;
           s->k += 1;
@@ -1554,7 +1600,7 @@ imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
   if (!b) return fail(IMASK_ERR_INVALID, "NULL batch");
   if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
   cudaStream_t st = (cudaStream_t)stream;
-  const int unroll = 2;
+  const int unroll = kGraphUnroll;
   const int replays = n_iters / unroll;
   if (replays > 0) {
     // bring the device counters up to date with eager steps taken meanwhile
@@ -1660,13 +1706,12 @@ imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *str
 imask_status imask_state_destroy(imask_state_t s) {
   if (!s) return IMASK_OK;
   if (s->self_batch) imask_batch_destroy(s->self_batch);
-  if (s->aux) {
-    // the last projector on aux is joined into s->stream, so the frees below,
-    // ordered on s->stream, come after it
-    cudaStreamDestroy(s->aux);
-  }
-  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-  if (s->ev_fp) cudaEventDestroy(s->ev_fp);
+  // the work on aux and aux2 is joined into s->stream at the end of every
+  // step, so the frees below, ordered on s->stream, come after it
+  if (s->aux) cudaStreamDestroy(s->aux);
+  if (s->aux2) cudaStreamDestroy(s->aux2);
+  for (cudaEvent_t ev : {s->ev_fork, s->ev_fp, s->ev_start, s->ev_bp, s->ev_upd[0], s->ev_upd[1]})
+    if (ev) cudaEventDestroy(ev);
   if (s->psi_block) cudaFreeAsync(s->psi_block, s->stream);
   if (s->block) cudaFreeAsync(s->block, s->stream);
   delete s;
