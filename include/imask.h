@@ -203,23 +203,27 @@ imask_status imask_levels(imask_plan_t plan, uint64_t seed, int64_t k0, int64_t 
 imask_status imask_state_create(imask_plan_t plan, const float *b_dev, uint64_t seed,
                                 imask_state_t *state_out, void *stream);
 /* Advances the state by n_iters iterations (Alg. 1, or the plan's variant) on
- * stream.  Runs of 8 or more iterations replay a captured CUDA graph of two
- * iterations (as imask_batch_step does for a batch of this state alone; the
- * first such call captures it).  With kernel profiling at a period of 4 or
- * more, the profiled iterations are launched kernel by kernel (so that their
- * events are recorded) and the pairs between them replay the graph; at
- * periods 1 to 3 every iteration is launched kernel by kernel.  Results are
- * the same either way. */
+ * stream.  For Alg. 1 the state's own two side streams run the projector and
+ * the back-projector concurrently with each other and with the previous
+ * update, ordered by events as the data require; all work is joined into
+ * `stream` before the call's last iteration ends, so later work on `stream`
+ * sees the result.  Runs of 8 or more iterations replay a captured CUDA graph
+ * of four iterations (as imask_batch_step does for a batch of this state
+ * alone; the first such call captures it).  With kernel profiling at a period
+ * of 4 or more, the profiled iterations are launched kernel by kernel and in
+ * order on `stream` (so that their events time each kernel alone) and the
+ * iterations between them replay the graph; at periods 1 to 3 every
+ * iteration is launched kernel by kernel.  Results are the same either way. */
 imask_status imask_step(imask_state_t state, int32_t n_iters, void *stream);
 
 /* Batches of independent solves (the paper has no counterpart; this is the
  * batched form of the same iteration).  A batch holds n_states distinct
  * states, of the same or of different plans.  imask_batch_step advances every
  * state by n_iters iterations with the same result as imask_step on each:
- * pairs of iterations of all states are captured once as one CUDA graph, each
- * state on its own branch so that the solves overlap on the device, and the
- * graph is replayed n_iters / 2 times on stream (the iteration counter is read
- * from a device copy held by each state); an odd last iteration runs with
+ * four iterations of all states are captured once as one CUDA graph, each
+ * state on its own branches so that the solves overlap on the device, and the
+ * graph is replayed n_iters / 4 times on stream (the iteration counter is read
+ * from a device copy held by each state); the remaining iterations run with
  * plain launches.  The graph is captured again when a state's dual ping-pong
  * parity differs from the captured one (after an odd number of steps) or its
  * buffers moved (imask_state_set_storage).
