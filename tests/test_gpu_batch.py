@@ -165,3 +165,24 @@ def test_profiled_steps_equal_graph_steps(imask):
     assert torch.equal(x_graph, x_prof)
     # iterations 0, 8, 16, 24, 32 were profiled: 5 of each kind
     assert sum(cnt[0:8]) == 5 and sum(cnt[8:16]) == 5 and sum(cnt[16:24]) == 5
+
+
+@pytest.mark.parametrize("extra", [{}, dict(dual_tables=1, draws=1), dict(reg=1, tv_lambda=0.02)],
+                         ids=["alg1", "alg1_snapshots_independent", "alg1_tv"])
+def test_overlapped_streams_equal_serial_order(imask, extra):
+    # profiling at period 1 runs every kernel in order on one stream; the
+    # default path overlaps projector, back-projector and update on the
+    # state's streams inside four-iteration graphs -- same iterates
+    prob = TV64 if extra.get("reg") else FAN64
+    plan = imask.Plan(dict(prob.params(), mu=0.1, sigma=0.04, **extra))
+    _, b, _ = inputs.measurements(prob, seed=8, noise="none")
+    bt = cuda(b)
+    x_fast = plan.solve(bt, 12, 41)
+    imask.imask_profile_enable(1)
+    try:
+        x_serial = plan.solve(bt, 12, 41)
+        torch.cuda.synchronize()
+    finally:
+        imask.imask_profile_enable(0)
+        imask.imask_profile_read(reset=True)
+    assert torch.equal(x_fast, x_serial)
