@@ -292,6 +292,15 @@ imask_status imask_rel_distance(int64_t n, const float *a_dev, const float *b_de
  * reset: ms[kind*8 + level], count[kind*8 + level]. */
 imask_status imask_profile_enable(int32_t period);
 imask_status imask_profile_read(double ms[24], int64_t count[24], int32_t reset);
+/* Failure-detection self-test (the paper has no counterpart): one projector
+ * launch whose first image strip is never requested, so that every CTA's
+ * bounded wait for it runs out; the CTAs record the failure in the plan's
+ * error flag, let their other copies land and return.  The next
+ * imask_plan_check reports IMASK_ERR_TIMEOUT (and clears the flag); the plan
+ * stays usable.  No GPU fault or hang is involved.  Allocates scratch with
+ * cudaMallocAsync on stream. */
+imask_status imask_selftest_projector_timeout(imask_plan_t plan, void *stream);
+
 /* Measured shared-memory ceilings of the current GPU, for roofline reports
  * (the paper has no counterpart): out[0] = GB/s of conflict-free 32-bit loads,
  * out[1] = GB/s (read + write bytes) of read-modify-writes of private slots,

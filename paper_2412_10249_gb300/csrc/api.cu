@@ -7,6 +7,7 @@
 // host.  States hold one solve of Alg. 1; imask_step launches the three
 // kernels of every iteration (see kernels.cu).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -51,6 +52,12 @@ imask_status cuda_fail(cudaError_t e, const char *what) {
   } while (0)
 
 inline size_t align64(size_t n) { return (n + 63) & ~(size_t)63; }
+
+// NVTX range for tools that record them (header-only; no cost without a tool)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ===================================================================================
 // profiling: CUDA events around projector / back-projector / update launches
@@ -867,6 +874,7 @@ imask_status imask_optimal_step(double L, double Lbar, double Lbar_p, double p_m
 }
 
 imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
+  NvtxRange nv("imask_plan");
   if (!plan_out) return fail(IMASK_ERR_INVALID, "plan_out is NULL");
   *plan_out = nullptr;
   imask_status rc = validate(desc);
@@ -1507,6 +1515,7 @@ imask_status batch_capture(imask_batch_s *b, int unroll) {
 }  // namespace
 
 imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
+  NvtxRange nv("imask_step");
   if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
   if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1597,6 +1606,7 @@ imask_status imask_batch_create(const imask_state_t *states, int32_t n_states,
 }
 
 imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
+  NvtxRange nv("imask_batch_step");
   if (!b) return fail(IMASK_ERR_INVALID, "NULL batch");
   if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1762,6 +1772,7 @@ imask_status imask_pdhg_params(double norm_K, double mu, double rho, double out[
 
 imask_status imask_pdhg(imask_plan_t p, const float *b_dev, int32_t iters, double s_step,
                         double t_step, double theta, float *x_dev, void *stream) {
+  NvtxRange nv("imask_pdhg");
   if (!p || !b_dev || !x_dev) return fail(IMASK_ERR_INVALID, "NULL argument");
   if (iters < 0) return fail(IMASK_ERR_INVALID, "iters < 0");
   if (!(s_step > 0.0) || !(t_step > 0.0) || !isfinite(theta))
@@ -1871,6 +1882,23 @@ imask_status imask_objective(imask_plan_t p, const float *x_dev, const float *b_
   if (p->desc.reg != 0) obj += p->desc.tv_lambda * h[3];
   if (!isfinite(obj)) return fail(IMASK_ERR_NONFINITE, "objective is not finite");
   *out = obj;
+  return IMASK_OK;
+}
+
+imask_status imask_selftest_projector_timeout(imask_plan_t p, void *stream) {
+  if (!p) return fail(IMASK_ERR_INVALID, "NULL plan");
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch sc;
+  imask_status rc = scratch_alloc(p, 1u, false, st, sc);   // level -1 images (zeros)
+  if (rc != IMASK_OK) return rc;
+  void *sino = nullptr;
+  cudaError_t e = cudaMallocAsync(&sino, (size_t)p->dp.m * sizeof(float), st);
+  if (e == cudaSuccess)
+    e = launch_fp(p->dp, fixed_level(-1), sc.pads, (float *)sino, no_dual(), p->n_cta_x,
+                  p->n_cta_y, p->d_err, st, 1);
+  if (sino) cudaFreeAsync(sino, st);
+  scratch_free(sc);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test projector");
   return IMASK_OK;
 }
 

@@ -149,7 +149,8 @@ cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet
                           ExtrapArgs ex, SnapArgs snap, cudaStream_t st);
 unsigned long long primal_seed(unsigned long long seed);
 cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
-                      int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st);
+                      int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st,
+                      int test_skip_first_strip = 0);
 cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
                       unsigned int *err, cudaStream_t st);
 long long bp_smem_bytes(const DevPlan &P);

@@ -98,8 +98,8 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
 }
 
 // Polls the barrier phase `parity` at most kWaitLimit times.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int limit = kWaitLimit) {
+  for (int it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -160,10 +160,11 @@ __device__ __forceinline__ void block_origin(float a_hi, float a_lo, float t_hi,
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(FP_THREADS, 2)
     k_fp(DevPlan P, LevelSel sel, PadSet pads, float *sino, DualArgs D, int n_cta_x,
-         unsigned int *err) {
+         unsigned int *err, int test_skip_first_strip) {
   extern __shared__ __align__(128) float fp_smem[];
   __shared__ __align__(8) unsigned long long full_bar[FP_STAGES];
   __shared__ unsigned int released[FP_STAGES];   // warps done with each stage (monotone)
+  __shared__ unsigned int issued[FP_STAGES];     // bulk loads issued into each stage
 
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
@@ -205,14 +206,20 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
     for (int s = 0; s < FP_STAGES; ++s) {
       mbar_init(smem_u32(&full_bar[s]), 1);
       released[s] = 0u;
+      issued[s] = 0u;
     }
     mbar_fence_init();
   }
   __syncthreads();
+  // (test_skip_first_strip: a self-test leaves the first strip unrequested, so
+  // that every warp's bounded wait for it runs out -- after a short limit)
+  const int wait_limit = test_skip_first_strip ? 256 : kWaitLimit;
   if (tid == 0) {
-    for (int s = 0; s < FP_STAGES && s < nstrips; ++s)
+    for (int s = test_skip_first_strip ? 1 : 0; s < FP_STAGES && s < nstrips; ++s) {
       bulk_load(smem_u32(fp_smem + s * FP_STAGE_FLOATS), img + (size_t)s * tc * ls, strip_bytes,
                 smem_u32(&full_bar[s]));
+      issued[s] += 1u;
+    }
   }
   constexpr unsigned kWarps = FP_THREADS / 32;
   const int lane = tid & 31;
@@ -225,7 +232,7 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
   for (int s = 0; s < nstrips; ++s) {
     const int st = s % FP_STAGES;
     const uint32_t parity = (uint32_t)((s / FP_STAGES) & 1);
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[st]), parity));
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[st]), parity, wait_limit));
     if (!ok) {
       failed = true;
       break;
@@ -287,14 +294,17 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
         fence_proxy_async();
         bulk_load(smem_u32(fp_smem + st * FP_STAGE_FLOATS),
                   img + (size_t)(s + FP_STAGES) * tc * ls, strip_bytes, smem_u32(&full_bar[st]));
+        issued[st] += 1u;   // only the last releaser of a stage issues its refill
       }
     }
   }
   if (__syncthreads_or(failed)) {
     if (tid == 0) {
       atomicOr(err, 1u);
-      // give the copies still in flight a bounded chance to land before exit
-      for (int s = 0; s < FP_STAGES; ++s) mbar_wait(smem_u32(&full_bar[s]), 0);
+      // give the copies still in flight a bounded chance to land before exit:
+      // at most one load per stage is outstanding, the latest issued one
+      for (int s = 0; s < FP_STAGES; ++s)
+        if (issued[s] > 0u) mbar_wait(smem_u32(&full_bar[s]), (issued[s] - 1u) & 1u);
     }
     return;
   }
@@ -1228,13 +1238,15 @@ cudaError_t launch_sketch(const DevPlan &P, LevelSel sel, const float *x, PadSet
 }
 
 cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
-                      int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st) {
+                      int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st,
+                      int test_skip_first_strip) {
   const int sm = (int)fp_smem_bytes();
   cudaError_t e = set_smem((const void *)k_fp, sm);
   if (e != cudaSuccess) return e;
   if (n_cta_x + n_cta_y == 0) return cudaSuccess;
   count_launch();
-  k_fp<<<n_cta_x + n_cta_y, FP_THREADS, sm, st>>>(P, sel, pads, sino, dual, n_cta_x, err);
+  k_fp<<<n_cta_x + n_cta_y, FP_THREADS, sm, st>>>(P, sel, pads, sino, dual, n_cta_x, err,
+                                                  test_skip_first_strip);
   return cudaGetLastError();
 }
 

@@ -94,6 +94,7 @@ SIGNATURES = {
     "imask_rel_distance": (_I32, [_I64, _VP, _VP, _DP, _VP]),
     "imask_state_set_storage": (_I32, [_VP, _I32, _VP]),
     "imask_probe_smem": (_I32, [_DP, _VP]),
+    "imask_selftest_projector_timeout": (_I32, [_VP, _VP]),
     "imask_batch_create": (_I32, [_VP, _I32, _VP]),
     "imask_batch_step": (_I32, [_VP, _I32, _VP]),
     "imask_batch_destroy": (_I32, [_VP]),
@@ -319,6 +320,10 @@ class Plan:
 
     def check(self):
         imask_plan_check(self.handle)
+
+    def selftest_timeout(self, stream=None):
+        """Runs the failure-detection self-test; check() then raises TIMEOUT."""
+        _check(lib().imask_selftest_projector_timeout(self.handle, _stream(stream)))
 
     def axis_split(self):
         na = int(self.params["n_angles"])
