@@ -147,7 +147,10 @@ imask_status imask_plan_get_info(imask_plan_t plan, imask_plan_info *info);
 
 /* Synchronises the device and reports IMASK_ERR_TIMEOUT if a projector
  * launch of this plan gave up a bounded wait for its image strips since the
- * last check (the flag is then cleared). */
+ * last check (the flag is then cleared).  A library built with
+ * -DIMASK_BOUNDS_CHECK also checks the kernels' computed indices, skips an
+ * access out of its buffer and records it; such a record (of any plan) is
+ * reported here as IMASK_ERR_INVALID and cleared. */
 imask_status imask_plan_check(imask_plan_t plan);
 
 /* Host copy of the per-view major-axis split that the plan uses: for view a,

@@ -26,42 +26,66 @@ def nvcc() -> str:
     return "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+# index-checked variant of the same library (kernels check their computed
+# indices and record failures instead of accessing out of bounds)
+CHECKED_OUT = os.path.join(OUT, "checked")
+CHECKED_LIB = os.path.join(CHECKED_OUT, "libimask.so")
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in HEADERS]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list | None = None) -> str:
-    """Compile the CUDA sources in parallel and link the shared library."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
-    extra = list(extra or [])
-    procs = []
-    objs = []
+def _compile(out_dir: str, lib: str, extra: list, verbose: bool):
+    """Starts the compiles of one variant; returns (processes, link step)."""
+    os.makedirs(out_dir, exist_ok=True)
+    procs, objs = [], []
     for s in SOURCES:
-        obj = os.path.join(OUT, s.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, s.replace(".cu", ".o"))
         objs.append(obj)
         cmd = [nvcc(), *NVCC_FLAGS, *extra, "-c", os.path.join(CSRC, s), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+
+    def link():
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        if r.returncode != 0:
+            sys.stderr.write(r.stdout.decode(errors="replace"))
+            raise RuntimeError("nvcc link failed")
+        os.replace(tmp, lib)
+
+    return procs, link
+
+
+def _finish(procs, link, verbose: bool):
     for cmd, pr in procs:
         out, _ = pr.communicate()
         if verbose or pr.returncode != 0:
             sys.stderr.write(out.decode(errors="replace"))
         if pr.returncode != 0:
             raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-    if r.returncode != 0:
-        sys.stderr.write(r.stdout.decode(errors="replace"))
-        raise RuntimeError("nvcc link failed")
-    os.replace(tmp, LIB)
+    link()
+
+
+def build(force: bool = False, verbose: bool = False, extra: list | None = None,
+          checked: bool = True) -> str:
+    """Compile the CUDA sources in parallel and link the shared library (and,
+    with `checked`, its index-checked variant, in parallel with it)."""
+    jobs = []
+    if force or _stale(LIB):
+        jobs.append(_compile(OUT, LIB, list(extra or []), verbose))
+    if checked and (force or _stale(CHECKED_LIB)):
+        jobs.append(_compile(CHECKED_OUT, CHECKED_LIB, ["-DIMASK_BOUNDS_CHECK", *(extra or [])],
+                             verbose))
+    for procs, link in jobs:
+        _finish(procs, link, verbose)
     return LIB
 
 

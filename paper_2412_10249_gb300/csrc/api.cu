@@ -1147,6 +1147,12 @@ imask_status imask_plan_axis_split(imask_plan_t p, int32_t *split, int32_t *firs
 imask_status imask_plan_check(imask_plan_t p) {
   if (!p) return fail(IMASK_ERR_INVALID, "NULL plan");
   CK(cudaDeviceSynchronize(), "synchronise");
+  unsigned int idx_flags = 0;
+  CK(read_index_check_flag(&idx_flags, true), "read index-check flag");
+  if (idx_flags)
+    return fail(IMASK_ERR_INVALID,
+                "an index check of the checked build failed (flags 0x%x: 2 projector line, "
+                "4 back-projector staging, 8 sketch writes)", idx_flags);
   unsigned int flag = 0;
   CK(cudaMemcpy(&flag, p->d_err, sizeof flag, cudaMemcpyDeviceToHost), "read error flag");
   if (flag) {

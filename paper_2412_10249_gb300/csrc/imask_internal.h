@@ -173,6 +173,8 @@ cudaError_t launch_counter(long long *k_dev, long long delta, int set_value, cud
 // dst[i] = src[i] converted between the table formats (0 float, 1 bfloat16, 2 binary16)
 cudaError_t launch_convert(long long n, const void *src, int src_fmt, void *dst, int dst_fmt,
                            cudaStream_t st);
+// flags of the index checks of a checked build (0 in the normal build)
+cudaError_t read_index_check_flag(unsigned int *flags, bool clear);
 // shared-memory bandwidth probe: blocks x 256 threads x iters x 8 accesses
 cudaError_t launch_probe_smem(int blocks, int iters, int rmw, float *sink, cudaStream_t st);
 // psi_mean = sum_l p_l psi_l over the level tables

@@ -31,6 +31,24 @@ constexpr int kMagicBits = 0x4B400000;
 constexpr float kBpEps = 0.01f;          // slack (in bins) of the back-projector's ray range
 constexpr int kWaitLimit = 1 << 20;      // bounded mbarrier polls before giving up
 
+}  // namespace
+
+// Index checks of a checked build (-DIMASK_BOUNDS_CHECK): a computed index
+// outside its buffer sets a bit of this flag (1 projector image line, 2
+// back-projector staging, 3 sketch / update writes) and the access is skipped
+// or redirected to element 0; the host reads the flag in imask_plan_check.
+// In the normal build the checks compile to nothing.
+__device__ unsigned int g_index_check_flag = 0u;
+
+namespace {
+
+#ifdef IMASK_BOUNDS_CHECK
+#define IMASK_INDEX_OK(cond, bit) \
+  ((cond) ? true : (atomicOr(&g_index_check_flag, 1u << (bit)), false))
+#else
+#define IMASK_INDEX_OK(cond, bit) true
+#endif
+
 // ---------------------------------------------------------------------------------
 // Level draw: SplitMix64 output k of `seed` against the integer thresholds of the
 // cumulative probabilities (Alg. 1, sampling step).
@@ -275,7 +293,8 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
           const float *line = buf + (cc + u) * ls;
           const float q = fmaf(dcf, thi[r], rl[r]);
           const float tq = __fadd_rd(q, kMagic);
-          const int i0 = boff[r] + (__float_as_int(tq) - kMagicBits);
+          int i0 = boff[r] + (__float_as_int(tq) - kMagicBits);
+          if (!IMASK_INDEX_OK(i0 >= 0 && i0 + 1 < ls, 1)) i0 = 0;
           const float f = q - (tq - kMagic);
           const float v0 = line[i0];
           const float v1 = line[i0 + 1];
@@ -565,6 +584,9 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
       const int v = vs;
       const int kk = e - pref[v];
       const int2 vi = vinfo[v];
+      if (!IMASK_INDEX_OK(vi.x + kk >= 0 && vi.x + kk < P.m && vi.y + kk >= 0 &&
+                              vi.y + kk < P.m, 2))
+        continue;
       cp_async(win + sl, P.rays + vi.x + kk, 16);
       cp_async(lo + sl, P.rays_lo + vi.x + kk, 8);
       cp_async(yv + sl, y + vi.y + kk, 4);
@@ -741,6 +763,7 @@ __device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, floa
   }
   for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
     const int I = p / side, J = p % side;
+    if (!IMASK_INDEX_OK(I0 + I < G.nl && J0 + J < G.nl, 3)) continue;
     R[(size_t)(I0 + I) * G.ls + IMASK_PAD + J0 + J] = vals[I * side + J];
   }
   for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
@@ -1383,6 +1406,15 @@ cudaError_t launch_pdhg_primal(long long d, float scale, float theta, float *xn,
   count_launch();
   k_pdhg_primal<<<grid_for(d, 256), 256, 0, st>>>(d, scale, theta, xn, x, xbar);
   return cudaGetLastError();
+}
+
+cudaError_t read_index_check_flag(unsigned int *flags, bool clear) {
+  cudaError_t e = cudaMemcpyFromSymbol(flags, g_index_check_flag, sizeof(unsigned int));
+  if (e == cudaSuccess && clear && *flags) {
+    const unsigned int zero = 0u;
+    e = cudaMemcpyToSymbol(g_index_check_flag, &zero, sizeof(unsigned int));
+  }
+  return e;
 }
 
 cudaError_t launch_counter(long long *k_dev, long long delta, int set_value, cudaStream_t st) {
