@@ -17,7 +17,9 @@
 #define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
 #define BP_THREADS 256         // back-projector: threads per CTA
 #define BP_W 16                // back-projector tile: lines along the major axis
+#ifndef BP_SEG
 #define BP_SEG 32              // back-projector tile: lines across (one owner segment)
+#endif
 #ifndef BP_SLOTS
 #define BP_SLOTS 256           // back-projector: ray slots per staged chunk
 #endif
