@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 // The x-major and y-major rays go to separate CTAs.  An x-major CTA owns a tile
 // of BP_W columns x BP_SEG rows of level pixels and a contiguous range of views
 // (bp_vgo ranges across CTAs; the consumer adds the partial images, 2 bp_vgo of
-// them, in a fixed order).  Thread t owns the column t % BP_W of the tile, a
+// them, in a fixed order).  CTAs take (role, tile) pairs from the plan's
+// heaviest-first order, so that light tiles fill the last wave.  Thread t owns the column t % BP_W of the tile, a
 // segment of BP_SEG rows with private accumulators in shared memory, and takes
 // every (BP_THREADS / BP_W)-th staged ray.  y-major CTAs do the same with rows
 // and columns exchanged.
@@ -396,13 +397,16 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 //             ray list;
 //   pipeline  the list is processed in chunks; while chunk k is scattered,
 //             the raw data of chunk k+1 (parameters, low words, y) stream into
-//             the other buffer by cp.async; after a barrier they are converted
+//             the other buffer by cp.async (each entry's view is found by
+//             galloping from the thread's previous one); after a barrier they
+//             are converted
 //             in place to (r, t, g y, I') in the local frame of the tile's line
 //             block (block_origin, as in k_fp);
 //   scatter   a thread applies a ray to its segment exactly as k_fp samples
 //             it: q = r + d t, row I + floor(q) gets (1 - f) g y and the next
 //             row f g y, f = q - floor(q); rows outside the segment land in
-//             guard slots.  Only the owner ever touches a slot.
+//             guard slots (one unsigned clamp).  Only the owner ever touches a
+//             slot.
 //   epilogue  every pixel sums its BP_THREADS / BP_W owners' slots.
 // ---------------------------------------------------------------------------------
 __device__ __forceinline__ float bin_of(const DevPlan &P, float c, float s, float x, float y) {
