@@ -13,6 +13,8 @@ after the last quantum its iterate is copied to pinned host memory and its
 state is freed.  Latency is measured from arrival to that host copy.
 
 All arithmetic runs in the library's kernels; this module only schedules.
+The device operations sit behind a backend object (CudaBackend by default),
+so that the scheduling itself can be exercised without a GPU.
 mu comes from the plan's power method; sigma is the Thm. 3 step for the
 normalised constants of r uniform levels (L = 2.46, Lbar = L / sqrt(r),
 Lbar_p = L), which the mu normalisation makes common to all geometries.
@@ -28,9 +30,6 @@ from dataclasses import dataclass, field
 from typing import Callable
 
 import numpy as np
-import torch
-
-from . import imask
 
 
 @dataclass
@@ -44,7 +43,7 @@ class Request:
     # filled by the server
     admitted: float = math.nan
     finished: float = math.nan
-    x: torch.Tensor | None = None     # pinned host copy of the result
+    x: object = None                  # host copy of the result (pinned tensor on CUDA)
     status: str = "pending"           # pending, queued, active, done, rejected, failed
 
 
@@ -52,12 +51,10 @@ class Request:
 class _Active:
     req: Request
     plan_key: tuple
-    stream: torch.cuda.Stream
-    state: imask.State
-    b_dev: torch.Tensor
+    solve: object          # the backend's handle of one running solve
     remaining: int
     bytes: int
-    event: torch.cuda.Event | None = None
+    event: object = None   # the backend's completion marker of the last work
     finishing: bool = False
 
 
@@ -72,10 +69,85 @@ _SIGMA_CACHE: dict = {}
 
 def normalised_sigma(levels: int) -> float:
     if levels not in _SIGMA_CACHE:
+        from . import imask
         L = 2.46
         _SIGMA_CACHE[levels] = imask.imask_optimal_step(L, L / math.sqrt(levels), L,
                                                         1.0 / levels)[0]
     return _SIGMA_CACHE[levels]
+
+
+class PlanBuildError(RuntimeError):
+    """A plan could not be built; the requests of its geometry fail."""
+
+
+class CudaBackend:
+    """Device side of the loop: plans, states and streams of the library."""
+
+    def __init__(self, power_iters: int = 20):
+        import torch
+        from . import imask
+        self.torch, self.imask = torch, imask
+        self.power_iters = power_iters
+        self.device = torch.cuda.current_device()
+
+    def build_plan(self, params: dict):
+        """(plan, plan bytes, state bytes); runs on a worker thread."""
+        self.torch.cuda.set_device(self.device)
+        try:
+            plan = self.imask.Plan(dict(params, mu=0.0, sigma=normalised_sigma(params["levels"]),
+                                        power_iters=self.power_iters))
+        except self.imask.ImaskError as e:
+            raise PlanBuildError(str(e)) from e
+        info = plan.info
+        return plan, int(info["plan_bytes"]), int(info["state_bytes"])
+
+    def host_sinogram(self, b):
+        return self.torch.from_numpy(np.ascontiguousarray(b, dtype=np.float32).ravel()).pin_memory()
+
+    def start(self, plan, host, seed: int):
+        torch = self.torch
+        stream = torch.cuda.Stream()
+        b_dev = torch.empty(host.numel(), device="cuda", dtype=torch.float32)
+        with torch.cuda.stream(stream):
+            b_dev.copy_(host, non_blocking=True)
+            state = plan.state(b_dev, seed, stream=stream)
+        return (stream, state, b_dev)
+
+    def step(self, solve, n: int):
+        stream, state, _ = solve
+        with self.torch.cuda.stream(stream):
+            state.step(n, stream=stream)
+
+    def fetch(self, solve):
+        """Starts the copy of the iterate to host memory; returns the host buffer."""
+        torch = self.torch
+        stream, state, _ = solve
+        with torch.cuda.stream(stream):
+            x_dev = state.get(state.X, stream=stream)
+            host = torch.empty(x_dev.numel(), dtype=torch.float32, pin_memory=True)
+            host.copy_(x_dev, non_blocking=True)
+        return host
+
+    def mark(self, solve):
+        ev = self.torch.cuda.Event()
+        ev.record(solve[0])
+        return ev
+
+    @staticmethod
+    def done(marker) -> bool:
+        return marker.query()
+
+    def finish(self, solve):
+        solve[1].close()
+
+    def close_plan(self, plan):
+        plan.close()
+
+    def check_plan(self, plan):
+        plan.check()
+
+    def synchronize(self):
+        self.torch.cuda.synchronize()
 
 
 @dataclass
@@ -96,12 +168,12 @@ class ServerStats:
 
 class Server:
     def __init__(self, budget_bytes: int, max_active: int = 16, max_queue: int = 64,
-                 quantum: int = 10, power_iters: int = 20, workers: int = 2):
+                 quantum: int = 10, power_iters: int = 20, workers: int = 2, backend=None):
         self.budget = int(budget_bytes)
         self.max_active = max_active
         self.max_queue = max_queue
         self.quantum = quantum
-        self.power_iters = power_iters
+        self.backend = backend if backend is not None else CudaBackend(power_iters)
         self.plans: collections.OrderedDict = collections.OrderedDict()   # key -> (plan, bytes)
         self.plan_users: collections.Counter = collections.Counter()
         self.building: dict = {}          # key -> future of the plan
@@ -113,7 +185,6 @@ class Server:
         self.stats = ServerStats()
         self.lock = threading.Lock()
         self.pool = cf.ThreadPoolExecutor(max_workers=workers)
-        self.device = torch.cuda.current_device()
         self.t0 = time.perf_counter()
 
     def now(self) -> float:
@@ -121,20 +192,16 @@ class Server:
 
     # -- preparation (worker threads) ----------------------------------------------
     def _build_plan(self, params: dict):
-        torch.cuda.set_device(self.device)
         t = time.perf_counter()
-        plan = imask.Plan(dict(params, mu=0.0, sigma=normalised_sigma(params["levels"]),
-                               power_iters=self.power_iters))
-        info = plan.info
+        out = self.backend.build_plan(params)
         with self.lock:
             self.stats.plan_seconds += time.perf_counter() - t
             self.stats.plans_built += 1
-        return plan, int(info["plan_bytes"]), int(info["state_bytes"])
+        return out
 
-    @staticmethod
-    def _make_b(req: Request):
+    def _make_b(self, req: Request):
         b = req.b() if callable(req.b) else req.b
-        return torch.from_numpy(np.ascontiguousarray(b, dtype=np.float32).ravel()).pin_memory()
+        return self.backend.host_sinogram(b)
 
     @staticmethod
     def plan_bytes_estimate(params: dict) -> int:
@@ -171,7 +238,7 @@ class Server:
                 est = self.reserved.pop(key)
                 try:
                     plan, pb, sb = fut.result()
-                except imask.ImaskError as e:
+                except PlanBuildError as e:
                     # the requests of this geometry fail; the loop carries on
                     self.used -= est
                     self.stats.failed_plans.append((key, str(e)))
@@ -191,7 +258,7 @@ class Server:
                 return
             if key != keep and self.plan_users[key] == 0:
                 plan, pb, _ = self.plans.pop(key)
-                plan.close()
+                self.backend.close_plan(plan)
                 self.used -= pb
 
     # -- scheduling ----------------------------------------------------------------
@@ -236,48 +303,41 @@ class Server:
                 continue
             self.plans.move_to_end(key)
             host = self.prepared.pop(req.rid).result()
-            stream = torch.cuda.Stream()
-            b_dev = torch.empty(m, device="cuda", dtype=torch.float32)
-            with torch.cuda.stream(stream):
-                b_dev.copy_(host, non_blocking=True)
-                state = plan.state(b_dev, req.seed, stream=stream)
+            solve = self.backend.start(plan, host, req.seed)
             self.plan_users[key] += 1
             self.used += need
             self.stats.peak_bytes = max(self.stats.peak_bytes, self.used)
             req.admitted = self.now()
             req.status = "active"
-            self.active.append(_Active(req, key, stream, state, b_dev, req.iters, need))
+            self.active.append(_Active(req, key, solve, req.iters, need))
             self.stats.admitted += 1
             self.stats.max_active = max(self.stats.max_active, len(self.active))
         self.queue = remaining
 
     def _advance(self):
+        be = self.backend
         for a in self.active:
-            if a.finishing or (a.event is not None and not a.event.query()):
+            if a.finishing or (a.event is not None and not be.done(a.event)):
                 continue
-            with torch.cuda.stream(a.stream):
-                if a.remaining > 0:
-                    q = min(self.quantum, a.remaining)
-                    a.state.step(q, stream=a.stream)
-                    a.remaining -= q
-                else:
-                    x_dev = a.state.get(a.state.X, stream=a.stream)
-                    a.req.x = torch.empty(x_dev.numel(), dtype=torch.float32, pin_memory=True)
-                    a.req.x.copy_(x_dev, non_blocking=True)
-                    a.finishing = True
-                a.event = torch.cuda.Event()
-                a.event.record(a.stream)
+            if a.remaining > 0:
+                q = min(self.quantum, a.remaining)
+                be.step(a.solve, q)
+                a.remaining -= q
+            else:
+                a.req.x = be.fetch(a.solve)
+                a.finishing = True
+            a.event = be.mark(a.solve)
 
     def _retire(self):
         keep = []
         for a in self.active:
-            if a.finishing and a.event.query():
+            if a.finishing and self.backend.done(a.event):
                 a.req.finished = self.now()
                 a.req.status = "done"
                 self.stats.completed += 1
                 self.stats.latencies.append(a.req.finished - a.req.arrival)
                 self.stats.waits.append(a.req.admitted - a.req.arrival)
-                a.state.close()
+                self.backend.finish(a.solve)
                 self.plan_users[a.plan_key] -= 1
                 self.used -= a.bytes
             else:
@@ -311,21 +371,24 @@ class Server:
                 break
             if not self.active and not self.queue and i < len(pending):
                 time.sleep(max(0.0, min(0.001, pending[i].arrival - t)))
-        torch.cuda.synchronize()
+        self.backend.synchronize()
         for plan, _, _ in self.plans.values():
-            plan.check()
+            self.backend.check_plan(plan)
         return self.stats
 
     def close(self):
-        torch.cuda.synchronize()
+        self.backend.synchronize()
         for a in self.active:
-            a.state.close()
+            self.backend.finish(a.solve)
         self.active = []
         for fut in self.building.values():
-            plan, _, _ = fut.result()
-            plan.close()
+            try:
+                plan, _, _ = fut.result()
+            except PlanBuildError:
+                continue
+            self.backend.close_plan(plan)
         self.building.clear()
         self.pool.shutdown(wait=True)
         for plan, _, _ in self.plans.values():
-            plan.close()
+            self.backend.close_plan(plan)
         self.plans.clear()
