@@ -352,6 +352,29 @@ def time_variants(imask, p, bt, info, iters, stream, flush, x, steps=3):
     out["pdhg"] = {"ms_per_iteration": a.elapsed_time(e) / n_it, "s": s_, "t": t_,
                    "theta": th_, "note": "includes the per-call work-buffer allocation"}
     plan.close()
+    # the 64x64 parallel-beam workload with quadratic + smoothed TV (two levels,
+    # 50 iterations; the parity case run against the oracle by the tests)
+    sp = inputs.small_problem()
+    _, sb, _ = inputs.measurements(sp, seed=0)
+    sbt = torch.as_tensor(sb.ravel().astype(np.float32), device="cuda")
+    splan = imask.Plan(dict(sp.params(), mu=0.0, sigma=0.0))
+    sinfo = splan.info
+    splan.close()
+    splan = imask.Plan(dict(sp.params(), mu=sinfo["mu"], sigma=sinfo["sigma"],
+                            tv_lambda=0.1 * sinfo["mu"]))
+    xs = torch.empty(sp.n * sp.n, device="cuda")
+    with torch.cuda.stream(stream):
+        splan.solve(sbt, 1, 50, out=xs, stream=stream)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for k in range(20):
+            splan.solve(sbt, 2 + k, 50, out=xs, stream=stream)
+        e.record(stream)
+    torch.cuda.synchronize()
+    out["small_tv64"] = {"solves_per_s": 20e3 / a.elapsed_time(e),
+                         "ms_per_solve": a.elapsed_time(e) / 20,
+                         "workload": "64x64 parallel 60x92, r=2, quadratic + smoothed TV, 50 its"}
+    splan.close()
     return out
 
 
