@@ -287,6 +287,9 @@ def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops, period=1, smem_probe=
     total = max(1e-12, float(sum(prof_ms)))
     rep["time_share"] = {f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / total, 4)
                          for k in range(24) if prof_cnt[k] > 0}
+    rep["avg_launch_us_by_level"] = {
+        f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / prof_cnt[k] * 1e3, 1)
+        for k in range(24) if prof_cnt[k] > 0}
     return rep
 
 
@@ -917,6 +920,7 @@ def run_ours(args):
                        "levels": p.levels, "iters_per_solve": args.iters,
                        "iteration": vopts,
                        "mu": info["mu"], "sigma": info["sigma"], "theta": info["theta"],
+                       "bp_view_groups": list(info["bp_view_groups"][:p.levels]),
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"replicas x{world}"},
             "gsamples_per_s": gs,

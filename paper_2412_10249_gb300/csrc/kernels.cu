@@ -328,53 +328,81 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
     return;
   }
 
+  // Epilogue.  Every load of the four rays is issued before the first store
+  // (two rounds of independent loads: the ray's sinogram index, then the
+  // state it indexes), so that a warp waits for two memory latencies rather
+  // than two per ray: the stores of one ray could alias the next ray's loads,
+  // which would otherwise keep them in order.
+  int qv[FP_RAYS];
+  float gz[FP_RAYS];
 #pragma unroll
   for (int r = 0; r < FP_RAYS; ++r) {
     const int idx = begin + r * FP_THREADS + tid;
-    if (idx >= end) continue;
-    const float4 p = P.rays[idx];
-    const float v = acc[r] * (p.z * G.scale2l);
-    const int q = __float_as_int(p.w);
-    if (!D.on) {
-      sino[q] = v;
-    } else {
-      // Alg. 1: zeta = psi_new - psi_l + sum p psi; y+ = (y + s zeta - s b)/(1+s);
-      // the running mean and the table entry take the refreshed value.  With
-      // snapshot tables the projector already applied K_l to the input
-      // difference, so v is psi_new - psi_l itself.
-      // With 16-bit tables the refreshed entry is stored rounded and the
-      // running mean moves by the stored change, so that it stays the
-      // p-weighted sum of the stored tables.
-      float delta = v, dmean = v;
-      if (D.psi) {
-        const size_t qi = (size_t)ell * P.m + q;
-        float old, stored;
-        if (D.psi_fmt == 1) {
-          __nv_bfloat16 *t = (__nv_bfloat16 *)D.psi;
-          old = __bfloat162float(t[qi]);
-          const __nv_bfloat16 h = __float2bfloat16_rn(v);
-          t[qi] = h;
-          stored = __bfloat162float(h);
-        } else if (D.psi_fmt == 2) {
-          __half *t = (__half *)D.psi;
-          old = __half2float(t[qi]);
-          const __half h = __float2half_rn(v);
-          t[qi] = h;
-          stored = __half2float(h);
-        } else {
-          float *t = (float *)D.psi;
-          old = t[qi];
-          t[qi] = v;
-          stored = v;
-        }
-        delta = v - old;
-        dmean = stored - old;
-      }
-      const float pm = D.psi_mean[q];
-      const float zeta = delta + pm;
-      D.y_out[q] = fmaf(D.sigma, zeta - D.b[q], D.y_in[q]) * D.inv_1ps;
-      D.psi_mean[q] = fmaf(P.probs[ell], dmean, pm);
+    qv[r] = -1;
+    gz[r] = 0.0f;
+    if (idx < end) {
+      const float4 p = P.rays[idx];
+      qv[r] = __float_as_int(p.w);
+      gz[r] = p.z * G.scale2l;
     }
+  }
+  if (!D.on) {
+#pragma unroll
+    for (int r = 0; r < FP_RAYS; ++r)
+      if (qv[r] >= 0) sino[qv[r]] = acc[r] * gz[r];
+    return;
+  }
+  // Alg. 1: zeta = psi_new - psi_l + sum p psi; y+ = (y + s zeta - s b)/(1+s);
+  // the running mean and the table entry take the refreshed value.  With
+  // snapshot tables the projector already applied K_l to the input
+  // difference, so v is psi_new - psi_l itself.  With 16-bit tables the
+  // refreshed entry is stored rounded and the running mean moves by the
+  // stored change, so that it stays the p-weighted sum of the stored tables.
+  float old[FP_RAYS], pmv[FP_RAYS], bv[FP_RAYS], yv[FP_RAYS];
+#pragma unroll
+  for (int r = 0; r < FP_RAYS; ++r) {
+    old[r] = pmv[r] = bv[r] = yv[r] = 0.0f;
+    const int q = qv[r];
+    if (q < 0) continue;
+    if (D.psi) {
+      const size_t qi = (size_t)ell * P.m + q;
+      if (D.psi_fmt == 1)
+        old[r] = __bfloat162float(((const __nv_bfloat16 *)D.psi)[qi]);
+      else if (D.psi_fmt == 2)
+        old[r] = __half2float(((const __half *)D.psi)[qi]);
+      else
+        old[r] = ((const float *)D.psi)[qi];
+    }
+    pmv[r] = D.psi_mean[q];
+    bv[r] = D.b[q];
+    yv[r] = D.y_in[q];
+  }
+#pragma unroll
+  for (int r = 0; r < FP_RAYS; ++r) {
+    const int q = qv[r];
+    if (q < 0) continue;
+    const float v = acc[r] * gz[r];
+    float delta = v, dmean = v;
+    if (D.psi) {
+      const size_t qi = (size_t)ell * P.m + q;
+      float stored = v;
+      if (D.psi_fmt == 1) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        ((__nv_bfloat16 *)D.psi)[qi] = h;
+        stored = __bfloat162float(h);
+      } else if (D.psi_fmt == 2) {
+        const __half h = __float2half_rn(v);
+        ((__half *)D.psi)[qi] = h;
+        stored = __half2float(h);
+      } else {
+        ((float *)D.psi)[qi] = v;
+      }
+      delta = v - old[r];
+      dmean = stored - old[r];
+    }
+    const float zeta = delta + pmv[r];
+    D.y_out[q] = fmaf(D.sigma, zeta - bv[r], yv[r]) * D.inv_1ps;
+    D.psi_mean[q] = fmaf(P.probs[ell], dmean, pmv[r]);
   }
 }
 
@@ -889,27 +917,47 @@ __global__ void __launch_bounds__(UPD_THREADS)
     if (P.levels > 1) tile_pyramid(aux, pyr, ts, P.levels);
   }
 
-  for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
-    const int li = p / ts, lj = p % ts;
-    const size_t gp = (size_t)(ti0 + li) * n + tj0 + lj;
-    float delta;
-    if (ell >= 1) {
-      delta = dc[(li >> ell) * cs + (lj >> ell)];
-    } else {
-      const float s0 = compensate_px(P, aux[p], pyr, ts, li, lj);
-      delta = s0 - A.phi0[gp];
-      A.phi0[gp] = s0;
+  // A thread's pixels go in groups of kUpdPix: every load of a group is
+  // issued before its first store (a store to one pixel could alias the next
+  // pixel's loads and would otherwise keep them waiting one by one).
+  constexpr int kUpdPix = 4;
+  for (int p0 = threadIdx.x; p0 < ts * ts; p0 += kUpdPix * blockDim.x) {
+    float pmv[kUpdPix], xov[kUpdPix], ph0[kUpdPix];
+#pragma unroll
+    for (int u = 0; u < kUpdPix; ++u) {
+      const int p = p0 + u * (int)blockDim.x;
+      pmv[u] = xov[u] = ph0[u] = 0.0f;
+      if (p >= ts * ts) continue;
+      const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
+      pmv[u] = A.phi_mean[gp];
+      xov[u] = A.x[gp];
+      if (ell < 1) ph0[u] = A.phi0[gp];
     }
-    const float pm = A.phi_mean[gp];
-    const float xi = delta + pm;
-    const float xo = A.x[gp];
-    const float v = fmaf(-A.tau, xi, xo);
-    A.phi_mean[gp] = fmaf(pl, delta, pm);
-    const float xn = A.prox_in_place ? v * A.inv_1ps : v;
-    A.x[gp] = xn;
-    if (A.x_prev) A.x_prev[gp] = xo;
-    // the next projector input: x+ (Alg. 1) or x+ + theta (x+ - x) (Alg. 7)
-    xs[p] = A.extrapolate ? fmaf(A.theta, xn - xo, xn) : xn;
+#pragma unroll
+    for (int u = 0; u < kUpdPix; ++u) {
+      const int p = p0 + u * (int)blockDim.x;
+      if (p >= ts * ts) continue;
+      const int li = p / ts, lj = p % ts;
+      const size_t gp = (size_t)(ti0 + li) * n + tj0 + lj;
+      float delta;
+      if (ell >= 1) {
+        delta = dc[(li >> ell) * cs + (lj >> ell)];
+      } else {
+        const float s0 = compensate_px(P, aux[p], pyr, ts, li, lj);
+        delta = s0 - ph0[u];
+        A.phi0[gp] = s0;
+      }
+      const float pm = pmv[u];
+      const float xi = delta + pm;
+      const float xo = xov[u];
+      const float v = fmaf(-A.tau, xi, xo);
+      A.phi_mean[gp] = fmaf(pl, delta, pm);
+      const float xn = A.prox_in_place ? v * A.inv_1ps : v;
+      A.x[gp] = xn;
+      if (A.x_prev) A.x_prev[gp] = xo;
+      // the next projector input: x+ (Alg. 1) or x+ + theta (x+ - x) (Alg. 7)
+      xs[p] = A.extrapolate ? fmaf(A.theta, xn - xo, xn) : xn;
+    }
   }
   if (!write_sketch) return;
   __syncthreads();
