@@ -1009,7 +1009,8 @@ def main():
 
 def run_probe(args):
     """Bare K_ell / K_ell^T launches on the fan512 geometry (a small, fixed
-    workload for profilers): three of each per level, timed with CUDA events."""
+    workload for profilers): three of each per level, timed with CUDA events;
+    then four iterations of one solve."""
     import torch
     from paper_2412_10249_gb300 import build as pkg_build
     pkg_build.build()
@@ -1035,6 +1036,16 @@ def run_probe(args):
                 ts.append(a.elapsed_time(b))
             res[f"{name}_l{ell}_ms"] = min(ts)
             res[f"{name}_l{ell}_gsamples_per_s"] = p.m * (p.n >> ell) / (min(ts) / 1e3) / 1e9
+    # four iterations of a solve from the fan512 sinogram (seed 0): the
+    # projector with its fused dual update and the back-projector as the timed
+    # solves launch them, inside the library's "imask_step" NVTX range
+    _, b, _ = inputs.measurements(p, seed=0)
+    bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
+    st = plan.state(bt, 0)
+    st.step(4)
+    torch.cuda.synchronize()
+    res["solve_levels"] = [int(v) for v in plan.levels(0, 0, 4).cpu()]
+    st.close()
     plan.check()
     print(json.dumps(res))
     return 0
