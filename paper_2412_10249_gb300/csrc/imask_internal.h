@@ -21,7 +21,7 @@
 #define BP_SEG 32              // back-projector tile: lines across (one owner segment)
 #endif
 #ifndef BP_SLOTS
-#define BP_SLOTS 256           // back-projector: ray slots per staged chunk
+#define BP_SLOTS 512           // back-projector: ray slots per staged chunk (2 per thread)
 #endif
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin);
                                // equal to BP_W so a back-projector tile is one block

@@ -423,13 +423,13 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 //             linear-fractional for fan beam, so its extremes over the box
 //             are at corners); window lengths are prefix-summed into one flat
 //             ray list;
-//   pipeline  the list is processed in chunks; while chunk k is scattered,
-//             the raw data of chunk k+1 (parameters, low words, y) stream into
-//             the other buffer by cp.async (each entry's view is found by
-//             galloping from the thread's previous one); after a barrier they
-//             are converted
-//             in place to (r, t, g y, I') in the local frame of the tile's line
-//             block (block_origin, as in k_fp);
+//   pipeline  the list is processed in chunks of BP_SLOTS entries; while
+//             chunk k is scattered from one shared-memory buffer, the raw data
+//             of chunk k+1 (parameters, low words, y) is loaded into registers
+//             (each entry's view is found by galloping from the thread's
+//             previous one), then converted to (r, t, g y, I') in the local
+//             frame of the tile's line block (block_origin, as in k_fp) and
+//             stored into the other buffer; one barrier per chunk;
 //   scatter   a thread applies a ray to its segment exactly as k_fp samples
 //             it: q = r + d t, row I + floor(q) gets (1 - f) g y and the next
 //             row f g y, f = q - floor(q); rows outside the segment land in
@@ -456,24 +456,6 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) {
   return fminf(fmaxf(v, lo), hi);
 }
 
-__device__ __forceinline__ void cp_async(void *dst, const void *src, int bytes) {
-  const uint32_t d = smem_u32(dst);
-  if (bytes == 16)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-  else if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;" ::: "memory");
-}
-
 #define BP_GROUPS (BP_THREADS / BP_W)   // ray residue classes per CTA
 #ifndef BP_UNROLL
 #define BP_UNROLL 2                      // unrolling of the scatter loop
@@ -482,15 +464,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 #define IMASK_UNROLL(n) _Pragma(IMASK_STR(unroll n))
 #define BP_ACC (BP_SEG + 4)             // accumulator slots per segment: 2 guards each side
 
-// shared-memory layout of k_bp (dynamic part)
+// shared-memory layout of k_bp (dynamic part): two buffers of BP_SLOTS
+// converted window entries, then the per-view table of the CTA's range
 __device__ __forceinline__ float4 *bp_win(float4 *raw, int b) { return raw + b * BP_SLOTS; }
-__device__ __forceinline__ float2 *bp_lo(float4 *raw, int b) {
-  return (float2 *)(raw + 2 * BP_SLOTS) + b * BP_SLOTS;
-}
-__device__ __forceinline__ float *bp_y(float4 *raw, int b) {
-  return (float *)((float2 *)(raw + 2 * BP_SLOTS) + 2 * BP_SLOTS) + b * BP_SLOTS;
-}
-__device__ __forceinline__ int2 *bp_vinfo(float4 *raw) { return (int2 *)bp_y(raw, 2); }
+__device__ __forceinline__ int2 *bp_vinfo(float4 *raw) { return (int2 *)(raw + 2 * BP_SLOTS); }
 
 // Block-wide exclusive scan of n counters held in a[0..n) (in place); a[n]
 // receives the total, which is also returned.
@@ -524,7 +501,7 @@ __device__ int scan_counts(int *a, int n) {
   return tot;
 }
 
-__global__ void __launch_bounds__(BP_THREADS, 3)
+__global__ void __launch_bounds__(BP_THREADS, 4)
     k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
          unsigned int *err, int nv_cap) {
   extern __shared__ __align__(16) float4 bp_raw[];
@@ -587,19 +564,28 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
   float *acc = acc_s + tid;
   const int nch = (NR + BP_SLOTS - 1) / BP_SLOTS;
 
-  // raw data of chunk k into buffer b
-  // view of a thread's current list entry: chunks are staged in order, so a
-  // thread's entries only move forward and the search starts from the last
-  // view found (galloping, then bisection)
+  // The flat ray list is processed in chunks of BP_SLOTS entries, each thread
+  // holding BP_SPT of them.  While chunk k is scattered from one buffer, the
+  // raw data of chunk k+1 (ray parameters, low words, y) is already loaded
+  // into registers; after the scatter it is converted to the tile's local
+  // frame (r, t, g y, I - cross0 + 2) and stored into the other buffer, and one
+  // barrier per chunk orders both buffers.  The view of a list entry is found
+  // by galloping forward from the thread's previous entry (entries only move
+  // forward), then bisecting the last step.
+  constexpr int BP_SPT = BP_SLOTS / BP_THREADS;
+  static_assert(BP_SLOTS % BP_THREADS == 0, "a chunk is a whole number of entries per thread");
   int vs = 0;
-  auto stage = [&](int k, int b) {
-    float4 *win = bp_win(bp_raw, b);
-    float2 *lo = bp_lo(bp_raw, b);
-    float *yv = bp_y(bp_raw, b);
-    for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
-      const int e = k * BP_SLOTS + sl;
-      if (e >= NR) break;
-      // gallop forward from the previous view, then bisect the last step
+  float4 rw[BP_SPT];
+  float2 rlo[BP_SPT];
+  float ry[BP_SPT];
+  auto fetch = [&](int k) {
+#pragma unroll
+    for (int u = 0; u < BP_SPT; ++u) {
+      const int e = k * BP_SLOTS + tid + u * BP_THREADS;
+      rw[u] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      rlo[u] = make_float2(0.0f, 0.0f);
+      ry[u] = 0.0f;
+      if (e >= NR) continue;
       int step = 1;
       while (vs + step < nv && pref[vs + step] <= e) {
         vs += step;
@@ -613,44 +599,39 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
         else
           hi = mid - 1;
       }
-      const int v = vs;
-      const int kk = e - pref[v];
-      const int2 vi = vinfo[v];
+      const int kk = e - pref[vs];
+      const int2 vi = vinfo[vs];
+      // (a checked build records an index outside the ray list and applies a
+      // zero-weight entry instead)
       if (!IMASK_INDEX_OK(vi.x + kk >= 0 && vi.x + kk < P.m && vi.y + kk >= 0 &&
                               vi.y + kk < P.m, 2))
         continue;
-      cp_async(win + sl, P.rays + vi.x + kk, 16);
-      cp_async(lo + sl, P.rays_lo + vi.x + kk, 8);
-      cp_async(yv + sl, y + vi.y + kk, 4);
+      rw[u] = __ldg(P.rays + vi.x + kk);
+      rlo[u] = __ldg(P.rays_lo + vi.x + kk);
+      ry[u] = __ldg(y + vi.y + kk);
     }
-    cp_async_commit();
   };
-  // in-place conversion to (r, t, g y, I - cross0 + 2)
-  auto convert = [&](int k, int b) {
+  auto put = [&](int k, int b) {
     float4 *win = bp_win(bp_raw, b);
-    const float2 *lo = bp_lo(bp_raw, b);
-    const float *yv = bp_y(bp_raw, b);
-    for (int sl = tid; sl < BP_SLOTS; sl += BP_THREADS) {
-      if (k * BP_SLOTS + sl >= NR) break;
-      const float4 p = win[sl];
-      const float2 pl = lo[sl];
+#pragma unroll
+    for (int u = 0; u < BP_SPT; ++u) {
+      const int sl = tid + u * BP_THREADS;
+      if (k * BP_SLOTS + sl >= NR) continue;
       int I;
       float r;
-      block_origin(p.x, pl.x, p.y, pl.y, G.inv2l, cco, I, r);
-      win[sl] = make_float4(r, p.y, p.z * yv[sl], __int_as_float(I - cross0 + 2));
+      block_origin(rw[u].x, rlo[u].x, rw[u].y, rlo[u].y, G.inv2l, cco, I, r);
+      win[sl] = make_float4(r, rw[u].y, rw[u].z * ry[u], __int_as_float(I - cross0 + 2));
     }
   };
 
   if (nch > 0) {
-    stage(0, 0);
-    cp_async_wait_all();
-    __syncthreads();
-    convert(0, 0);
-    __syncthreads();
+    fetch(0);
+    put(0, 0);
   }
+  __syncthreads();
   for (int k = 0; k < nch; ++k) {
     const int b = k & 1;
-    if (k + 1 < nch) stage(k + 1, b ^ 1);
+    if (k + 1 < nch) fetch(k + 1);
     const float4 *win = bp_win(bp_raw, b);
     const int n = min(BP_SLOTS, NR - k * BP_SLOTS);
     IMASK_UNROLL(BP_UNROLL)
@@ -671,12 +652,10 @@ __global__ void __launch_bounds__(BP_THREADS, 3)
       pa[0] += e.z - w1;
       pa[BP_THREADS] += w1;
     }
-    cp_async_wait_all();
+    // buffer b ^ 1 was last read by the scatter of chunk k - 1, which ended
+    // before the previous barrier
+    if (k + 1 < nch) put(k + 1, b ^ 1);
     __syncthreads();
-    if (k + 1 < nch) {
-      convert(k + 1, b ^ 1);
-      __syncthreads();
-    }
   }
   // ---- epilogue: every pixel of the tile sums its owners' slots ----
   float *plane = gout + (size_t)(role * vgo + vg) * G.nl * G.nl;
@@ -1343,7 +1322,7 @@ int bp_blocks_per_sm(long long dyn_smem) {
 }
 
 long long bp_smem_bytes(const DevPlan &P) {   // dynamic part only
-  return 2LL * BP_SLOTS * (16 + 8 + 4) + (long long)bp_nv_cap(P) * 8 +
+  return 2LL * BP_SLOTS * 16 + (long long)bp_nv_cap(P) * 8 +
          (long long)(bp_nv_cap(P) + 1) * 4;
 }
 
