@@ -979,8 +979,10 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.upd_tile = update_tile(desc->n, r);
   // Grid sizes from the SM count: the projector runs exactly one wave of
   // 2 CTAs per SM (ray chunks shrink below FP_CHUNK to fill it); the
-  // back-projector's view groups are chosen for the best last-wave occupancy
-  // of 3 CTAs per SM.
+  // back-projector's view groups are chosen for the best last-wave fill at
+  // the resident CTAs per SM that an undivided view range allows (a lower
+  // bound: split ranges need less shared memory), and the plan-time
+  // autotuner, when asked for, times the splits around that choice.
   int n_sm = 152;
   {
     int dev = 0;
