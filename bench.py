@@ -978,7 +978,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-queue", type=int, default=64)
-    ap.add_argument("--profile-period", type=int, default=16,
+    ap.add_argument("--profile-period", type=int, default=32,
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--sigma", type=float, default=0.0)
