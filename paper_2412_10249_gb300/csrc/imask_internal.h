@@ -25,7 +25,9 @@
 #endif
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin);
                                // equal to BP_W so a back-projector tile is one block
+#ifndef UPD_THREADS
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
+#endif
 
 // Per-view data for the pixel-driven back-projector (32 bytes).
 struct ViewInfo {
