@@ -15,7 +15,9 @@
 #define FP_CHUNK (FP_THREADS * FP_RAYS)
 #define FP_STAGES 3            // TMA strip pipeline depth
 #define FP_STAGE_FLOATS 9216   // 36 KB per strip buffer (4 lines of a 2048-wide level)
+#ifndef BP_THREADS
 #define BP_THREADS 256         // back-projector: threads per CTA
+#endif
 #define BP_W 16                // back-projector tile: lines along the major axis
 #ifndef BP_SEG
 #define BP_SEG 32              // back-projector tile: lines across (one owner segment)
