@@ -306,7 +306,7 @@ VARIANT_SET = {
     "snapshot_tables": ("alg1", 1, 0, {}),
     "independent_draws": ("alg1", 0, 1, {}),
     "alg7_seq_snapshot_tables": ("seq", 1, 0, {}),
-    # TV with nonnegativity (Sec. 5.3), prox by 20 dual-FISTA steps
+    # TV with nonnegativity (Sec. 4.5), prox by 20 dual-FISTA steps
     "tv_nonneg": ("alg1", 0, 0, {"reg": 2, "tv_inner": 20}),
     # back-projector split measured at plan time instead of the occupancy rule
     "autotuned_plan": ("alg1", 0, 0, {"autotune": 1}),

@@ -68,7 +68,7 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  * R(x) = mu/2 |x|^2 (reg 0) or mu/2 |x|^2 + tv_lambda sum sqrt(|grad x|^2 +
  * tv_eps^2) with forward differences (reg 1, prox by tv_inner FISTA steps),
  * or tv_lambda sum |grad x| restricted to x >= 0 (reg 2, the non-smooth TV
- * with nonnegativity of Sec. 5.3; prox by tv_inner steps of the fast gradient
+ * with nonnegativity of Sec. 4.5; prox by tv_inner steps of the fast gradient
  * projection on the dual; no quadratic term, mu only scales the primal step
  * sigma/mu -- the paper uses the TV weight itself there).
  * mu <= 0 picks mu = |K|^2 / 2.46^2; sigma <= 0 picks a step from power-method
@@ -100,7 +100,7 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               SplitMix64 stream whose seed is the SplitMix64 finaliser of
  *               the seed, the dual level (projector) from the first
  *               (independent primal and dual samples, an open question of the
- *               paper's concluding section). */
+ *               paper's discussion, Sec. 6). */
 typedef struct {
   int32_t n, n_angles, n_det, geometry;  /* geometry: 0 parallel, 1 fan */
   double fov, det_spacing, angle_start, angle_span, src_dist, det_dist;
@@ -260,7 +260,7 @@ imask_status imask_state_destroy(imask_state_t state);
 imask_status imask_solve(imask_plan_t plan, const float *b_dev, uint64_t seed, int32_t iters,
                          float *x_dev, void *stream);
 
-/* PDHG (Chambolle & Pock 2011), the comparison method of Sec. 5.4 and a
+/* PDHG (Chambolle & Pock 2011), the comparison method of Sec. 5 and a
  * generator of reference solutions, on the plan's sketched problem
  * min_x 1/2 |Kbar x - b|^2 + R(x), Kbar = sum_l p_l K_l (= K for one level):
  *   y+ = (y + s (Kbar xbar - b)) / (1 + s);  x+ = prox_{t R}(x - t Kbar^T y+);

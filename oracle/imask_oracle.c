@@ -330,7 +330,7 @@ void orc_apply_KT(const orc_desc *d, int32_t ell, const double *y, double *img) 
 }
 
 /* ------------------------------------------------------------------------ */
-/* Regulariser and its prox -- eq. prox_op; TV prox by FISTA as in Sec. 4.4.  */
+/* Regulariser and its prox -- eq. prox_op; TV prox by FISTA as in Sec. 4.5.  */
 /* ------------------------------------------------------------------------ */
 
 /* Forward differences with zero difference on the last row / column. */
@@ -387,7 +387,7 @@ double orc_regulariser(const orc_desc *d, const double *x) {
   return r;
 }
 
-/* argmin_{x >= 0} 1/2 |x - v|^2 + alpha |grad x|_{1,2} (Sec. 5.3: TV with a
+/* argmin_{x >= 0} 1/2 |x - v|^2 + alpha |grad x|_{1,2} (Sec. 4.5: TV with a
  * nonnegativity constraint, prox by FISTA) by exactly tv_inner iterations of
  * the fast gradient projection on the dual (Beck & Teboulle, IEEE TIP 2009):
  * for a dual field p = (p1, p2) with |p_j| <= 1 the primal point is
@@ -624,7 +624,7 @@ int32_t orc_imask_seq_run(const orc_desc *d, const double *b, uint64_t seed, int
 /*  - independent: the primal level (back-projector, phi tables) is drawn     */
 /*    from a second stream, the dual level (projector, psi tables) from the   */
 /*    first (the separate primal and dual samples named as an open question   */
-/*    in the concluding section).                                             */
+/*    in the discussion, Sec. 6).                                              */
 /* ------------------------------------------------------------------------ */
 
 /* Nearest representable value with RNE: the quantum is 2^(e - bits + 1) for a
@@ -735,12 +735,12 @@ static void apply_KbarT(const orc_desc *d, const double *y, double *out);
 
 /* ------------------------------------------------------------------------ */
 /* PDHG (Chambolle & Pock 2011), the comparison method and x_nat generator of */
-/* Sec. 5.4, on min_x 1/2 |Kbar x - b|^2 + R(x) with Kbar = sum_l p_l K_l:     */
+/* Sec. 5, on min_x 1/2 |Kbar x - b|^2 + R(x) with Kbar = sum_l p_l K_l:     */
 /*   y+ = prox_{s f*}(y + s Kbar xbar) = (y + s Kbar xbar - s b) / (1 + s)     */
 /*   x+ = prox_{t R}(x - t Kbar^T y+),  xbar = x+ + theta (x+ - x).            */
 /* ------------------------------------------------------------------------ */
 
-/* The parameters printed with the comparison of Sec. 5.4 for a mu-strongly
+/* The parameters printed with the comparison of Sec. 5 for a mu-strongly
  * convex R: kappa = sqrt(1 + |K|^2 / (mu rho^2)), s = 1/(kappa - 1),
  * t = 1/((kappa - 1) mu), theta = 1 - 2/(1 + kappa).  out = {s, t, theta}. */
 void orc_pdhg_params(double norm_K, double mu, double rho, double out[3]) {

@@ -71,7 +71,7 @@ void orc_compensate(const orc_desc *d, const double *x, double *out);        /* 
 void orc_apply_K(const orc_desc *d, int32_t ell, const double *x, double *sino);
 void orc_apply_KT(const orc_desc *d, int32_t ell, const double *y, double *img);
 
-/* ---- prox of tau * R (eq. prox_op; Sec. 4.4 for the TV part) ---- */
+/* ---- prox of tau * R (eq. prox_op; Sec. 4.5 for the TV part) ---- */
 void orc_prox(const orc_desc *d, double tau, const double *v, double *out);
 double orc_regulariser(const orc_desc *d, const double *x);
 
@@ -113,7 +113,7 @@ int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const d
                               double *y, double *phi, double *psi, double *snap,
                               double *psi_mean, int32_t *levels_dual, int32_t *levels_primal);
 
-/* ---- PDHG (Sec. 5.4 comparison, x_nat generator) on Kbar = sum_l p_l K_l ---- */
+/* ---- PDHG (Sec. 5 comparison, x_nat generator) on Kbar = sum_l p_l K_l ---- */
 void orc_pdhg_params(double norm_K, double mu, double rho, double out[3]);
 int32_t orc_pdhg_run(const orc_desc *d, const double *b, int32_t iters, double s, double t,
                      double theta, double *x, double *xbar, double *y);

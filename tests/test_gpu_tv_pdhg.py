@@ -1,5 +1,5 @@
-"""GPU parity of the TV-with-nonnegativity regulariser (Sec. 5.3) and of PDHG
-(Sec. 5.4 comparison method) against the FP64 oracle; relative L2 1e-4 on
+"""GPU parity of the TV-with-nonnegativity regulariser (Sec. 4.5) and of PDHG
+(Sec. 5 comparison method) against the FP64 oracle; relative L2 1e-4 on
 iterates after K iterations."""
 import math
 

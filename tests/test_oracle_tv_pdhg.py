@@ -1,5 +1,5 @@
-"""Pins of the oracle's TV-with-nonnegativity prox (Sec. 5.3, FISTA on the
-dual) and of its PDHG (Sec. 5.4 comparison method) -- CPU only."""
+"""Pins of the oracle's TV-with-nonnegativity prox (Sec. 4.5, FISTA on the
+dual) and of its PDHG (Sec. 5 comparison method) -- CPU only."""
 import math
 
 import numpy as np
