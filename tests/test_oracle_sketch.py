@@ -106,3 +106,22 @@ def test_coarse_level_sees_only_block_means(oracle_lib):
         g = o.KT(ell, rng.standard_normal((8, 24)))
         blocks = g.reshape(16 // b, b, 16 // b, b)
         np.testing.assert_allclose(blocks - blocks[:, :1, :, :1], 0.0, atol=1e-14)
+
+
+def test_sketched_operator_is_close_to_k_on_smooth_images(oracle_lib):
+    # Fig. 2(f): the sinogram of the sketched operator Kbar = sum_l p_l K_l
+    # differs from K x by a discretisation error that shrinks as the image
+    # gets smoother (Gaussian blobs of width w = 4, 8, 16 pixels, 64x64,
+    # r = 4).  A coarse projector with the wrong pixel width or grid offset
+    # misses by tens of percent.
+    o = Oracle(n=64, n_angles=60, n_det=92, geometry=0, angle_span=math.pi, levels=4)
+    pr = o.probs()
+    yy, xx = np.mgrid[0:64, 0:64]
+    errs = []
+    for w in (4.0, 8.0, 16.0):
+        img = np.exp(-((xx - 31.5) ** 2 + (yy - 31.5) ** 2) / (2 * w * w))
+        kx = o.K(-1, img).ravel()
+        kb = sum(pr[l] * o.K(l, img).ravel() for l in range(4))
+        errs.append(np.linalg.norm(kx - kb) / np.linalg.norm(kx))
+    assert errs[0] < 0.045 and errs[1] < 0.025 and errs[2] < 0.012
+    assert errs[2] < errs[1] < errs[0]

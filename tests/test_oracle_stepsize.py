@@ -131,3 +131,36 @@ def test_constants_on_a_projector_plan(oracle_lib):
     nk = o.norm_K(400)
     for v in (L, Lb, Lp):
         assert abs(v - nk / math.sqrt(2.0)) < 1e-8 * v
+
+
+def test_lemma1_saddle_operator_is_skew_with_norm_l(oracle_lib):
+    # Lemma 1: B z = (A~^* y, -A~ x), A~ = sum_l p_l K_l / sqrt(mu), is
+    # skew-symmetric (<z, B z> = 0: the projector pair is adjoint) and its
+    # norm is L, attained at z = (v, 0) with v the top right singular vector
+    p = inputs.Problem(n=16, n_angles=12, n_det=24, geometry=1, angle_span=2 * math.pi,
+                       levels=3)
+    mu = 0.6
+    o = Oracle(**dict(p.params(), mu=mu, sigma=0.1))
+    pr = o.probs()
+
+    def A(x):
+        return sum(pr[l] * o.K(l, x).ravel() for l in range(o.r)) / math.sqrt(mu)
+
+    def At(y):
+        return sum(pr[l] * o.KT(l, y).ravel() for l in range(o.r)) / math.sqrt(mu)
+
+    L = o.constants(300)[0]
+    rng = np.random.default_rng(3)
+    for _ in range(4):
+        x = rng.standard_normal(o.n * o.n)
+        y = rng.standard_normal(o.m)
+        bx, by = At(y), -A(x)
+        nz = math.sqrt(x @ x + y @ y)
+        nb = math.sqrt(bx @ bx + by @ by)
+        assert abs(x @ bx + y @ by) <= 1e-13 * nz * nb
+        assert nb <= L * nz * (1 + 1e-9)
+    v = rng.standard_normal(o.n * o.n)
+    for _ in range(400):
+        v = At(A(v))
+        v /= np.linalg.norm(v)
+    assert abs(np.linalg.norm(A(v)) - L) <= 1e-6 * L
