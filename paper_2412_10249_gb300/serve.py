@@ -10,7 +10,9 @@ against the budget too; idle plans are evicted least recently used).  Every
 admitted solve runs on its own CUDA stream, so solves that arrive while others
 are on the device overlap with them.  A solve advances in quanta of iterations;
 after the last quantum its iterate is copied to pinned host memory and its
-state is freed.  Latency is measured from arrival to that host copy.
+state is freed.  Latency is measured from arrival to that host copy.  A
+request can be withdrawn while it waits or runs (Server.cancel): a running
+solve stops at the end of its quantum in flight and frees its state.
 
 All arithmetic runs in the library's kernels; this module only schedules.
 The device operations sit behind a backend object (CudaBackend by default),
@@ -44,7 +46,8 @@ class Request:
     admitted: float = math.nan
     finished: float = math.nan
     x: object = None                  # host copy of the result (pinned tensor on CUDA)
-    status: str = "pending"           # pending, queued, active, done, rejected, failed
+    status: str = "pending"           # pending, queued, active, done, rejected, failed,
+                                      # cancelled
 
 
 @dataclass
@@ -56,6 +59,7 @@ class _Active:
     bytes: int
     event: object = None   # the backend's completion marker of the last work
     finishing: bool = False
+    cancelled: bool = False
 
 
 def geometry_key(params: dict) -> tuple:
@@ -161,6 +165,7 @@ class ServerStats:
     plans_built: int = 0
     plan_seconds: float = 0.0
     failed: int = 0
+    cancelled: int = 0
     failed_plans: list = field(default_factory=list)
     latencies: list = field(default_factory=list)
     waits: list = field(default_factory=list)
@@ -271,6 +276,25 @@ class Server:
         self.queue.append(req)
         return True
 
+    def cancel(self, rid: int) -> bool:
+        """Withdraws request `rid` (call from the thread that polls).  A queued
+        request leaves the queue; an active solve stops at the end of the
+        quantum in flight, without a result, and its state is freed.  False if
+        the request is not queued or active, or its result is already being
+        copied out."""
+        for req in self.queue:
+            if req.rid == rid:
+                self.queue.remove(req)
+                self.prepared.pop(rid, None)
+                req.status = "cancelled"
+                self.stats.cancelled += 1
+                return True
+        for a in self.active:
+            if a.req.rid == rid and not a.cancelled and not a.finishing:
+                a.cancelled = True
+                return True
+        return False
+
     def _admit(self):
         self._collect_plans()
         for req in list(self.queue[: 2 * self.max_active]):
@@ -319,7 +343,9 @@ class Server:
         for a in self.active:
             if a.finishing or (a.event is not None and not be.done(a.event)):
                 continue
-            if a.remaining > 0:
+            if a.cancelled:
+                a.finishing = True   # nothing more is launched; no result is read
+            elif a.remaining > 0:
                 q = min(self.quantum, a.remaining)
                 be.step(a.solve, q)
                 a.remaining -= q
@@ -333,10 +359,14 @@ class Server:
         for a in self.active:
             if a.finishing and self.backend.done(a.event):
                 a.req.finished = self.now()
-                a.req.status = "done"
-                self.stats.completed += 1
-                self.stats.latencies.append(a.req.finished - a.req.arrival)
-                self.stats.waits.append(a.req.admitted - a.req.arrival)
+                if a.cancelled:
+                    a.req.status = "cancelled"
+                    self.stats.cancelled += 1
+                else:
+                    a.req.status = "done"
+                    self.stats.completed += 1
+                    self.stats.latencies.append(a.req.finished - a.req.arrival)
+                    self.stats.waits.append(a.req.admitted - a.req.arrival)
                 self.backend.finish(a.solve)
                 self.plan_users[a.plan_key] -= 1
                 self.used -= a.bytes

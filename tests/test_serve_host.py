@@ -135,3 +135,30 @@ def test_idle_plans_are_evicted_under_pressure():
     assert st.completed == 6
     assert st.peak_bytes <= budget
     assert st.plans_built > 3                    # some plans were rebuilt after eviction
+
+
+def test_cancelled_requests_free_their_slots():
+    be = FakeBackend()
+    reqs = [_req(i, 8, 40) for i in range(4)]
+    srv = serve.Server(budget_bytes=10 ** 9, max_active=2, quantum=4, backend=be)
+    for r in reqs:
+        srv.offer(r)
+    for _ in range(1000):
+        srv.poll()
+        if reqs[0].status == "active" and reqs[1].status == "active":
+            break
+    assert reqs[0].status == "active" and reqs[3].status == "queued"
+    assert srv.cancel(reqs[3].rid)          # queued: leaves at once
+    assert reqs[3].status == "cancelled"
+    assert srv.cancel(reqs[0].rid)          # active: stops after its quantum
+    assert not srv.cancel(reqs[0].rid)      # already withdrawn
+    assert not srv.cancel(12345)            # unknown
+    st = srv.run([])
+    assert reqs[0].status == "cancelled" and reqs[0].x is None
+    assert [r.status for r in reqs[1:3]] == ["done", "done"]
+    assert [list(r.x) for r in reqs[1:3]] == [[40, 101], [40, 102]]
+    assert st.completed == 2 and st.cancelled == 2
+    # only the plan still holds memory; no solve is left running
+    assert srv.used == sum(pb for _, pb, _ in srv.plans.values())
+    assert sum(be.running.values()) == 0
+    srv.close()
