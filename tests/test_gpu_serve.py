@@ -78,3 +78,28 @@ def test_oversize_request_is_rejected(mods):
     st = srv.run(reqs)
     srv.close()
     assert st.rejected_too_large == 2 and st.completed == 0
+
+
+def test_cancelled_solve_frees_its_state(mods):
+    imask, serve = mods
+    reqs = _requests(serve)[:3]
+    for r in reqs:
+        r.arrival = 0.0
+        r.iters = 400               # long enough to still be running when withdrawn
+    srv = serve.Server(budget_bytes=8 << 30, max_active=2, quantum=5)
+    for r in reqs:
+        srv.offer(r)
+    for _ in range(100000):
+        srv.poll()
+        if reqs[0].status == "active" and reqs[1].status == "active":
+            break
+    assert reqs[0].status == "active" and reqs[2].status == "queued"
+    assert srv.cancel(reqs[0].rid)
+    st = srv.run([])
+    assert reqs[0].status == "cancelled" and reqs[0].x is None
+    assert [r.status for r in reqs[1:]] == ["done", "done"]
+    assert st.cancelled == 1 and st.completed == 2
+    assert srv.used == sum(pb for _, pb, _ in srv.plans.values())
+    srv.close()
+    for r in reqs[1:]:
+        assert torch.equal(r.x, _alone(imask, serve, r)), r.rid
