@@ -126,6 +126,9 @@ struct imask_plan_s {
   float2 *d_rays_lo = nullptr;
   ViewInfo *d_views = nullptr;
   int *d_bp_order = nullptr;
+  int *d_bp_views = nullptr;    // per role, the views holding rays of that role
+  int *d_bp_vb = nullptr;       // per level and role, the view-group bounds
+  std::vector<int> role_rays[2];   // rays of the role in each listed view
   size_t gcap = 0;   // floats of the back-projector's partial-sum buffer
   unsigned int *d_err = nullptr;
   std::vector<int> split, first_x;
@@ -465,6 +468,56 @@ imask_status apply_KT(const imask_plan_s *p, int ell, const float *y, float *img
 }
 
 // ---------------------------------------------------------------------------------
+// Back-projector view groups: the views holding rays of one major axis are
+// split into vgo consecutive groups of about equal numbers of rays (a view
+// goes to the group that holds the midpoint of its rays in the running
+// count).  Writes bounds[0..vgo] (positions in the role's view list) and
+// returns the largest group.  Groups may be empty.
+// ---------------------------------------------------------------------------------
+int bp_group_bounds(const std::vector<int> &rays, int vgo, int *bounds) {
+  const int nv = (int)rays.size();
+  long long tot = 0;
+  for (int w : rays) tot += w;
+  int g = 0, largest = 0, start = 0;
+  bounds[0] = 0;
+  long long acc = 0;
+  for (int i = 0; i < nv; ++i) {
+    const int gi = tot > 0 ? (int)std::min<long long>(vgo - 1, ((2 * acc + rays[i]) * vgo) / (2 * tot))
+                           : 0;
+    while (g < gi) {
+      bounds[++g] = i;
+      largest = std::max(largest, i - start);
+      start = i;
+    }
+    acc += rays[i];
+  }
+  while (g < vgo) {
+    bounds[++g] = nv;
+    largest = std::max(largest, nv - start);
+    start = nv;
+  }
+  return largest;
+}
+
+// Bounds of both roles for level index li into the plan's device table (on
+// st), and the level's largest group.
+imask_status upload_bp_groups(imask_plan_s *p, int li, cudaStream_t st) {
+  LevelGeom &g = p->dp.lg[li];
+  const int na = p->desc.n_angles;
+  std::vector<int> b(2 * (size_t)(na + 1), 0);
+  int largest = 1;
+  for (int role = 0; role < 2; ++role)
+    largest = std::max(largest, bp_group_bounds(p->role_rays[role], g.bp_vgo,
+                                                b.data() + role * (na + 1)));
+  g.bp_nv = largest;
+  if (p->d_bp_vb)
+    CK(cudaMemcpyAsync(p->d_bp_vb + (size_t)li * 2 * (na + 1), b.data(), b.size() * sizeof(int),
+                       cudaMemcpyHostToDevice, st),
+       "upload view groups");
+  return IMASK_OK;
+}
+
+// ---------------------------------------------------------------------------------
 // Plan-time autotuning of the back-projector's view-group split: for every
 // level, K_ell^T (back-projector and the partial-image sum that consumes its
 // output) is timed with CUDA events for split counts around the occupancy
@@ -505,7 +558,7 @@ imask_status autotune_bp(imask_plan_s *p, cudaStream_t st) {
     for (int v : cand[li]) {
       LevelGeom &g = dp.lg[li];
       g.bp_vgo = v;
-      g.bp_nv = (na + v - 1) / v;
+      if ((rc = upload_bp_groups(p, li, st)) != IMASK_OK) break;
       if (bp_smem_bytes(dp) > 160 * 1024) continue;
       float ms = 0.0f, tot = 0.0f;
       for (int rep = 0; rep < 4 && rc == IMASK_OK && e == cudaSuccess; ++rep) {
@@ -524,7 +577,7 @@ imask_status autotune_bp(imask_plan_s *p, cudaStream_t st) {
       }
     }
     dp.lg[li].bp_vgo = best_v;
-    dp.lg[li].bp_nv = (na + best_v - 1) / best_v;
+    if (rc == IMASK_OK) rc = upload_bp_groups(p, li, st);
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
@@ -1027,10 +1080,23 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
       g.bp_vgo = bv;
     }
   }
+  std::vector<int> role_views;   // role 0 list, then role 1 list, each padded to na
+  role_views.assign(2 * (size_t)na, 0);
+  {
+    int cnt[2] = {0, 0};
+    for (int a = 0; a < na; ++a) {
+      const int nr[2] = {views[a].xj1 - views[a].xj0, views[a].yj1 - views[a].yj0};
+      for (int role = 0; role < 2; ++role)
+        if (nr[role] > 0) {
+          role_views[(size_t)role * na + cnt[role]++] = a;
+          p->role_rays[role].push_back(nr[role]);
+        }
+    }
+  }
   p->gcap = 0;
   for (int li = 0; li <= r; ++li) {
     LevelGeom &g = dp.lg[li];
-    g.bp_nv = (desc->n_angles + g.bp_vgo - 1) / g.bp_vgo;
+    upload_bp_groups(p, li, nullptr);   // bounds and bp_nv only (no table yet)
     p->gcap = std::max(p->gcap, (size_t)2 * g.bp_vgo * g.nl * g.nl);
   }
   if (bp_smem_bytes(dp) > 160 * 1024) {
@@ -1051,7 +1117,10 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
       (e = cudaMalloc(&p->d_rays_lo, rays_lo.size() * sizeof(float2))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_views, views.size() * sizeof(ViewInfo))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_bp_order, order.size() * sizeof(int))) != cudaSuccess) {
+      (e = cudaMalloc(&p->d_bp_order, order.size() * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_bp_views, role_views.size() * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_bp_vb, (size_t)(r + 1) * 2 * (na + 1) * sizeof(int))) !=
+          cudaSuccess) {
     imask_plan_destroy(p);
     return cuda_fail(e, "cudaMalloc(plan)");
   }
@@ -1073,6 +1142,8 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(p->d_bp_order, order.data(), order.size() * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p->d_bp_views, role_views.data(), role_views.size() * sizeof(int),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess) {
     cudaStreamSynchronize(st);
@@ -1084,8 +1155,11 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.rays_lo = p->d_rays_lo;
   dp.views = p->d_views;
   dp.bp_order = p->d_bp_order;
+  dp.bp_views = p->d_bp_views;
+  dp.bp_vb = p->d_bp_vb;
+  for (int li = 0; li <= r && rc == IMASK_OK; ++li) rc = upload_bp_groups(p, li, st);
 
-  rc = p->desc.autotune ? autotune_bp(p, st) : IMASK_OK;
+  if (rc == IMASK_OK && p->desc.autotune) rc = autotune_bp(p, st);
   if (rc == IMASK_OK) rc = plan_constants(p, st);
   e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
@@ -1106,6 +1180,8 @@ imask_status imask_plan_destroy(imask_plan_t p) {
   if (p->d_views) cudaFree(p->d_views);
   if (p->d_err) cudaFree(p->d_err);
   if (p->d_bp_order) cudaFree(p->d_bp_order);
+  if (p->d_bp_views) cudaFree(p->d_bp_views);
+  if (p->d_bp_vb) cudaFree(p->d_bp_vb);
   delete p;
   return IMASK_OK;
 }

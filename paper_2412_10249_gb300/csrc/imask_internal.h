@@ -76,6 +76,13 @@ struct DevPlan {
   // back-projector CTA order per level: (role * tiles + tile) codes, heaviest
   // (most rays to apply) first; the view groups of one code are adjacent
   const int *bp_order;
+  // back-projector view groups.  bp_views[role * n_angles + i] lists the views
+  // holding rays of that major axis (role 0: x-major); for level index li the
+  // view group vg of a role covers list positions [b[vg], b[vg + 1]) with
+  // b = bp_vb + (li * 2 + role) * (n_angles + 1), the groups holding about
+  // equal numbers of rays
+  const int *bp_views;
+  const int *bp_vb;
 };
 
 // Padded level images: for every level index li (0: level -1, ell + 1: ell),

@@ -410,8 +410,9 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 // Back-projector: g = R_ell^T y on the level grid, owner-computes (no atomics).
 //
 // The x-major and y-major rays go to separate CTAs.  An x-major CTA owns a tile
-// of BP_W columns x BP_SEG rows of level pixels and a contiguous range of views
-// (bp_vgo ranges across CTAs; the consumer adds the partial images, 2 bp_vgo of
+// of BP_W columns x BP_SEG rows of level pixels and one of bp_vgo groups of
+// consecutive views that hold x-major rays, the groups holding about equal
+// numbers of such rays (the consumer adds the partial images, 2 bp_vgo of
 // them, in a fixed order).  CTAs take (role, tile) pairs from the plan's
 // heaviest-first order, so that light tiles fill the last wave.  Thread t owns the column t % BP_W of the tile, a
 // segment of BP_SEG rows with private accumulators in shared memory, and takes
@@ -520,9 +521,11 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
   const int tile = code - role * ntile;
   const int mb = tile % nm, cb = tile / nm;   // march block (BP_W lines), cross block (BP_SEG)
   const int tid = threadIdx.x;
-  const int a0 = (int)(((long long)vg * P.n_angles) / vgo);
-  const int a1 = (int)(((long long)(vg + 1) * P.n_angles) / vgo);
-  const int nv = a1 - a0;
+  // this CTA's views: a group of the views holding rays of its major axis
+  const int *vb = P.bp_vb + ((ell + 1) * 2 + role) * (P.n_angles + 1);
+  const int a0 = vb[vg];
+  const int nv = vb[vg + 1] - a0;
+  const int *vlist = P.bp_views + role * P.n_angles + a0;
   const float hl = G.hl, W = P.fov;
   int2 *vinfo = bp_vinfo(bp_raw);   // per view: ray-list index and y index of the window start
   int *pref = (int *)(vinfo + nv_cap);   // nv_cap + 1 prefix counts
@@ -535,7 +538,13 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
     const float clo = -0.5f * W + ((float)c0 + 0.5f) * hl - hl;
     const float chi = -0.5f * W + ((float)c1 + 0.5f) * hl + hl;
     for (int v = tid; v < nv; v += BP_THREADS) {
-      const ViewInfo V = P.views[a0 + v];
+      const int a = vlist[v];
+      if (!IMASK_INDEX_OK(a >= 0 && a < P.n_angles, 2)) {
+        vinfo[v] = make_int2(0, 0);
+        pref[v] = 0;
+        continue;
+      }
+      const ViewInfo V = P.views[a];
       float mn = 1.0e30f, mx = -1.0e30f;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -549,7 +558,7 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
       const int lo = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
       const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
       const int base = role == 0 ? V.xoff - V.xj0 : V.yoff - V.yj0;
-      vinfo[v] = make_int2(base + lo, (a0 + v) * P.n_det + lo);
+      vinfo[v] = make_int2(base + lo, a * P.n_det + lo);
       pref[v] = max(hi - lo + 1, 0);
     }
     for (int k = tid; k < BP_ACC * BP_THREADS; k += BP_THREADS) acc_s[k] = 0.0f;
