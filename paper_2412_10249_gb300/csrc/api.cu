@@ -1207,9 +1207,12 @@ imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
     info->bp_view_groups[l] = l < p->desc.levels ? p->dp.lg[l + 1].bp_vgo : 0;
   int64_t n_order = 0;
   for (int li = 0; li <= p->desc.levels; ++li) n_order += 2 * p->dp.lg[li].bp_nm * p->dp.lg[li].bp_nc;
+  const int64_t na = p->dp.n_angles;
   info->plan_bytes = (int64_t)(p->dp.m * (sizeof(float4) + sizeof(float2)) +
-                               p->dp.n_angles * sizeof(ViewInfo) + sizeof(unsigned int)) +
-                     n_order * (int64_t)sizeof(int);
+                               na * sizeof(ViewInfo) + sizeof(unsigned int)) +
+                     n_order * (int64_t)sizeof(int) +
+                     (2 * na + (int64_t)(p->desc.levels + 1) * 2 * (na + 1)) *
+                         (int64_t)sizeof(int);   // view lists and view-group bounds
   return IMASK_OK;
 }
 

@@ -211,10 +211,13 @@ class Server:
     @staticmethod
     def plan_bytes_estimate(params: dict) -> int:
         # the plan's device tables: 24 bytes per ray, 32 per view, an error
-        # flag, and the back-projector's tile order (under 4 x 2 n^2/512 bytes)
-        m = int(params["n_angles"]) * int(params["n_det"])
+        # flag, the back-projector's tile order (under 4 x 2 n^2/512 bytes),
+        # its per-axis view lists and the view-group bounds of every level
+        na = int(params["n_angles"])
+        m = na * int(params["n_det"])
         n = int(params["n"])
-        return 24 * m + 32 * int(params["n_angles"]) + 4 + 16 * (n // 16 + 1) * (n // 32 + 1)
+        groups = 8 * na + 8 * (int(params.get("levels", 1)) + 1) * (na + 1)
+        return 24 * m + 32 * na + 4 + 16 * (n // 16 + 1) * (n // 32 + 1) + groups
 
     def _prepare(self, req: Request) -> bool:
         """Starts the plan build (memory permitting) and the sinogram; False

@@ -103,3 +103,12 @@ def test_cancelled_solve_frees_its_state(mods):
     srv.close()
     for r in reqs[1:]:
         assert torch.equal(r.x, _alone(imask, serve, r)), r.rid
+
+
+def test_plan_bytes_estimate_bounds_the_plan(mods):
+    # the loop reserves the estimate while a plan is being built
+    imask, serve = mods
+    for r in _requests(serve):
+        plan = imask.Plan(dict(r.params, mu=0.3, sigma=0.03))
+        assert serve.Server.plan_bytes_estimate(r.params) >= plan.info["plan_bytes"]
+        plan.close()
