@@ -162,6 +162,17 @@ imask_status imask_plan_axis_split(imask_plan_t plan, int32_t *split, int32_t *f
  * host geometry).  Errors: INVALID, SHAPE. */
 imask_status imask_geometry_axis_split(const imask_desc *desc, int32_t *split, int32_t *first_x);
 
+/* The back-projector's view groups, on the host alone: the views holding rays
+ * of one major axis (role 0 x-major, 1 y-major) in increasing order, into
+ * views[0 .. *n_views) (n_angles entries of room), and their split into
+ * n_groups consecutive groups of about equal numbers of such rays, group g
+ * being views[bounds[g] .. bounds[g + 1]) (n_groups + 1 entries; a view goes to
+ * the group that holds the midpoint of its rays in the running count; groups
+ * may be empty).  Plans use these groups for their per-level split counts.
+ * Errors: INVALID, SHAPE. */
+imask_status imask_geometry_view_groups(const imask_desc *desc, int32_t role, int32_t n_groups,
+                                        int32_t *views, int32_t *n_views, int32_t *bounds);
+
 /* Thm. 3 step size from given constants (host FP64, grid x grid search over
  * (c, rho) in (0, cbar) x (0, 1)): out = {sigma, theta, c, rho}. */
 imask_status imask_optimal_step(double L, double Lbar, double Lbar_p, double p_min,

@@ -474,6 +474,25 @@ imask_status apply_KT(const imask_plan_s *p, int ell, const float *y, float *img
 // count).  Writes bounds[0..vgo] (positions in the role's view list) and
 // returns the largest group.  Groups may be empty.
 // ---------------------------------------------------------------------------------
+// Per major axis (role 0: x-major), the views that hold rays of that axis and
+// their ray counts, from the per-view split of the ray list.
+void bp_role_lists(const std::vector<int> &split, const std::vector<int> &first_x, int n_det,
+                   std::vector<int> views[2], std::vector<int> rays[2]) {
+  for (int role = 0; role < 2; ++role) {
+    views[role].clear();
+    rays[role].clear();
+  }
+  for (int a = 0; a < (int)split.size(); ++a) {
+    const int nx = first_x[a] ? split[a] : n_det - split[a];
+    const int nr[2] = {nx, n_det - nx};
+    for (int role = 0; role < 2; ++role)
+      if (nr[role] > 0) {
+        views[role].push_back(a);
+        rays[role].push_back(nr[role]);
+      }
+  }
+}
+
 int bp_group_bounds(const std::vector<int> &rays, int vgo, int *bounds) {
   const int nv = (int)rays.size();
   long long tot = 0;
@@ -883,6 +902,25 @@ imask_status imask_geometry_axis_split(const imask_desc *desc, int32_t *split, i
   return IMASK_OK;
 }
 
+imask_status imask_geometry_view_groups(const imask_desc *desc, int32_t role, int32_t n_groups,
+                                        int32_t *views, int32_t *n_views, int32_t *bounds) {
+  imask_status rc = validate(desc);
+  if (rc != IMASK_OK) return rc;
+  if (!views || !n_views || !bounds) return fail(IMASK_ERR_INVALID, "NULL output");
+  if (role != 0 && role != 1) return fail(IMASK_ERR_INVALID, "role must be 0 or 1");
+  if (n_groups < 1) return fail(IMASK_ERR_INVALID, "n_groups must be >= 1");
+  std::vector<int> s, f;
+  if ((rc = axis_split(*desc, s, f)) != IMASK_OK) return rc;
+  std::vector<int> lists[2], rays[2];
+  bp_role_lists(s, f, desc->n_det, lists, rays);
+  std::vector<int> b((size_t)n_groups + 1);
+  bp_group_bounds(rays[role], n_groups, b.data());
+  *n_views = (int32_t)lists[role].size();
+  for (size_t i = 0; i < lists[role].size(); ++i) views[i] = lists[role][i];
+  for (int g = 0; g <= n_groups; ++g) bounds[g] = b[g];
+  return IMASK_OK;
+}
+
 // Thm. 3 on the grid c = cbar (i + 1/2)/G, rho = (j + 1/2)/G: eta* = c when
 // p_min > (Lbar^2/rho (1 - (1+L^2)c) / (1 - (1+L^2+Lbar_p^2)c) + 1 - rho) c,
 // else the crossing (sqrt(1 + D (p_min + rho c)) - 1) / D, D = 1/alpha - 1/c;
@@ -1083,15 +1121,10 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   std::vector<int> role_views;   // role 0 list, then role 1 list, each padded to na
   role_views.assign(2 * (size_t)na, 0);
   {
-    int cnt[2] = {0, 0};
-    for (int a = 0; a < na; ++a) {
-      const int nr[2] = {views[a].xj1 - views[a].xj0, views[a].yj1 - views[a].yj0};
-      for (int role = 0; role < 2; ++role)
-        if (nr[role] > 0) {
-          role_views[(size_t)role * na + cnt[role]++] = a;
-          p->role_rays[role].push_back(nr[role]);
-        }
-    }
+    std::vector<int> lists[2];
+    bp_role_lists(p->split, p->first_x, nd, lists, p->role_rays);
+    for (int role = 0; role < 2; ++role)
+      std::copy(lists[role].begin(), lists[role].end(), role_views.begin() + (size_t)role * na);
   }
   p->gcap = 0;
   for (int li = 0; li <= r; ++li) {

@@ -78,6 +78,8 @@ SIGNATURES = {
     "imask_plan_check": (_I32, [_VP]),
     "imask_plan_axis_split": (_I32, [_VP, _I32P, _I32P]),
     "imask_geometry_axis_split": (_I32, [ctypes.POINTER(Desc), _I32P, _I32P]),
+    "imask_geometry_view_groups": (_I32, [ctypes.POINTER(Desc), _I32, _I32, _I32P, _I32P,
+                                          _I32P]),
     "imask_optimal_step": (_I32, [ctypes.c_double] * 4 + [_I32, _DP]),
     "imask_project": (_I32, [_VP, _I32, _VP, _VP, _VP]),
     "imask_backproject": (_I32, [_VP, _I32, _VP, _VP, _VP]),
@@ -220,6 +222,17 @@ def imask_geometry_axis_split(params: dict):
     fx = (ctypes.c_int32 * na)()
     _check(lib().imask_geometry_axis_split(ctypes.byref(d), split, fx))
     return list(split), list(fx)
+
+
+def imask_geometry_view_groups(params: dict, role: int, n_groups: int):
+    """(views of the role, group bounds) of the back-projector's split."""
+    d, keep = make_desc(params)
+    views = (ctypes.c_int32 * max(1, d.n_angles))()
+    nv = ctypes.c_int32(0)
+    bounds = (ctypes.c_int32 * (n_groups + 1))()
+    _check(lib().imask_geometry_view_groups(ctypes.byref(d), role, n_groups, views,
+                                            ctypes.byref(nv), bounds))
+    return list(views[:nv.value]), list(bounds)
 
 
 def imask_optimal_step(L, Lbar, Lbar_p, p_min, grid=200):

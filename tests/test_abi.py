@@ -99,3 +99,52 @@ def test_pdhg_params_match_oracle(imask):
         np.testing.assert_allclose(got, ref, rtol=1e-15)
     with pytest.raises(imask.ImaskError):
         imask.imask_pdhg_params(1.0, 0.0, 0.99)
+
+
+def _role_rays(imask, params):
+    split, first_x = imask.imask_geometry_axis_split(params)
+    nd = params["n_det"]
+    nx = [s if f else nd - s for s, f in zip(split, first_x)]
+    return nx, [nd - v for v in nx]
+
+
+@pytest.mark.parametrize("name", ["fan512", "parallel_pi", "fan_small"])
+@pytest.mark.parametrize("n_groups", [1, 4, 7, 57, 400])
+def test_view_groups_cover_the_axis_and_balance_its_rays(imask, name, n_groups):
+    # the back-projector's view groups (host logic, no device): every view with
+    # rays of a major axis is listed once, in order; the groups are consecutive
+    # and cover the list; a view sits in the group of its rays' midpoint, so a
+    # group's ray count is within one view's count of the even share
+    if name == "fan512":
+        params = dict(inputs.fan512_problem().params(), mu=1.0, sigma=0.1)
+    elif name == "parallel_pi":
+        params = dict(inputs.Problem(n=64, n_angles=60, n_det=92, geometry=0,
+                                     levels=2).params(), mu=1.0, sigma=0.1)
+    else:
+        params = dict(inputs.Problem(n=32, n_angles=30, n_det=48, geometry=1,
+                                     angle_span=2 * math.pi, levels=3).params(), mu=1.0,
+                      sigma=0.1)
+    rays = _role_rays(imask, params)
+    for role in (0, 1):
+        views, bounds = imask.imask_geometry_view_groups(params, role, n_groups)
+        assert views == [a for a in range(params["n_angles"]) if rays[role][a] > 0]
+        assert bounds[0] == 0 and bounds[-1] == len(views) and len(bounds) == n_groups + 1
+        assert all(b0 <= b1 for b0, b1 in zip(bounds, bounds[1:]))
+        w = [rays[role][a] for a in views]
+        tot, wmax = sum(w), max(w)
+        for g in range(n_groups):
+            share = sum(w[bounds[g]:bounds[g + 1]])
+            assert abs(share - tot / n_groups) <= wmax + 1e-9
+        # the midpoint rule, view by view
+        acc = 0
+        for i, wi in enumerate(w):
+            g = min(n_groups - 1, ((2 * acc + wi) * n_groups) // (2 * tot))
+            assert bounds[g] <= i < bounds[g + 1]
+            acc += wi
+
+
+def test_view_groups_reject_bad_arguments(imask):
+    params = dict(inputs.fan512_problem().params(), mu=1.0, sigma=0.1)
+    for role, g in ((2, 4), (-1, 4), (0, 0)):
+        with pytest.raises(imask.ImaskError):
+            imask.imask_geometry_view_groups(params, role, g)
