@@ -255,6 +255,19 @@ int64_t imask_state_iteration(imask_state_t state);
  * 2 the running mean sum_l p_l phi_l [n*n], 3 the running mean sum_l p_l psi_l [m]. */
 imask_status imask_state_get(imask_state_t state, int32_t what, float *dst_dev, void *stream);
 imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
+/* Checkpoints.  imask_state_save writes the whole state (iterates, tables,
+ * running means, sketch images, b, the iteration counter, the seeds and the
+ * dual ping-pong parity) into dst_dev, a device buffer of
+ * imask_state_checkpoint_bytes(state) bytes, ordered after the state's work
+ * and on stream.  imask_state_load restores such a checkpoint into a state of
+ * a plan with the same descriptor (it synchronises stream and the state's
+ * stream); stepping then continues exactly as the saved state would have, the
+ * level streams being counter-based.  INVALID for a checkpoint of another
+ * plan or storage format, or for a state whose tables changed storage
+ * (imask_state_set_storage). */
+int64_t imask_state_checkpoint_bytes(imask_state_t state);
+imask_status imask_state_save(imask_state_t state, void *dst_dev, void *stream);
+imask_status imask_state_load(imask_state_t state, const void *src_dev, void *stream);
 /* Converts the state's measurement-side tables to another storage format
  * (0 fp32, 1 bf16, 2 fp16) and re-forms their running mean from the converted
  * tables; later iterations use the new format (widening to fp32 is exact: the

@@ -1799,6 +1799,84 @@ imask_status imask_state_get_x(imask_state_t s, float *x_dev, void *stream) {
   return imask_state_get(s, 0, x_dev, stream);
 }
 
+namespace {
+
+// Header of a state checkpoint, followed by the state's device block.
+struct CheckpointHeader {
+  uint64_t magic;          // kCheckpointMagic
+  uint64_t block_floats;   // size of the state's block
+  int64_t k;               // iteration counter
+  uint64_t seed, seed_x;   // level streams
+  int32_t cur;             // dual ping-pong parity
+  int32_t psi_fmt;         // storage format of the tables
+  uint64_t reserved[2];
+};
+constexpr uint64_t kCheckpointMagic = 0x31504b43534b4d49ull;   // "IMSKCKP1"
+
+size_t state_block_floats(const imask_state_s *s) { return state_layout(s->plan).total; }
+
+}  // namespace
+
+int64_t imask_state_checkpoint_bytes(imask_state_t s) {
+  if (!s) return -1;
+  return (int64_t)(sizeof(CheckpointHeader) + state_block_floats(s) * sizeof(float));
+}
+
+imask_status imask_state_save(imask_state_t s, void *dst, void *stream) {
+  if (!s || !dst) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (s->psi_block)
+    return fail(IMASK_ERR_INVALID, "a state whose tables changed storage cannot be saved");
+  cudaStream_t st = (cudaStream_t)stream;
+  CheckpointHeader h{};
+  h.magic = kCheckpointMagic;
+  h.block_floats = state_block_floats(s);
+  h.k = s->k;
+  h.seed = s->seed;
+  h.seed_x = s->seed_x;
+  h.cur = s->cur;
+  h.psi_fmt = s->psi_fmt;
+  // the state's side streams are joined into its stream after every step
+  if (s->stream != st) {
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "checkpoint order");
+    cudaError_t e = cudaEventRecord(ev, s->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "checkpoint order");
+  }
+  CK(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, st), "checkpoint header");
+  CK(cudaMemcpyAsync((char *)dst + sizeof(h), s->block, h.block_floats * sizeof(float),
+                     cudaMemcpyDeviceToDevice, st),
+     "checkpoint block");
+  return IMASK_OK;
+}
+
+imask_status imask_state_load(imask_state_t s, const void *src, void *stream) {
+  if (!s || !src) return fail(IMASK_ERR_INVALID, "NULL argument");
+  if (s->psi_block)
+    return fail(IMASK_ERR_INVALID, "a state whose tables changed storage cannot be loaded");
+  cudaStream_t st = (cudaStream_t)stream;
+  CheckpointHeader h{};
+  CK(cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, st), "checkpoint header");
+  CK(cudaStreamSynchronize(st), "checkpoint header");
+  if (h.magic != kCheckpointMagic) return fail(IMASK_ERR_INVALID, "not a state checkpoint");
+  if (h.block_floats != state_block_floats(s) || h.psi_fmt != s->psi_fmt)
+    return fail(IMASK_ERR_INVALID, "checkpoint of a state of another plan or storage");
+  // the state's own pending work comes first
+  CK(cudaStreamSynchronize(s->stream), "checkpoint order");
+  CK(cudaMemcpyAsync(s->block, (const char *)src + sizeof(h), h.block_floats * sizeof(float),
+                     cudaMemcpyDeviceToDevice, st),
+     "checkpoint block");
+  s->k = h.k;
+  s->seed = h.seed;
+  s->seed_x = h.seed_x;
+  s->cur = h.cur;
+  s->stream = st;
+  s->k_dev_stale = true;   // the device counter is set again before the next replay
+  s->gen += 1;             // graphs captured before the load are captured again
+  return IMASK_OK;
+}
+
 imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *stream) {
   if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
   if (storage < 0 || storage > 2) return fail(IMASK_ERR_INVALID, "storage must be 0, 1 or 2");

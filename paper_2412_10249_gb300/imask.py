@@ -89,6 +89,9 @@ SIGNATURES = {
     "imask_step": (_I32, [_VP, _I32, _VP]),
     "imask_state_iteration": (_I64, [_VP]),
     "imask_state_get": (_I32, [_VP, _I32, _VP, _VP]),
+    "imask_state_checkpoint_bytes": (_I64, [_VP]),
+    "imask_state_save": (_I32, [_VP, _VP, _VP]),
+    "imask_state_load": (_I32, [_VP, _VP, _VP]),
     "imask_state_get_x": (_I32, [_VP, _VP, _VP]),
     "imask_state_destroy": (_I32, [_VP]),
     "imask_solve": (_I32, [_VP, _VP, _U64, _I32, _VP, _VP]),
@@ -418,6 +421,24 @@ class State:
         _check(lib().imask_state_get(self.handle, what, _ptr(out, n, name="out"),
                                      _stream(stream)))
         return out
+
+    def save(self, stream=None) -> torch.Tensor:
+        """A checkpoint of the whole state in a device byte tensor."""
+        n = int(lib().imask_state_checkpoint_bytes(self.handle))
+        out = torch.empty(n, device="cuda", dtype=torch.uint8)
+        _check(lib().imask_state_save(self.handle, ctypes.c_void_p(out.data_ptr()),
+                                      _stream(stream)))
+        return out
+
+    def load(self, checkpoint: torch.Tensor, stream=None):
+        """Restores a checkpoint of a state of a plan with the same descriptor."""
+        if not (checkpoint.is_cuda and checkpoint.dtype == torch.uint8
+                and checkpoint.is_contiguous()):
+            raise ValueError("checkpoint must be a contiguous CUDA uint8 tensor")
+        if checkpoint.numel() != int(lib().imask_state_checkpoint_bytes(self.handle)):
+            raise ValueError("checkpoint size does not match this state")
+        _check(lib().imask_state_load(self.handle, ctypes.c_void_p(checkpoint.data_ptr()),
+                                      _stream(stream)))
 
     def close(self):
         if self.handle:
