@@ -260,9 +260,11 @@ imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
  * dual ping-pong parity) into dst_dev, a device buffer of
  * imask_state_checkpoint_bytes(state) bytes, ordered after the state's work
  * and on stream.  imask_state_load restores such a checkpoint into a state of
- * a plan with the same descriptor (it synchronises stream and the state's
- * stream); stepping then continues exactly as the saved state would have, the
- * level streams being counter-based.  INVALID for a checkpoint of another
+ * the same plan, or of a plan built from the same descriptor on the same kind
+ * of device (with autotune, its split counts must match too: the block holds
+ * the back-projector's partial images); it synchronises stream and the
+ * state's stream.  Stepping then continues exactly as the saved state would
+ * have, the level streams being counter-based.  INVALID for a checkpoint of another
  * plan or storage format, or for a state whose tables changed storage
  * (imask_state_set_storage). */
 int64_t imask_state_checkpoint_bytes(imask_state_t state);
