@@ -148,3 +148,20 @@ def test_view_groups_reject_bad_arguments(imask):
     for role, g in ((2, 4), (-1, 4), (0, 0)):
         with pytest.raises(imask.ImaskError):
             imask.imask_geometry_view_groups(params, role, g)
+
+
+def test_null_handles_are_refused_without_device(imask):
+    # calls on a missing state, plan or batch return INVALID (1) and never
+    # touch the device
+    lib = imask.lib()
+    buf = ctypes.create_string_buffer(64)
+    assert lib.imask_state_checkpoint_bytes(None) == -1
+    assert lib.imask_state_iteration(None) == -1
+    assert lib.imask_state_save(None, ctypes.cast(buf, ctypes.c_void_p), None) == 1
+    assert lib.imask_state_load(None, ctypes.cast(buf, ctypes.c_void_p), None) == 1
+    assert lib.imask_step(None, 1, None) == 1
+    assert lib.imask_state_get(None, 0, ctypes.cast(buf, ctypes.c_void_p), None) == 1
+    assert lib.imask_batch_step(None, 1, None) == 1
+    assert lib.imask_state_destroy(None) == 0     # destroying nothing is fine
+    assert lib.imask_plan_destroy(None) == 0
+    assert lib.imask_last_error()                  # the message of the last failure
