@@ -169,6 +169,75 @@ def oracle_sample(p: inputs.Problem, params: dict, b: np.ndarray, seed: int, ite
     return dt, float(samples_per_iteration(p, lv).sum())
 
 
+def cpu_description() -> dict:
+    """Host core count and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count() or 1, "cpu_model": model or platform.machine()}
+
+
+def _oracle_worker(job):
+    """One oracle process's share: `iters` iterations from seed `seed`;
+    returns (seconds, level stream)."""
+    params, b, seed, iters = job
+    from oracle import Oracle
+    o = Oracle(**params)
+    t0 = time.perf_counter()
+    _, lv = o.run(b, seed, iters)
+    return time.perf_counter() - t0, np.asarray(lv)
+
+
+class OraclePool:
+    """Independent, unmodified oracle processes, one per host core (spawned,
+    so that no CUDA state is inherited), each running its own seed: the
+    oracle on all host cores without changing it."""
+
+    def __init__(self, cores: int):
+        import multiprocessing as mp
+        self.cores = max(1, int(cores))
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        os.environ["OMP_NUM_THREADS"] = "1"
+        os.environ["OPENBLAS_NUM_THREADS"] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(self.cores)
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, p: inputs.Problem, params: dict, b: np.ndarray, seed0: int, iters: int):
+        """All cores at once, `iters` iterations each; returns (wall seconds,
+        total ray-samples)."""
+        jobs = [(params, b, seed0 + k, iters) for k in range(self.cores)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_worker, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        return wall, float(sum(samples_per_iteration(p, lv).sum() for _, lv in res))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(False)
     if rank != 0:
@@ -179,13 +248,18 @@ def run_reference(args):
     # derives for this workload (its cost per iteration does not depend on them)
     params = dict(p.params(), mu=args.mu, sigma=args.sigma)
     per_solve = expected_samples_per_solve(p)
-    for w in range(args.warmup):
-        oracle_sample(p, params, b.ravel(), 1000 + w, args.ref_iters)
-    times, samples = [], []
-    for k in range(args.steps):
-        dt, sm = oracle_sample(p, params, b.ravel(), k, args.ref_iters)
-        times.append(dt)
-        samples.append(sm)
+    host = cpu_description()
+    pool = OraclePool(host["nproc"])
+    try:
+        for w in range(args.warmup):
+            pool.run(p, params, b.ravel(), 1000 + 100 * w, args.ref_iters)
+        times, samples = [], []
+        for k in range(args.steps):
+            dt, sm = pool.run(p, params, b.ravel(), 100 * k, args.ref_iters)
+            times.append(dt)
+            samples.append(sm)
+    finally:
+        pool.close()
     T, S = sum(times), sum(samples)
     gs = S / T / 1e9
     solves = S / per_solve / T
@@ -196,10 +270,13 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
         "gsamples_per_s": gs,
-        "cpu_baseline": {"value": solves, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.ref_iters} oracle iterations per step of the "
-                                   f"fan512 solve, extrapolated by ray-samples to a "
-                                   f"{ITERS}-iteration solve"},
+        "cpu_baseline": {"value": solves, "unit": "solves/s", "cores": pool.cores,
+                         "kind": "oracle", "cpu_model": host["cpu_model"],
+                         "nproc": host["nproc"],
+                         "sample": f"per step, {pool.cores} independent oracle processes (one "
+                                   f"per host core, seeds differ), {args.ref_iters} iterations "
+                                   f"of the fan512 solve each, wall time of the step; "
+                                   f"extrapolated by ray-samples to {ITERS}-iteration solves"},
         "e2e": {"value": solves, "unit": "solves/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -212,11 +289,119 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------
 KINDS = ["forward projector (k_fp)", "back-projector (k_bp)", "primal update (k_update)"]
 KNAMES = ["k_fp", "k_bp", "k_update"]
-# algorithmic work per (ray, line) sample: FP32 flops and shared-memory bytes
+# algorithmic work per (ray, line) sample: FP32 flops, and the shared-memory
+# bytes of the method (two 4-byte pixel accesses: the projector's two loads,
+# the back-projector's two accumulations)
 FLOPS_PER_SAMPLE = {0: 6.0, 1: 7.0}          # q FMA 2, f 1, lerp 3 | q 2, f 1, weights 2, adds 2
-SMEM_BYTES_PER_SAMPLE = {0: 8.0, 1: 17.0}    # two pixel loads | two accumulator RMWs + 1/16 entry
-N_SM, MAX_CLK = 152, 2.07e9
-SMEM_PEAK_GBS = N_SM * 128 * MAX_CLK / 1e9    # 128 B per clock per SM
+SMEM_BYTES_PER_SAMPLE = 8.0
+
+
+def device_units(torch=None, clocks=None) -> dict:
+    """SM count of the current device and its maximum SM clock (from the clock
+    record of the run, else the driver's measurement file, else 2070 MHz)."""
+    n_sm = None
+    if torch is not None:
+        try:
+            n_sm = int(torch.cuda.get_device_properties(torch.cuda.current_device())
+                       .multi_processor_count)
+        except Exception:
+            n_sm = None
+    mhz = (clocks or {}).get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or 2070.0
+    return {"n_sm": n_sm or 152, "max_mhz": float(mhz)}
+
+
+def algorithmic_dram_bytes(p: inputs.Problem, kind: int, lvl: int) -> float:
+    """Bytes a launch must move at least (each input read once, each output
+    written once), fp32: projector with its dual epilogue: the sketch image and
+    y in, b, psi_l in / out, psi_mean in / out, y out (7 m); back-projector: y
+    in, the level image out; update: the back-projector's image, x, phi_mean
+    and the level's table in / out, and the next level's sketch in its two
+    layouts (expected over the level draw)."""
+    nl = p.n >> lvl
+    d, m = p.n * p.n, p.m
+    pr = np.full(p.levels, 1.0 / p.levels) if p.probs is None else np.asarray(p.probs)
+    if kind == 0:
+        return 4.0 * (nl * nl + 7 * m)
+    if kind == 1:
+        return 4.0 * (m + nl * nl)
+    nxt = 2.0 * sum(pr[l] * (p.n >> l) ** 2 for l in range(p.levels))
+    table = 2.0 * d if lvl == 0 else 2.0 * nl * nl
+    return 4.0 * (nl * nl + 4 * d + table + nxt)
+
+
+def roofline_report(p, prof_ms, prof_cnt, dev, period=1, smem_probe=None, l2_gbs=None,
+                    hbm_gbs=None):
+    """Dominant (kernel, level) by total event time.  The projectors bind on
+    the on-chip shared-memory pipe (Sec. 4.1 workload: hundreds of millions of
+    samples against tens of MB of state): achieved = samples x 8 B per launch
+    / average launch time against the measured shared-memory load ceiling.
+    The FP32-ALU view is kept beside it, and every (kernel, level) is also
+    put against the measured L2 copy and HBM bandwidth on its algorithmic
+    DRAM bytes (the memory view, where the fused epilogues and the coarse
+    levels are judged)."""
+    best = int(np.argmax(prof_ms))
+    kind, lvl = best // 8, best % 8
+    cnt = max(1, prof_cnt[best])
+    avg_s = prof_ms[best] / cnt / 1e3
+    nl = p.n >> lvl
+    samples_launch = p.m * nl
+    n_sm, clk = dev["n_sm"], dev["max_mhz"] * 1e6
+    smem_derived = n_sm * 128 * clk / 1e9
+    alu_peak = n_sm * 128 * 2 * clk / 1e12
+    alg_dram = algorithmic_dram_bytes(p, kind, lvl)
+    traffic = _dram_traffic(KNAMES[kind], lvl)
+    rep = {"kernel": f"{KINDS[kind]} at level {lvl} ({nl}x{nl} grid)",
+           "avg_launch_us": avg_s * 1e6, "launches": int(prof_cnt[best]),
+           "timed_launches": f"CUDA events around the launches of every {period}-th iteration "
+                             f"inside the timed region",
+           "gsamples_per_s": samples_launch / avg_s / 1e9,
+           "traffic": traffic, "algorithmic_dram_bytes": alg_dram,
+           "traffic_over_algorithmic": (traffic / alg_dram) if traffic else None,
+           "device": {"n_sm": n_sm, "max_sm_mhz": dev["max_mhz"]}}
+    if kind in FLOPS_PER_SAMPLE:
+        ach = samples_launch * SMEM_BYTES_PER_SAMPLE / avg_s / 1e9
+        if smem_probe is not None:
+            peak, src = float(smem_probe[0]), ("measured here: conflict-free 32-bit shared-memory "
+                                                "loads on every SM (imask_probe_smem)")
+        else:
+            peak, src = smem_derived, f"derived: {n_sm} SMs x 128 B x {dev['max_mhz']:.0f} MHz"
+        flops = samples_launch * FLOPS_PER_SAMPLE[kind] / avg_s / 1e12
+        rep.update(bound="smem", unit="GB/s", achieved=ach, peak=peak, peak_source=src,
+                   frac=ach / peak,
+                   algorithmic={"samples_per_launch": samples_launch,
+                                "smem_bytes_per_sample": SMEM_BYTES_PER_SAMPLE,
+                                "flops_per_sample": FLOPS_PER_SAMPLE[kind]},
+                   smem_derived_peak_gbs=smem_derived,
+                   alu_view={"achieved_tflops": flops, "peak_tflops": alu_peak,
+                             "peak_source": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x "
+                                            f"{dev['max_mhz']:.0f} MHz",
+                             "frac": flops / alu_peak})
+    else:
+        ach = alg_dram / avg_s / 1e9
+        peak = l2_gbs or hbm_gbs
+        rep.update(bound="hbm", unit="GB/s", achieved=ach, peak=peak,
+                   peak_source="measured L2 copy" if l2_gbs else "measured HBM copy",
+                   frac=(ach / peak) if peak else None)
+    views = []
+    for k in range(24):
+        if prof_cnt[k] <= 0:
+            continue
+        kd, lv = k // 8, k % 8
+        a_s = prof_ms[k] / prof_cnt[k] / 1e3
+        by = algorithmic_dram_bytes(p, kd, lv)
+        gbs = by / a_s / 1e9
+        views.append({"kernel": KNAMES[kd], "level": lv, "avg_us": round(a_s * 1e6, 2),
+                      "algorithmic_bytes": by, "achieved_gbs": gbs,
+                      "frac_of_l2_copy": (gbs / l2_gbs) if l2_gbs else None,
+                      "frac_of_hbm": (gbs / hbm_gbs) if hbm_gbs else None})
+    rep["memory_view"] = {"l2_copy_gbs": l2_gbs, "hbm_gbs": hbm_gbs, "launches": views}
+    total = max(1e-12, float(sum(prof_ms)))
+    rep["time_share"] = {f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / total, 4)
+                         for k in range(24) if prof_cnt[k] > 0}
+    rep["avg_launch_us_by_level"] = {
+        f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / prof_cnt[k] * 1e3, 1)
+        for k in range(24) if prof_cnt[k] > 0}
+    return rep
 
 
 def _kernels_sha() -> str:
@@ -266,52 +451,6 @@ def l2_copy_gbs(torch, stream, mib: int = 32, reps: int = 20) -> float:
             e1.synchronize()
             best = max(best, 2.0 * a.numel() * 4 * reps / (e0.elapsed_time(e1) / 1e3) / 1e9)
     return best
-
-
-def roofline_report(p, prof_ms, prof_cnt, alu_peak_tflops, period=1, smem_probe=None):
-    """Dominant (kernel, level) by total event time; its average launch against
-    the FP32 CUDA-core peak (bound "alu": the projectors are limited by issue
-    slots and the shared-memory pipe, not by DRAM), plus the shared-memory
-    bandwidth view of the same launches."""
-    best = int(np.argmax(prof_ms))
-    kind, lvl = best // 8, best % 8
-    cnt = max(1, prof_cnt[best])
-    avg_s = prof_ms[best] / cnt / 1e3
-    nl = p.n >> lvl
-    samples_launch = p.m * nl
-    rep = {"kernel": f"{KINDS[kind]} at level {lvl} ({nl}x{nl} grid)", "bound": "alu",
-           "unit": "TFLOP/s", "peak": alu_peak_tflops,
-           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-           "avg_launch_us": avg_s * 1e6, "launches": int(prof_cnt[best]),
-           "timed_launches": f"CUDA events around the launches of every {period}-th iteration "
-                             f"inside the timed region",
-           "gsamples_per_s": samples_launch / avg_s / 1e9}
-    if kind in FLOPS_PER_SAMPLE:
-        ach = samples_launch * FLOPS_PER_SAMPLE[kind] / avg_s / 1e12
-        smem = samples_launch * SMEM_BYTES_PER_SAMPLE[kind] / avg_s / 1e9
-        rep.update(achieved=ach, frac=ach / alu_peak_tflops,
-                   traffic=_dram_traffic(KNAMES[kind], lvl),
-                   algorithmic={"samples_per_launch": samples_launch,
-                                "flops_per_sample": FLOPS_PER_SAMPLE[kind],
-                                "smem_bytes_per_sample": SMEM_BYTES_PER_SAMPLE[kind]},
-                   smem={"achieved_gbs": smem, "peak_gbs": SMEM_PEAK_GBS,
-                         "peak_source": "derived: 152 SMs x 128 B x 2070 MHz",
-                         "frac": smem / SMEM_PEAK_GBS})
-        if smem_probe is not None:
-            # measured ceiling of the access pattern: loads (projector) or
-            # private read-modify-writes (back-projector)
-            ceil_gbs = smem_probe[1] if kind == 1 else smem_probe[0]
-            rep["smem"].update(measured_peak_gbs=ceil_gbs, measured_frac=smem / ceil_gbs,
-                               measured_pattern="read-modify-write" if kind == 1 else "load")
-    else:
-        rep.update(achieved=None, frac=None, traffic=None)
-    total = max(1e-12, float(sum(prof_ms)))
-    rep["time_share"] = {f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / total, 4)
-                         for k in range(24) if prof_cnt[k] > 0}
-    rep["avg_launch_us_by_level"] = {
-        f"{KINDS[k // 8].split(' (')[0]} l{k % 8}": round(prof_ms[k] / prof_cnt[k] * 1e3, 1)
-        for k in range(24) if prof_cnt[k] > 0}
-    return rep
 
 
 # ---------------------------------------------------------------------------------
@@ -891,15 +1030,16 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (kind, level) ----
     smem_probe = imask.imask_probe_smem()
-    roofline = roofline_report(p, prof_ms, prof_cnt, args.alu_peak_tflops,
-                               args.profile_period, smem_probe)
+    hbm = measured_peaks().get("hbm_gbs")
+    l2 = l2_copy_gbs(torch, stream)
+    dev = device_units(torch, clk)
+    roofline = roofline_report(p, prof_ms, prof_cnt, dev, args.profile_period, smem_probe,
+                               l2_gbs=l2, hbm_gbs=hbm)
     # the fused epilogues' algorithmic traffic (7 m + 5 d floats per
     # iteration: y in/out, b, psi_l in/out, psi_mean in/out; x, phi_0 in/out,
     # phi_mean in/out) against the measured HBM copy bandwidth
     bytes_it = 4.0 * (7 * p.m + 5 * p.d)
     mem_gbs = bytes_it * args.iters * args.steps / T_max / 1e9
-    hbm = measured_peaks().get("hbm_gbs")
-    l2 = l2_copy_gbs(torch, stream)
     memory = {"algorithmic_bytes_per_iteration": bytes_it, "achieved_gbs": mem_gbs,
               "hbm_peak_gbs": hbm, "frac_of_hbm": (mem_gbs / hbm) if hbm else None,
               "l2_copy_gbs": l2, "frac_of_l2_copy": mem_gbs / l2,
@@ -928,11 +1068,26 @@ def run_ours(args):
         oracle_err = {"iters": args.cpu_iters, "seed": 0,
                       "rel_l2": float(np.linalg.norm(xg - x_orc) / np.linalg.norm(x_orc))}
         per_solve = expected_samples_per_solve(p)
-        cpu = {"value": sm / per_solve / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-               "sample": f"{args.cpu_iters} FP64 oracle iterations of the fan512 solve "
-                         f"({sm / 1e9:.2f} G ray-samples in {dt:.1f} s), extrapolated by "
-                         f"ray-samples to a {ITERS}-iteration solve",
-               "gsamples_per_s": sm / dt / 1e9}
+        single = {"value": sm / per_solve / dt, "unit": "solves/s", "cores": 1,
+                  "gsamples_per_s": sm / dt / 1e9,
+                  "sample": f"{args.cpu_iters} FP64 oracle iterations of the fan512 solve "
+                            f"({sm / 1e9:.2f} G ray-samples in {dt:.1f} s)"}
+        # all host cores: one unmodified oracle process per core, own seeds
+        host = cpu_description()
+        pool = OraclePool(host["nproc"])
+        try:
+            pool.run(p, params, b.ravel(), 500, 1)          # process start-up and imports
+            wall, sm_all = pool.run(p, params, b.ravel(), 600, args.cpu_iters)
+        finally:
+            pool.close()
+        cpu = {"value": sm_all / per_solve / wall, "unit": "solves/s", "cores": pool.cores,
+               "kind": "oracle", "nproc": host["nproc"], "cpu_model": host["cpu_model"],
+               "sample": f"{pool.cores} independent FP64 oracle processes (one per host core, "
+                         f"seeds differ), {args.cpu_iters} iterations of the fan512 solve each "
+                         f"({sm_all / 1e9:.2f} G ray-samples in {wall:.1f} s of wall time), "
+                         f"extrapolated by ray-samples to {ITERS}-iteration solves",
+               "gsamples_per_s": sm_all / wall / 1e9,
+               "single_thread": single}
 
     if rank == 0:
         line = {
@@ -1007,8 +1162,6 @@ def main():
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--sigma", type=float, default=0.0)
-    # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2.07 GHz
-    ap.add_argument("--alu-peak-tflops", type=float, default=152 * 128 * 2 * 2.07e9 / 1e12)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

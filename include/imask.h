@@ -199,7 +199,9 @@ imask_status imask_backproject(imask_plan_t plan, int32_t level, const float *y_
  * exits); a plan whose scratch need exceeds it gets IMASK_ERR_SHAPE.  The
  * first call on each device looks up that array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * All calls share the array and it keeps the last call's contents: calls
+ * The address is kept per device and CUDA context: after a cudaDeviceReset
+ * (which also invalidates every plan) the first call in the new context
+ * looks it up again.  All calls share the array and it keeps the last call's contents: calls
  * that may overlap on the GPU (other streams, other host threads) race and
  * must be serialised by the caller. */
 imask_status imask_backproject_noalloc(imask_plan_t plan, int32_t level, const float *y_dev,
@@ -217,7 +219,10 @@ imask_status imask_levels(imask_plan_t plan, uint64_t seed, int64_t k0, int64_t 
 imask_status imask_state_create(imask_plan_t plan, const float *b_dev, uint64_t seed,
                                 imask_state_t *state_out, void *stream);
 /* Advances the state by n_iters iterations (Alg. 1, or the plan's variant) on
- * stream.  For Alg. 1 the state's own two side streams run the projector and
+ * stream.  Every call that takes a state and a stream (step, batch step, get,
+ * save, load, set_storage) is ordered after the state's previous call even
+ * when that one used another stream (an event joins the two), unless either
+ * stream is being captured into a graph.  For Alg. 1 the state's own two side streams run the projector and
  * the back-projector concurrently with each other and with the previous
  * update, ordered by events as the data require; all work is joined into
  * `stream` before the call's last iteration ends, so later work on `stream`
@@ -259,14 +264,17 @@ imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
  * running means, sketch images, b, the iteration counter, the seeds and the
  * dual ping-pong parity) into dst_dev, a device buffer of
  * imask_state_checkpoint_bytes(state) bytes, ordered after the state's work
- * and on stream.  imask_state_load restores such a checkpoint into a state of
- * the same plan, or of a plan built from the same descriptor on the same kind
- * of device (with autotune, its split counts must match too: the block holds
- * the back-projector's partial images); it synchronises stream and the
- * state's stream.  Stepping then continues exactly as the saved state would
- * have, the level streams being counter-based.  INVALID for a checkpoint of another
- * plan or storage format, or for a state whose tables changed storage
- * (imask_state_set_storage). */
+ * and on stream; the state's later calls, on any stream, come after the
+ * copy.  The header carries a fingerprint of the saving state's plan: the
+ * descriptor, the derived mu, sigma and theta, and every level's
+ * back-projector split and partial-image size.  imask_state_load restores
+ * such a checkpoint into a state of the same plan, or of a plan with the same
+ * fingerprint (built from the same descriptor on the same kind of device,
+ * with the same autotuned splits); it synchronises stream and the state's
+ * stream.  Stepping then continues exactly as the saved state would have, the
+ * level streams being counter-based.  INVALID for a checkpoint of a plan with
+ * another fingerprint or storage format, or for a state whose tables changed
+ * storage (imask_state_set_storage). */
 int64_t imask_state_checkpoint_bytes(imask_state_t state);
 imask_status imask_state_save(imask_state_t state, void *dst_dev, void *stream);
 imask_status imask_state_load(imask_state_t state, const void *src_dev, void *stream);

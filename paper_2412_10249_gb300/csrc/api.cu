@@ -6,6 +6,7 @@
 // on the device (FP32 operators, FP64 reductions) before solving Thm. 3 on the
 // host.  States hold one solve of Alg. 1; imask_step launches the three
 // kernels of every iteration (see kernels.cu).
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 #include <math.h>
@@ -136,6 +137,10 @@ struct imask_plan_s {
   int n_split_views = 0;
   double mu = 0, sigma = 0, theta = 0, L = 0, Lbar = 0, Lbar_p = 0, norm_K = 0;
   bool autotuned = false;
+  // hash of everything that decides how a state's block is laid out and read
+  // (descriptor, derived step size, per-level back-projector splits); a
+  // checkpoint loads only into a state of a plan with the same value
+  uint64_t fingerprint = 0;
 };
 
 struct imask_state_s {
@@ -172,6 +177,7 @@ struct imask_state_s {
   bool k_dev_stale = true;      // k advanced by eager launches since the last sync
   struct imask_batch_s *self_batch = nullptr;   // graph replays of this state alone
   int gen = 0;                  // bumped when buffers move; captured graphs go stale
+  cudaEvent_t ev_order = nullptr;   // orders a call on a new stream after the last one
 };
 
 struct imask_batch_s {
@@ -880,6 +886,59 @@ std::vector<int> bp_tile_order(const DevPlan &dp, const std::vector<ViewInfo> &v
 
 }  // namespace
 
+namespace {
+
+// FNV-1a (64-bit) over the bytes of the values that fix a state's layout and
+// meaning: the descriptor's scalars, the level probabilities, the derived mu,
+// sigma and theta, and every level's back-projector split and the size of its
+// partial-image buffer.
+struct Fnv64 {
+  uint64_t h = 0xcbf29ce484222325ull;
+  void bytes(const void *p, size_t n) {
+    const unsigned char *c = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 0x100000001b3ull;
+  }
+  template <class T> void add(const T &v) { bytes(&v, sizeof(T)); }
+};
+
+uint64_t plan_fingerprint(const imask_plan_s *p) {
+  const imask_desc &d = p->desc;
+  Fnv64 f;
+  f.add(d.n); f.add(d.n_angles); f.add(d.n_det); f.add(d.geometry);
+  f.add(d.fov); f.add(d.det_spacing); f.add(d.angle_start); f.add(d.angle_span);
+  f.add(d.src_dist); f.add(d.det_dist); f.add(d.levels);
+  f.add(d.reg); f.add(d.tv_lambda); f.add(d.tv_eps); f.add(d.tv_inner);
+  f.add(d.storage); f.add(d.variant); f.add(d.dual_tables); f.add(d.draws); f.add(d.step_rule);
+  for (double v : p->probs) f.add(v);
+  f.add(p->mu); f.add(p->sigma); f.add(p->theta);
+  for (int li = 0; li <= d.levels; ++li) f.add(p->dp.lg[li].bp_vgo);
+  f.add((uint64_t)p->gcap);
+  return f.h;
+}
+
+// Orders the work that a call is about to enqueue on st after the state's
+// earlier work, which ran on s->stream (the stream of its last call), when
+// the two differ; the state then belongs to st.  Skipped while either stream
+// is being captured into a graph (the capture's own dependencies order it).
+imask_status state_use_stream(imask_state_s *s, cudaStream_t st) {
+  if (s->stream == st) return IMASK_OK;
+  cudaStreamCaptureStatus c0 = cudaStreamCaptureStatusNone, c1 = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &c0) == cudaSuccess &&
+      cudaStreamIsCapturing(s->stream, &c1) == cudaSuccess &&
+      c0 == cudaStreamCaptureStatusNone && c1 == cudaStreamCaptureStatusNone) {
+    if (!s->ev_order)
+      CK(cudaEventCreateWithFlags(&s->ev_order, cudaEventDisableTiming), "state order event");
+    CK(cudaEventRecord(s->ev_order, s->stream), "state order");
+    CK(cudaStreamWaitEvent(st, s->ev_order, 0), "state order");
+  } else {
+    cudaGetLastError();   // a failed query leaves no sticky error behind
+  }
+  s->stream = st;
+  return IMASK_OK;
+}
+
+}  // namespace
+
 // ===================================================================================
 // C ABI
 // ===================================================================================
@@ -1201,6 +1260,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
     imask_plan_destroy(p);
     return rc;
   }
+  p->fingerprint = plan_fingerprint(p);
   *plan_out = p;
   return IMASK_OK;
 }
@@ -1318,8 +1378,48 @@ imask_status imask_backproject(imask_plan_t p, int32_t level, const float *y_dev
 static __device__ __align__(256) float g_noalloc_scratch[IMASK_NOALLOC_FLOATS];
 
 namespace {
+// Device address of the array per device, looked up once per CUDA context
+// (a cudaDeviceReset ends the context; the module is loaded again, possibly
+// at another address, in the next one).  The context is identified through
+// the driver's cuCtxGetCurrent / cuCtxGetId, reached via the runtime.
 std::mutex g_noalloc_mu;
-float *g_noalloc_ptr[256] = {nullptr};   // device address of the array, per device
+struct NoallocAddr {
+  unsigned long long ctx_id = 0;
+  bool known = false;
+  float *ptr = nullptr;
+};
+NoallocAddr g_noalloc_addr[256];
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+bool g_ctx_fns_tried = false;
+
+// Identifier of the calling thread's current context; 0 if it cannot be read
+// (the address is then looked up on every call).
+unsigned long long current_ctx_id() {
+  if (!g_ctx_fns_tried) {
+    g_ctx_fns_tried = true;
+    void *f0 = nullptr, *f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) ==
+            cudaSuccess &&
+        q0 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess) {
+      g_ctx_get_current = (CtxGetCurrentFn)f0;
+      g_ctx_get_id = (CtxGetIdFn)f1;
+    }
+    cudaGetLastError();
+  }
+  if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx || g_ctx_get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 }  // namespace
 
 imask_status imask_backproject_noalloc(imask_plan_t p, int32_t level, const float *y_dev,
@@ -1337,16 +1437,21 @@ imask_status imask_backproject_noalloc(imask_plan_t p, int32_t level, const floa
   if (dev < 0 || dev >= 256) return fail(IMASK_ERR_INVALID, "device index %d out of range", dev);
   float *ptr = nullptr;
   {
-    // first call on this device: look up the array's device address (in host
-    // code the array's name is only a host-side stand-in)
+    // first call on this device (in this context): look up the array's
+    // device address (in host code the array's name is only a host-side
+    // stand-in)
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    const unsigned long long ctx = current_ctx_id();
+    NoallocAddr &a = g_noalloc_addr[dev];
+    if (!a.known || ctx == 0 || a.ctx_id != ctx) {
       void *addr = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
-      g_noalloc_ptr[dev] = (float *)addr;
+      a.ptr = (float *)addr;
+      a.ctx_id = ctx;
+      a.known = true;
     }
-    ptr = g_noalloc_ptr[dev];
+    ptr = a.ptr;
   }
   // every scratch element read below is written earlier in the same call,
   // so nothing is cleared
@@ -1639,7 +1744,8 @@ imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
   if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
   if (n_iters < 0) return fail(IMASK_ERR_INVALID, "n_iters < 0");
   cudaStream_t st = (cudaStream_t)stream;
-  s->stream = st;
+  imask_status rc0 = state_use_stream(s, st);
+  if (rc0 != IMASK_OK) return rc0;
   // Runs of several iterations replay a captured two-iteration graph (same
   // kernels, fewer launch gaps).  With kernel profiling every period-th
   // iteration is launched on its own so that its events are recorded, and the
@@ -1732,6 +1838,10 @@ imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   const int unroll = kGraphUnroll;
   const int replays = n_iters / unroll;
+  for (auto *s : b->states) {
+    imask_status rc = state_use_stream(s, st);
+    if (rc != IMASK_OK) return rc;
+  }
   if (replays > 0) {
     // bring the device counters up to date with eager steps taken meanwhile
     for (auto *s : b->states)
@@ -1790,6 +1900,8 @@ imask_status imask_state_get(imask_state_t s, int32_t what, float *dst, void *st
     case 3: src = s->psi_mean; n = p->dp.m; break;
     default: return fail(IMASK_ERR_INVALID, "unknown state part %d", what);
   }
+  imask_status rc = state_use_stream(s, (cudaStream_t)stream);
+  if (rc != IMASK_OK) return rc;
   CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
      "copy state");
   return IMASK_OK;
@@ -1809,7 +1921,8 @@ struct CheckpointHeader {
   uint64_t seed, seed_x;   // level streams
   int32_t cur;             // dual ping-pong parity
   int32_t psi_fmt;         // storage format of the tables
-  uint64_t reserved[2];
+  uint64_t plan_fp;        // fingerprint of the saving state's plan
+  uint64_t reserved;
 };
 constexpr uint64_t kCheckpointMagic = 0x31504b43534b4d49ull;   // "IMSKCKP1"
 
@@ -1835,15 +1948,12 @@ imask_status imask_state_save(imask_state_t s, void *dst, void *stream) {
   h.seed_x = s->seed_x;
   h.cur = s->cur;
   h.psi_fmt = s->psi_fmt;
-  // the state's side streams are joined into its stream after every step
-  if (s->stream != st) {
-    cudaEvent_t ev = nullptr;
-    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "checkpoint order");
-    cudaError_t e = cudaEventRecord(ev, s->stream);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
-    cudaEventDestroy(ev);
-    if (e != cudaSuccess) return cuda_fail(e, "checkpoint order");
-  }
+  h.plan_fp = s->plan->fingerprint;
+  // the copy comes after the state's earlier work (its side streams are joined
+  // into its stream after every step), and the state's later calls, on any
+  // stream, come after the copy: the state now belongs to st
+  imask_status rc = state_use_stream(s, st);
+  if (rc != IMASK_OK) return rc;
   CK(cudaMemcpyAsync(dst, &h, sizeof(h), cudaMemcpyHostToDevice, st), "checkpoint header");
   CK(cudaMemcpyAsync((char *)dst + sizeof(h), s->block, h.block_floats * sizeof(float),
                      cudaMemcpyDeviceToDevice, st),
@@ -1862,6 +1972,10 @@ imask_status imask_state_load(imask_state_t s, const void *src, void *stream) {
   if (h.magic != kCheckpointMagic) return fail(IMASK_ERR_INVALID, "not a state checkpoint");
   if (h.block_floats != state_block_floats(s) || h.psi_fmt != s->psi_fmt)
     return fail(IMASK_ERR_INVALID, "checkpoint of a state of another plan or storage");
+  if (h.plan_fp != s->plan->fingerprint)
+    return fail(IMASK_ERR_INVALID,
+                "checkpoint of a state of another plan (descriptor, step size or "
+                "back-projector splits differ)");
   // the state's own pending work comes first
   CK(cudaStreamSynchronize(s->stream), "checkpoint order");
   CK(cudaMemcpyAsync(s->block, (const char *)src + sizeof(h), h.block_floats * sizeof(float),
@@ -1886,6 +2000,8 @@ imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *str
     return IMASK_OK;
   }
   cudaStream_t st = (cudaStream_t)stream;
+  imask_status rc = state_use_stream(s, st);
+  if (rc != IMASK_OK) return rc;
   const imask_plan_s *p = s->plan;
   const long long n = (long long)p->dp.m * p->desc.levels;
   void *mem = nullptr;
@@ -1918,7 +2034,8 @@ imask_status imask_state_destroy(imask_state_t s) {
   // step, so the frees below, ordered on s->stream, come after it
   if (s->aux) cudaStreamDestroy(s->aux);
   if (s->aux2) cudaStreamDestroy(s->aux2);
-  for (cudaEvent_t ev : {s->ev_fork, s->ev_fp, s->ev_start, s->ev_bp, s->ev_upd[0], s->ev_upd[1]})
+  for (cudaEvent_t ev : {s->ev_fork, s->ev_fp, s->ev_start, s->ev_bp, s->ev_upd[0], s->ev_upd[1],
+                        s->ev_order})
     if (ev) cudaEventDestroy(ev);
   if (s->psi_block) cudaFreeAsync(s->psi_block, s->stream);
   if (s->block) cudaFreeAsync(s->block, s->stream);

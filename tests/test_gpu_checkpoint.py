@@ -77,3 +77,42 @@ def test_foreign_or_corrupt_checkpoints_are_refused(imask):
     assert c.k == 0
     for s in (a, s2, c):
         s.close()
+
+
+def test_save_on_a_side_stream_then_step_at_once(imask):
+    """A save enqueued on a second stream is ordered before the state's next
+    step on the first: the checkpoint is the state at the save, not a torn mix
+    of it and the later iterations."""
+    plan, b = _setup(imask, n=128)
+    a = plan.state(b, 11)
+    a.step(10)
+    side = torch.cuda.Stream()
+    ck = a.save(stream=side)
+    a.step(40)                      # on the current stream, enqueued at once
+    c = plan.state(torch.zeros_like(b), 12)
+    c.load(ck)
+    assert c.k == 10
+    c.step(40)
+    torch.cuda.synchronize()
+    assert torch.equal(a.get(a.X), c.get(c.X))
+    assert torch.equal(a.get(a.Y), c.get(c.Y))
+    for s in (a, c):
+        s.close()
+
+
+def test_checkpoint_of_a_plan_of_the_same_size_is_refused(imask):
+    """Two plans whose states have the same size but another mu (hence another
+    step size): the plan fingerprint in the header refuses the load."""
+    plan, b = _setup(imask)
+    a = plan.state(b, 1)
+    a.step(5)
+    ck = a.save()
+    p = inputs.Problem(n=64, n_angles=90, n_det=96, geometry=1, angle_span=2 * math.pi, levels=3)
+    other = imask.Plan(dict(p.params(), mu=0.31, sigma=0.03))
+    s2 = other.state(b, 1)
+    assert int(imask.lib().imask_state_checkpoint_bytes(s2.handle)) == ck.numel()
+    with pytest.raises(imask.ImaskError):
+        s2.load(ck)
+    assert s2.k == 0
+    for s in (a, s2):
+        s.close()
