@@ -691,35 +691,48 @@ def run_batch(args):
             plans[(p.n, p.n_angles)].solve(bs[i], i, args.iters, out=xs_plain[i], stream=stream)
         e[1].record(stream)
     torch.cuda.synchronize()
-    states = [plans[(p.n, p.n_angles)].state(bs[i], i, stream=stream)
-              for i, p in enumerate(probs)]
-    batch = imask.Batch(states)
-    torch.cuda.synchronize()
-    launches0 = imask.imask_launch_count()
-    with torch.cuda.stream(stream):
-        e[2].record(stream)
-        batch.step(args.iters, stream=stream)
-        e[3].record(stream)
-    torch.cuda.synchronize()
-    launches = imask.imask_launch_count() - launches0
+    forms = {}
+    for name, fused in (("batched", False), ("fused", True)):
+        states = [plans[(p.n, p.n_angles)].state(bs[i], i, stream=stream)
+                  for i, p in enumerate(probs)]
+        batch = imask.Batch(states, fused=fused)
+        torch.cuda.synchronize()
+        launches0 = imask.imask_launch_count()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            batch.step(args.iters, stream=stream)
+            z.record(stream)
+        torch.cuda.synchronize()
+        launches = imask.imask_launch_count() - launches0
+        t = a.elapsed_time(z) / 1e3
+        worst, identical = 0.0, True
+        for i, s in enumerate(states):
+            xi = s.get(s.X)
+            torch.cuda.synchronize()
+            worst = max(worst, imask.imask_rel_distance(xi, xs_plain[i]))
+            identical = identical and bool(torch.equal(xi, xs_plain[i]))
+        batch.close()
+        for s in states:
+            s.close()
+        forms[name] = {"value": len(probs) / t, "seconds": t,
+                       "gsamples_per_s": samples / t / 1e9,
+                       "includes": "graph capture and instantiation in the first call",
+                       "gpu_launches": int(launches),
+                       "max_rel_dist_sq_vs_plain": worst,
+                       "bit_identical_to_plain": identical}
     clk = clocks.stop()
     t_plain = e[0].elapsed_time(e[1]) / 1e3
-    t_batch = e[2].elapsed_time(e[3]) / 1e3
-    worst = 0.0
-    for i, s in enumerate(states):
-        worst = max(worst, imask.imask_rel_distance(s.get(s.X), xs_plain[i]))
-    batch.close()
+    oracle_err = batch_oracle_check(imask, plans, probs, sinos, args.cpu_iters)
     n = len(probs)
     line = {"metric": "batched ImaSk solves/s (mixed slice sizes)", "unit": "solves/s",
             "slices": n, "iters_per_solve": args.iters, "sigma": sigma,
             "plain": {"value": n / t_plain, "seconds": t_plain,
                       "gsamples_per_s": samples / t_plain / 1e9},
-            "batched": {"value": n / t_batch, "seconds": t_batch,
-                        "gsamples_per_s": samples / t_batch / 1e9,
-                        "includes": "graph capture and instantiation in the first call",
-                        "gpu_launches": int(launches)},
-            "speedup": t_plain / t_batch,
-            "max_rel_dist_sq_batched_vs_plain": worst,
+            "batched": forms["batched"], "fused": forms["fused"],
+            "speedup": t_plain / forms["batched"]["seconds"],
+            "speedup_fused": t_plain / forms["fused"]["seconds"],
+            "rel_err_vs_fp64_oracle": oracle_err,
             "plan_setup_s": t_plans, "distinct_plans": len(plans),
             "clocks": clk,
             "config": {"workload": "mixed slices: side {256,384,512,768,1024}, views "
@@ -729,32 +742,69 @@ def run_batch(args):
     return 0
 
 
-def time_batch_fan512(imask, p, bt, info, iters, stream, n_states=8):
-    """n_states copies of the headline solve advanced as one batch."""
+def batch_oracle_check(imask, plans, probs, sinos, iters, n_check=3):
+    """The smallest n_check slices of a batch, advanced `iters` iterations as
+    one fused batch from their timed seeds, each against the FP64 oracle on
+    the same seed and iterations (relative L2 of x)."""
     import torch
-    plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
-    warm = [plan.state(bt, 900 + i, stream=stream) for i in range(n_states)]
-    wb = imask.Batch(warm)
-    wb.step(4, stream=stream)
+    from oracle import Oracle
+    idx = sorted(range(len(probs)), key=lambda i: (probs[i].n, probs[i].n_angles))[:n_check]
+    states = [plans[(probs[i].n, probs[i].n_angles)].state(
+        torch.as_tensor(sinos[i], device="cuda"), i) for i in idx]
+    batch = imask.Batch(states, fused=True)
+    batch.step(iters)
     torch.cuda.synchronize()
-    wb.close()
-    for w in warm:
-        w.close()
-    states = [plan.state(bt, 950 + i, stream=stream) for i in range(n_states)]
-    batch = imask.Batch(states)
-    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        a.record(stream)
-        batch.step(iters, stream=stream)
-        e.record(stream)
-    torch.cuda.synchronize()
-    t = a.elapsed_time(e) / 1e3
+    out = []
+    for i, s in zip(idx, states):
+        p = probs[i]
+        info = plans[(p.n, p.n_angles)].info
+        st, _ = Oracle(**dict(p.params(), mu=info["mu"], sigma=info["sigma"])).run(
+            np.asarray(sinos[i], dtype=np.float64), i, iters)
+        x = s.get(s.X).double().cpu().numpy()
+        out.append({"slice": i, "n": p.n, "views": p.n_angles, "iters": iters,
+                    "rel_l2": float(np.linalg.norm(x - st["x"]) / np.linalg.norm(st["x"]))})
     batch.close()
     for s in states:
         s.close()
+    return out
+
+
+def time_batch_fan512(imask, p, bt, info, iters, stream, n_states=8):
+    """n_states copies of the headline solve advanced as one batch, with one
+    graph branch per state and fused (one launch of each kernel per iteration
+    for all states); the first batched state's iterate is compared bit for bit
+    with a plain solve of the same seed."""
+    import torch
+    plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
+    out = {"states": n_states, "includes": "graph capture and instantiation"}
+    x_plain = plan.solve(bt, 950, iters, stream=stream)
+    for name, fused in (("branches", False), ("fused", True)):
+        warm = [plan.state(bt, 900 + i, stream=stream) for i in range(n_states)]
+        wb = imask.Batch(warm, fused=fused)
+        wb.step(4, stream=stream)
+        torch.cuda.synchronize()
+        wb.close()
+        for w in warm:
+            w.close()
+        states = [plan.state(bt, 950 + i, stream=stream) for i in range(n_states)]
+        batch = imask.Batch(states, fused=fused)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            batch.step(iters, stream=stream)
+            e.record(stream)
+        torch.cuda.synchronize()
+        t = a.elapsed_time(e) / 1e3
+        x0 = states[0].get(states[0].X, stream=stream)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(x0, x_plain))
+        batch.close()
+        for s in states:
+            s.close()
+        out[name] = {"solves_per_s": n_states / t, "seconds": t,
+                     "bit_identical_to_plain_solve": same}
     plan.close()
-    return {"states": n_states, "solves_per_s": n_states / t, "seconds": t,
-            "includes": "graph capture and instantiation"}
+    return out
 
 
 # ---------------------------------------------------------------------------------
@@ -1101,6 +1151,7 @@ def run_ours(args):
                        "iteration": vopts,
                        "mu": info["mu"], "sigma": info["sigma"], "theta": info["theta"],
                        "bp_view_groups": list(info["bp_view_groups"][:p.levels]),
+                       "fp_strip_lines": list(info["fp_strip_lines"][:p.levels]),
                        "l2": "flushed between steps (512 MB write outside the step events)",
                        "parallelism": f"replicas x{world}"},
             "gsamples_per_s": gs,

@@ -117,8 +117,9 @@ typedef struct {
   int32_t draws;                         /* 0 common level, 1 independent primal/dual */
   int32_t step_rule;                     /* sigma <= 0: 0 sigma*, 1 half, 2 sigma_B */
   int32_t power_iters;                   /* power-method iterations; 0 picks 100 */
-  int32_t autotune;                      /* 1: time the back-projector's view-group
-                                            split per level at plan time */
+  int32_t autotune;                      /* 1: time, per level at plan time, the
+                                            back-projector's view-group split and
+                                            the projector's strip height */
 } imask_desc;
 
 /* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,
@@ -131,8 +132,9 @@ typedef struct {
   int64_t n_xmajor_rays;
   int64_t state_bytes;                  /* device bytes one imask_state_create allocates */
   int64_t plan_bytes;                   /* device bytes the plan holds */
-  int32_t autotuned;                    /* 1 when the split below was measured */
+  int32_t autotuned;                    /* 1 when the choices below were measured */
   int32_t bp_view_groups[8];            /* back-projector view groups per level */
+  int32_t fp_strip_lines[8];            /* projector strip height (lines) per level */
 } imask_plan_info;
 
 /* Creates a plan: validates the descriptor, builds the per-ray geometry tables
@@ -252,6 +254,20 @@ imask_status imask_step(imask_state_t state, int32_t n_iters, void *stream);
  * Destroy a batch before its states.  Errors: INVALID, OOM, CUDA. */
 imask_status imask_batch_create(const imask_state_t *states, int32_t n_states,
                                 imask_batch_t *batch_out);
+/* A fused batch: the same results as imask_batch_create's (bit for bit: the
+ * same per-solve work in the same order), with one projector, one
+ * back-projector and one update launch per iteration for all n_states
+ * states, whose sizes, view counts and level sets may all differ.  The
+ * projector and update grids are the solves' own grids one after the other;
+ * the back-projector runs resident CTAs that take (solve, tile, view group)
+ * items from a device counter, the solves' items listed at the levels drawn
+ * for the iteration (a one-CTA planner launch writes the list), so that the
+ * coarse levels of some solves fill the GPU beside the fine levels of
+ * others.  Four iterations of these launches are captured as one CUDA graph
+ * and replayed, as for imask_batch_create.  The states must use the quadratic
+ * regulariser (reg = 0); at most 1024 states.  Errors: INVALID, OOM, CUDA. */
+imask_status imask_batch_create_fused(const imask_state_t *states, int32_t n_states,
+                                      imask_batch_t *batch_out);
 imask_status imask_batch_step(imask_batch_t batch, int32_t n_iters, void *stream);
 imask_status imask_batch_destroy(imask_batch_t batch);
 /* Iteration counter k of the state (host value, no synchronisation). */

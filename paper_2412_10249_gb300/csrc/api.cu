@@ -191,6 +191,20 @@ struct imask_batch_s {
   std::vector<int> gen_at_capture;     // state buffer generations it was captured with
   int unroll = 0;                      // iterations per replay (even)
   int64_t kernels_per_replay = 0;
+  // fused mode: one projector, one back-projector and one update launch per
+  // iteration for every state (see kernels.cu, k_fp_multi and friends)
+  bool fused = false;
+  std::vector<int> order;              // states by decreasing size (launch order)
+  FusedSlice *d_recs = nullptr;        // [unroll][n] iteration records
+  int *d_fp_start = nullptr;           // [n + 1] first projector CTA of each state
+  int *d_upd_start = nullptr;          // [n + 1] first update CTA of each state
+  int *d_bp_start = nullptr;           // [unroll][n + 1] back-projector item offsets
+  int *d_bp_counter = nullptr;         // [unroll] back-projector work counters
+  int fp_total = 0, upd_total = 0, upd_smem = 0, bp_grid = 0, nv_cap = 0;
+  long long bp_smem = 0;
+  bool any_seq = false;                // some state runs Alg. 7
+  cudaStream_t f_fp = nullptr, f_bp = nullptr;   // capture branches of the fused launches
+  std::vector<cudaEvent_t> f_ev;       // [3 * unroll]: projector, back-projector, update done
 };
 
 namespace {
@@ -617,6 +631,61 @@ imask_status autotune_bp(imask_plan_s *p, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------------
+// Plan-time autotuning of the projector's strip height: for every level the
+// bare projector K_ell is timed with CUDA events for every strip height (a
+// multiple of 4 lines) that fits a stage buffer, and the fastest is kept.  The
+// strip height changes only how the image streams through shared memory (and
+// how many zero lines pad the last strip), never a sample's value.
+// ---------------------------------------------------------------------------------
+imask_status autotune_fp(imask_plan_s *p, cudaStream_t st) {
+  DevPlan &dp = p->dp;
+  const int r = p->desc.levels;
+  float *sino = nullptr;
+  CK(cudaMallocAsync((void **)&sino, (size_t)dp.m * sizeof(float), st), "cudaMallocAsync(autotune)");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  imask_status rc = IMASK_OK;
+  for (int li = 1; li <= r && e == cudaSuccess && rc == IMASK_OK; ++li) {
+    LevelGeom &g = dp.lg[li];
+    const int tmax = std::min(32, std::max(4, (FP_STAGE_FLOATS / g.ls) & ~3));
+    const int t0 = g.tc;
+    float best_ms = 1e30f;
+    int best_t = t0;
+    for (int t = 4; t <= tmax && e == cudaSuccess && rc == IMASK_OK; t += 4) {
+      g.tc = t;
+      g.lines = (g.nl + t - 1) / t * t;
+      Scratch sc;
+      if ((rc = scratch_alloc(p, 1u << li, false, st, sc)) != IMASK_OK) break;
+      float ms = 0.0f, tot = 0.0f;
+      for (int rep = 0; rep < 4; ++rep) {
+        if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+        if ((e = launch_fp(dp, fixed_level(li - 1), sc.pads, sino, no_dual(), p->n_cta_x,
+                           p->n_cta_y, p->d_err, st)) != cudaSuccess)
+          break;
+        if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+        if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+        if (rep > 0) tot += ms;   // the first launch warms up
+      }
+      scratch_free(sc);
+      if (e == cudaSuccess && tot < best_ms) {
+        best_ms = tot;
+        best_t = t;
+      }
+    }
+    g.tc = best_t;
+    g.lines = (g.nl + best_t - 1) / best_t * best_t;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFreeAsync(sino, st);
+  if (rc != IMASK_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(e, "autotune (projector)");
+  return IMASK_OK;
+}
+
+// ---------------------------------------------------------------------------------
 // FP64 power method on the device (Sec. 3.6): largest eigenvalue of
 // sum_l w_l K_l^T K_l (image space), sum_l w_l K_l K_l^T (measurement space), or
 // (sum_l w_l K_l)^T (sum_l w_l K_l) (cross); level -1 alone when plain = true.
@@ -911,7 +980,10 @@ uint64_t plan_fingerprint(const imask_plan_s *p) {
   f.add(d.storage); f.add(d.variant); f.add(d.dual_tables); f.add(d.draws); f.add(d.step_rule);
   for (double v : p->probs) f.add(v);
   f.add(p->mu); f.add(p->sigma); f.add(p->theta);
-  for (int li = 0; li <= d.levels; ++li) f.add(p->dp.lg[li].bp_vgo);
+  for (int li = 0; li <= d.levels; ++li) {
+    f.add(p->dp.lg[li].bp_vgo);
+    f.add(p->dp.lg[li].tc);
+  }
   f.add((uint64_t)p->gcap);
   return f.h;
 }
@@ -1252,6 +1324,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   for (int li = 0; li <= r && rc == IMASK_OK; ++li) rc = upload_bp_groups(p, li, st);
 
   if (rc == IMASK_OK && p->desc.autotune) rc = autotune_bp(p, st);
+  if (rc == IMASK_OK && p->desc.autotune) rc = autotune_fp(p, st);
   if (rc == IMASK_OK) rc = plan_constants(p, st);
   e = cudaStreamSynchronize(st);
   cudaStreamDestroy(st);
@@ -1298,6 +1371,8 @@ imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
   info->autotuned = p->autotuned ? 1 : 0;
   for (int l = 0; l < IMASK_MAX_LEVELS; ++l)
     info->bp_view_groups[l] = l < p->desc.levels ? p->dp.lg[l + 1].bp_vgo : 0;
+  for (int l = 0; l < 8; ++l)
+    info->fp_strip_lines[l] = l < p->desc.levels ? p->dp.lg[l + 1].tc : 0;
   int64_t n_order = 0;
   for (int li = 0; li <= p->desc.levels; ++li) n_order += 2 * p->dp.lg[li].bp_nm * p->dp.lg[li].bp_nc;
   const int64_t na = p->dp.n_angles;
@@ -1737,6 +1812,144 @@ imask_status batch_capture(imask_batch_s *b, int unroll) {
   return IMASK_OK;
 }
 
+// The iteration records of a fused batch for `unroll` iterations starting at
+// the states' current ping-pong parity, in launch order (states by decreasing
+// size).  Mirrors the arguments enqueue_iteration gives the three kernels.
+std::vector<FusedSlice> fused_records(const imask_batch_s *b, int unroll) {
+  const int n = (int)b->states.size();
+  std::vector<FusedSlice> recs((size_t)unroll * n);
+  for (int pos = 0; pos < unroll; ++pos)
+    for (int i = 0; i < n; ++i) {
+      const imask_state_s *s = b->states[b->order[i]];
+      const imask_plan_s *p = s->plan;
+      const bool seq = p->desc.variant == 1;
+      const int cur = s->cur ^ (pos & 1);
+      FusedSlice &R = recs[(size_t)pos * n + i];
+      memset(&R, 0, sizeof(R));
+      R.P = p->dp;
+      R.sel.fixed = -2;
+      R.sel.seed = s->seed;
+      R.sel.seed_x = s->seed_x;
+      R.sel.k = 0;
+      R.sel.k_dev = s->k_dev;
+      R.sel.k_add = pos;
+      R.pads_fp = s->pads[cur];
+      R.pads_upd = s->pads[1 - cur];
+      R.D.on = 1;
+      R.D.y_in = s->y[cur];
+      R.D.y_out = s->y[1 - cur];
+      R.D.b = s->b;
+      R.D.psi = s->psi;
+      R.D.psi_fmt = s->psi_fmt;
+      R.D.psi_mean = s->psi_mean;
+      R.D.sigma = (float)p->sigma;
+      R.D.inv_1ps = (float)(1.0 / (1.0 + p->sigma));
+      R.y_bp = seq ? s->y[1 - cur] : s->y[cur];
+      R.g = cur != 0 ? s->g2 : s->g;
+      R.A.g = R.g;
+      R.A.x = s->x;
+      R.A.phi0 = s->phi0;
+      R.A.phic = s->phic;
+      for (int l = 0; l < IMASK_MAX_LEVELS; ++l) R.A.phic_off[l] = s->phic_off[l];
+      R.A.phi_mean = s->phi_mean;
+      R.A.tau = (float)(p->sigma / p->mu);
+      R.A.inv_1ps = (float)(1.0 / (1.0 + p->sigma));
+      R.A.prox_in_place = 1;
+      R.A.x_prev = nullptr;
+      R.A.extrapolate = seq ? 1 : 0;
+      R.A.theta = (float)p->desc.theta;
+      R.A.snap = s->snap;
+      R.err = p->d_err;
+      R.n_cta_x = p->n_cta_x;
+    }
+  return recs;
+}
+
+// Captures `unroll` iterations of a fused batch: per iteration one projector,
+// one back-projector (with its planner) and one update launch for all states,
+// then one launch that advances every state's device iteration counter.  The
+// launches are ordered as Alg. 1's data require, on three capture branches,
+// so that the projector of k runs beside the back-projector of k and the
+// back-projector of k + 1 beside the update of k: the projector of k after
+// the update of k - 1 (the sketch it reads), the back-projector of k after
+// the projector of k - 1 (y^k; Alg. 7: of k, whose y^{k+1} it reads) and the
+// update of k - 2 (which read the partial images it overwrites), the update
+// of k after the back-projector of k.
+imask_status batch_capture_fused(imask_batch_s *b, int unroll) {
+  batch_release_graph(b);
+  const int n = (int)b->states.size();
+  const std::vector<FusedSlice> recs = fused_records(b, unroll);
+  cudaStream_t origin = b->origin;
+  CK(cudaMemcpyAsync(b->d_recs, recs.data(), recs.size() * sizeof(FusedSlice),
+                     cudaMemcpyHostToDevice, origin),
+     "fused records");
+  CK(cudaStreamSynchronize(origin), "fused records");
+  if ((int)b->f_ev.size() < 3 * unroll) {
+    while ((int)b->f_ev.size() < 3 * unroll) {
+      cudaEvent_t ev = nullptr;
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "fused events");
+      b->f_ev.push_back(ev);
+    }
+  }
+  if (!b->f_fp) CK(cudaStreamCreateWithFlags(&b->f_fp, cudaStreamNonBlocking), "fused streams");
+  if (!b->f_bp) CK(cudaStreamCreateWithFlags(&b->f_bp, cudaStreamNonBlocking), "fused streams");
+  cudaEvent_t *ev_fp = b->f_ev.data(), *ev_bp = ev_fp + unroll, *ev_upd = ev_bp + unroll;
+  const int64_t c0 = launch_counter();
+  CK(cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed), "begin capture");
+  cudaError_t e = cudaEventRecord(b->fork, origin);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->f_fp, b->fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(b->f_bp, b->fork, 0);
+  for (int pos = 0; pos < unroll && e == cudaSuccess; ++pos) {
+    const FusedSlice *r = b->d_recs + (size_t)pos * n;
+    if (pos > 0 && (e = cudaStreamWaitEvent(b->f_fp, ev_upd[pos - 1], 0)) != cudaSuccess) break;
+    if ((e = launch_fp_multi(r, b->d_fp_start, n, b->fp_total, b->f_fp)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(ev_fp[pos], b->f_fp)) != cudaSuccess) break;
+    if (b->any_seq) {
+      if ((e = cudaStreamWaitEvent(b->f_bp, ev_fp[pos], 0)) != cudaSuccess) break;
+    } else if (pos > 0 && (e = cudaStreamWaitEvent(b->f_bp, ev_fp[pos - 1], 0)) != cudaSuccess) {
+      break;
+    }
+    if (pos >= 2 && (e = cudaStreamWaitEvent(b->f_bp, ev_upd[pos - 2], 0)) != cudaSuccess) break;
+    if ((e = launch_bp_multi(r, n, b->d_bp_start + (size_t)pos * (n + 1), b->d_bp_counter + pos,
+                             b->nv_cap, b->bp_smem, b->bp_grid, b->f_bp)) != cudaSuccess)
+      break;
+    if ((e = cudaEventRecord(ev_bp[pos], b->f_bp)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(origin, ev_bp[pos], 0)) != cudaSuccess) break;
+    if ((e = launch_update_multi(r, b->d_upd_start, n, b->upd_total, b->upd_smem, origin)) !=
+        cudaSuccess)
+      break;
+    e = cudaEventRecord(ev_upd[pos], origin);
+  }
+  // join both branches: the last projector (y of the next iteration) and the
+  // last back-projector (ordered before the last update already)
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, ev_fp[unroll - 1], 0);
+  if (e == cudaSuccess) e = launch_counter_multi(b->d_recs, n, unroll, origin);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(origin, &graph);
+  const int64_t captured = launch_counter() - c0;
+  add_launches(-captured);   // captured, not run
+  if (e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return cuda_fail(e, "fused graph capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_fail(e, "graph instantiate");
+  }
+  b->unroll = unroll;
+  b->kernels_per_replay = captured;
+  b->cur_at_capture.clear();
+  b->gen_at_capture.clear();
+  for (auto *s : b->states) {
+    b->cur_at_capture.push_back(s->cur);
+    b->gen_at_capture.push_back(s->gen);
+  }
+  return IMASK_OK;
+}
+
 }  // namespace
 
 imask_status imask_step(imask_state_t s, int32_t n_iters, void *stream) {
@@ -1831,6 +2044,67 @@ imask_status imask_batch_create(const imask_state_t *states, int32_t n_states,
   return IMASK_OK;
 }
 
+imask_status imask_batch_create_fused(const imask_state_t *states, int32_t n_states,
+                                      imask_batch_t *batch_out) {
+  if (!states || !batch_out || n_states < 1) return fail(IMASK_ERR_INVALID, "bad argument");
+  if (n_states > IMASK_MAX_FUSED)
+    return fail(IMASK_ERR_INVALID, "a fused batch holds at most %d states", IMASK_MAX_FUSED);
+  for (int i = 0; i < n_states; ++i)
+    if (states[i] && states[i]->plan->desc.reg != 0)
+      return fail(IMASK_ERR_INVALID,
+                  "state %d: fused batches take the quadratic regulariser (reg = 0) only", i);
+  imask_status rc = imask_batch_create(states, n_states, batch_out);
+  if (rc != IMASK_OK) return rc;
+  imask_batch_s *b = *batch_out;
+  const int n = n_states;
+  b->fused = true;
+  for (int i = 0; i < n_states; ++i) b->any_seq = b->any_seq || b->states[i]->plan->desc.variant == 1;
+  // launch order: largest solves first, so that the back-projector's dynamic
+  // item list ends with the small ones
+  b->order.resize(n);
+  for (int i = 0; i < n; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int a, int c) {
+    const DevPlan &A = b->states[a]->plan->dp, &C = b->states[c]->plan->dp;
+    return (long long)A.m * A.n > (long long)C.m * C.n;
+  });
+  std::vector<int> fp_start(n + 1, 0), upd_start(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    const imask_plan_s *p = b->states[b->order[i]]->plan;
+    const DevPlan &P = p->dp;
+    fp_start[i + 1] = fp_start[i] + p->n_cta_x + p->n_cta_y;
+    upd_start[i + 1] = upd_start[i] + (P.n / P.upd_tile) * (P.n / P.upd_tile);
+    b->bp_smem = std::max(b->bp_smem, bp_smem_bytes(P));
+    b->upd_smem = std::max(b->upd_smem, upd_smem_bytes_of(P));
+    for (int li = 0; li <= P.levels; ++li) b->nv_cap = std::max(b->nv_cap, P.lg[li].bp_nv);
+  }
+  b->fp_total = fp_start[n];
+  b->upd_total = upd_start[n];
+  int n_sm = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n_sm = v;
+  }
+  b->bp_grid = bp_multi_blocks_per_sm(b->bp_smem) * n_sm;
+  const int unroll = kGraphUnroll;
+  cudaError_t e;
+  if ((e = cudaMalloc(&b->d_recs, (size_t)unroll * n * sizeof(FusedSlice))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_fp_start, (n + 1) * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_upd_start, (n + 1) * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_bp_start, (size_t)unroll * (n + 1) * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&b->d_bp_counter, unroll * sizeof(int))) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_fp_start, fp_start.data(), (n + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, b->origin)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(b->d_upd_start, upd_start.data(), (n + 1) * sizeof(int),
+                           cudaMemcpyHostToDevice, b->origin)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(b->origin)) != cudaSuccess) {
+    imask_batch_destroy(b);
+    *batch_out = nullptr;
+    return cuda_fail(e, "fused batch buffers");
+  }
+  return IMASK_OK;
+}
+
 imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
   NvtxRange nv("imask_batch_step");
   if (!b) return fail(IMASK_ERR_INVALID, "NULL batch");
@@ -1854,7 +2128,7 @@ imask_status imask_batch_step(imask_batch_t b, int32_t n_iters, void *stream) {
       match = b->cur_at_capture[i] == b->states[i]->cur &&
               b->gen_at_capture[i] == b->states[i]->gen;
     if (!match) {
-      imask_status rc = batch_capture(b, unroll);
+      imask_status rc = b->fused ? batch_capture_fused(b, unroll) : batch_capture(b, unroll);
       if (rc != IMASK_OK) return rc;
     }
     for (int r = 0; r < replays; ++r) {
@@ -1882,6 +2156,12 @@ imask_status imask_batch_destroy(imask_batch_t b) {
   if (b->origin) cudaStreamDestroy(b->origin);
   for (auto ev : b->joins) cudaEventDestroy(ev);
   if (b->fork) cudaEventDestroy(b->fork);
+  for (auto ev : b->f_ev) cudaEventDestroy(ev);
+  if (b->f_fp) cudaStreamDestroy(b->f_fp);
+  if (b->f_bp) cudaStreamDestroy(b->f_bp);
+  for (void *ptr : {(void *)b->d_recs, (void *)b->d_fp_start, (void *)b->d_upd_start,
+                    (void *)b->d_bp_start, (void *)b->d_bp_counter})
+    if (ptr) cudaFree(ptr);
   delete b;
   return IMASK_OK;
 }

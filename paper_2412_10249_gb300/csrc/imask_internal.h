@@ -153,6 +153,25 @@ struct PrimalArgs {
   SnapArgs snap;
 };
 
+// One solve of a fused batch: everything the projector, back-projector and
+// update launches of one iteration need for it (the device copy of its plan
+// and its buffers for the iteration's ping-pong parity).  A fused launch
+// covers every solve of the batch, the CTAs of solve s after those of solves
+// 0..s-1.
+struct FusedSlice {
+  DevPlan P;
+  LevelSel sel;        // seed, device iteration counter and offset
+  PadSet pads_fp;      // sketch images the projector reads
+  PadSet pads_upd;     // sketch images the update writes
+  DualArgs D;          // projector epilogue
+  const float *y_bp;   // back-projector input
+  float *g;            // back-projector partial images
+  PrimalArgs A;        // update
+  unsigned int *err;
+  int n_cta_x;         // projector CTAs of x-major rays
+};
+#define IMASK_MAX_FUSED 1024   // solves per fused batch
+
 // ---- kernel launchers (kernels.cu) -------------------------------------------
 extern "C++" {
 int lvl_host_draw(const DevPlan &P, unsigned long long seed, long long k);
@@ -172,6 +191,24 @@ cudaError_t launch_adjsketch(const DevPlan &P, int ell, const float *g, float *i
                              cudaStream_t st);
 cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int write_sketch,
                           PadSet pads, cudaStream_t st);
+// Fused batches: one launch of each kernel for all n_slices solves.
+// fp_start / upd_start[s] (device, n_slices + 1 entries): the first CTA of
+// solve s.  The back-projector launches a one-CTA planner that writes the
+// solves' item offsets at their drawn levels into bp_start (device,
+// n_slices + 1 ints) and zeroes bp_counter (device int), then `grid` resident
+// CTAs that take items from the counter.  smem sizes and nv_cap are the
+// largest over the solves.
+cudaError_t launch_fp_multi(const FusedSlice *recs, const int *fp_start, int n_slices,
+                            int total_ctas, cudaStream_t st);
+cudaError_t launch_bp_multi(const FusedSlice *recs, int n_slices, int *bp_start, int *bp_counter,
+                            int nv_cap, long long smem, int grid, cudaStream_t st);
+int bp_multi_blocks_per_sm(long long dyn_smem);
+cudaError_t launch_update_multi(const FusedSlice *recs, const int *upd_start, int n_slices,
+                                int total_ctas, int smem, cudaStream_t st);
+int upd_smem_bytes_of(const DevPlan &P);
+// *k_dev += delta for the iteration counter of every solve (recs[s].sel.k_dev)
+cudaError_t launch_counter_multi(const FusedSlice *recs, int n_slices, long long delta,
+                                 cudaStream_t st);
 cudaError_t launch_tv_prox(const DevPlan &P, float tau, float mu, float lam, float eps, int inner,
                            float *x, float *work, cudaStream_t st);
 cudaError_t launch_tv_nonneg_prox(const DevPlan &P, float alpha, int inner, float *x, float *work,

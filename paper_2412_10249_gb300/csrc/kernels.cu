@@ -28,6 +28,9 @@ std::atomic<int64_t> g_launches{0};
 
 constexpr float kMagic = 12582912.0f;   // 1.5 * 2^23: floor via round-down add
 constexpr int kMagicBits = 0x4B400000;
+#define kMagic2 make_float2(kMagic, kMagic)
+#define kNegMagic2 make_float2(-kMagic, -kMagic)
+#define kMinusOne2 make_float2(-1.0f, -1.0f)
 constexpr float kBpEps = 0.01f;          // slack (in bins) of the back-projector's ray range
 constexpr int kWaitLimit = 1 << 20;      // bounded mbarrier polls before giving up
 
@@ -176,9 +179,22 @@ __device__ __forceinline__ void block_origin(float a_hi, float a_lo, float t_hi,
 // misses the grid entirely is redirected into the leading zeros: no per-sample
 // bounds check is needed.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(FP_THREADS, 2)
-    k_fp(DevPlan P, LevelSel sel, PadSet pads, float *sino, DualArgs D, int n_cta_x,
-         unsigned int *err, int test_skip_first_strip) {
+// Ray slot r of thread tid in a CTA whose rays start at `begin`.  Slots go in
+// pairs: pair p of warp w covers the 64 consecutive list entries from
+// begin + 2 p FP_THREADS + 64 w, lane l taking entries l and l + 32, so that
+// the two rays of a pair are close bins of one view (they hit or miss the
+// grid together) and the 32 lanes of a slot read 32 neighbouring rays' rows
+// (no shared-memory bank conflicts).
+__device__ __forceinline__ int fp_ray(int begin, int r, int tid) {
+  return begin + (r >> 1) * (2 * FP_THREADS) + (tid >> 5) * 64 + (r & 1) * 32 + (tid & 31);
+}
+
+// One projector CTA (block `bid` of the plan's projector grid); the plan and
+// the arguments may live in kernel parameters (k_fp) or in device memory
+// (k_fp_multi, several solves in one launch).
+__device__ __forceinline__ void fp_body(const DevPlan &P, const LevelSel &sel, const PadSet &pads,
+                                        float *sino, const DualArgs &D, int n_cta_x,
+                                        unsigned int *err, int test_skip_first_strip, int bid) {
   extern __shared__ __align__(128) float fp_smem[];
   __shared__ __align__(8) unsigned long long full_bar[FP_STAGES];
   __shared__ unsigned int released[FP_STAGES];   // warps done with each stage (monotone)
@@ -186,19 +202,20 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
 
   const int ell = sel_level(P, sel);
   const LevelGeom G = P.lg[ell + 1];
-  const bool xaxis = (int)blockIdx.x < n_cta_x;
-  const int chunk = xaxis ? (int)blockIdx.x : (int)blockIdx.x - n_cta_x;
+  const bool xaxis = bid < n_cta_x;
+  const int chunk = xaxis ? bid : bid - n_cta_x;
   const int csz = xaxis ? P.fp_chunk_x : P.fp_chunk_y;
   const int begin = xaxis ? chunk * csz : P.m_x + chunk * csz;
   const int end = xaxis ? min(begin + csz, P.m_x) : min(begin + csz, P.m);
   const float *img = xaxis ? pads.T[ell + 1] : pads.R[ell + 1];
   const int tid = threadIdx.x;
 
+  static_assert(FP_RAYS % 2 == 0, "rays go in pairs");
   float ahi[FP_RAYS], alo[FP_RAYS], thi[FP_RAYS], tlo[FP_RAYS], rl[FP_RAYS], acc[FP_RAYS];
   int boff[FP_RAYS];
 #pragma unroll
   for (int r = 0; r < FP_RAYS; ++r) {
-    const int idx = begin + r * FP_THREADS + tid;
+    const int idx = fp_ray(begin, r, tid);
     acc[r] = 0.0f;
     rl[r] = 0.0f;
     boff[r] = 0;
@@ -283,24 +300,37 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
         }
       }
       const float d0 = (float)(c & (LBLOCK - 1));
+      // Rays go in pairs through the packed FP32x2 instructions of sm_100+
+      // (one issue slot for both rays; per component the rounding is that of
+      // the scalar operation, so the samples are bit for bit those of
+      // fmaf / __fadd_rd / subtraction).  A pair is skipped when neither of its
+      // slots has a ray on the grid in this block.
 #pragma unroll
-      for (int r = 0; r < FP_RAYS; ++r) {
-        if (!(act & (1u << r))) continue;
-        float a[4];
+      for (int r = 0; r < FP_RAYS; r += 2) {
+        if (!(act & (3u << r))) continue;
+        const float2 t2 = make_float2(thi[r], thi[r + 1]);
+        const float2 r2 = make_float2(rl[r], rl[r + 1]);
+        float2 a[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const float dcf = d0 + (float)u;
           const float *line = buf + (cc + u) * ls;
-          const float q = fmaf(dcf, thi[r], rl[r]);
-          const float tq = __fadd_rd(q, kMagic);
-          int i0 = boff[r] + (__float_as_int(tq) - kMagicBits);
+          const float2 q = __ffma2_rn(make_float2(dcf, dcf), t2, r2);
+          const float2 tq = __fadd2_rd(q, kMagic2);
+          int i0 = boff[r] + (__float_as_int(tq.x) - kMagicBits);
+          int i1 = boff[r + 1] + (__float_as_int(tq.y) - kMagicBits);
           if (!IMASK_INDEX_OK(i0 >= 0 && i0 + 1 < ls, 1)) i0 = 0;
-          const float f = q - (tq - kMagic);
-          const float v0 = line[i0];
-          const float v1 = line[i0 + 1];
-          a[u] = fmaf(f, v1 - v0, v0);   // independent samples, summed as a tree
+          if (!IMASK_INDEX_OK(i1 >= 0 && i1 + 1 < ls, 1)) i1 = 0;
+          // f = q - (tq - magic), the subtraction as a fused multiply-add by -1
+          const float2 f = __ffma2_rn(__fadd2_rn(tq, kNegMagic2), kMinusOne2, q);
+          const float2 v0 = make_float2(line[i0], line[i1]);
+          const float2 v1 = make_float2(line[i0 + 1], line[i1 + 1]);
+          // independent samples, summed as a tree
+          a[u] = __ffma2_rn(f, __ffma2_rn(v0, kMinusOne2, v1), v0);
         }
-        part[r] += (a[0] + a[1]) + (a[2] + a[3]);
+        const float2 sum = __fadd2_rn(__fadd2_rn(a[0], a[1]), __fadd2_rn(a[2], a[3]));
+        part[r] += sum.x;
+        part[r + 1] += sum.y;
       }
     }
 #pragma unroll
@@ -337,7 +367,7 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
   float gz[FP_RAYS];
 #pragma unroll
   for (int r = 0; r < FP_RAYS; ++r) {
-    const int idx = begin + r * FP_THREADS + tid;
+    const int idx = fp_ray(begin, r, tid);
     qv[r] = -1;
     gz[r] = 0.0f;
     if (idx < end) {
@@ -404,6 +434,12 @@ __global__ void __launch_bounds__(FP_THREADS, 2)
     D.y_out[q] = fmaf(D.sigma, zeta - bv[r], yv[r]) * D.inv_1ps;
     D.psi_mean[q] = fmaf(P.probs[ell], dmean, pmv[r]);
   }
+}
+
+__global__ void __launch_bounds__(FP_THREADS, 2)
+    k_fp(DevPlan P, LevelSel sel, PadSet pads, float *sino, DualArgs D, int n_cta_x,
+         unsigned int *err, int test_skip_first_strip) {
+  fp_body(P, sel, pads, sino, D, n_cta_x, err, test_skip_first_strip, (int)blockIdx.x);
 }
 
 // ---------------------------------------------------------------------------------
@@ -502,9 +538,12 @@ __device__ int scan_counts(int *a, int n) {
   return tot;
 }
 
-__global__ void __launch_bounds__(BP_THREADS, 4)
-    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
-         unsigned int *err, int nv_cap) {
+// One back-projector work item (block `bid` of the plan's grid at the drawn
+// level); returns with every shared-memory read done except the last
+// barrier's.
+__device__ __forceinline__ void bp_body(const DevPlan &P, const LevelSel &sel,
+                                        const float *__restrict__ y, float *__restrict__ gout,
+                                        unsigned int *err, int nv_cap, int bid) {
   extern __shared__ __align__(16) float4 bp_raw[];
   // private accumulators: [slot][thread]; slots 0..BP_ACC-1 are cross lines
   // -2..BP_SEG+1 of the owner's segment
@@ -514,7 +553,7 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
   const int nm = G.bp_nm, nc = G.bp_nc, vgo = G.bp_vgo;
   const int ntile = nm * nc;
   // CTAs go heaviest (role, tile) first so that light tiles fill the last wave
-  const int rank = (int)blockIdx.x / vgo, vg = (int)blockIdx.x % vgo;
+  const int rank = bid / vgo, vg = bid % vgo;
   if (rank >= 2 * ntile) return;
   const int code = P.bp_order[G.bp_order_off + rank];
   const int role = code >= ntile ? 1 : 0;   // 0: x-major rays, 1: y-major
@@ -680,12 +719,35 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
   }
 }
 
+__global__ void __launch_bounds__(BP_THREADS, 4)
+    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
+         unsigned int *err, int nv_cap) {
+  bp_body(P, sel, y, gout, err, nv_cap, (int)blockIdx.x);
+}
+
 // The back-projector leaves 2 bp_vgo partial images (x- and y-major rays, one
 // per view group), each of side nl; their sum in a fixed order is R_ell^T y.
-__device__ __forceinline__ float g_sum(const float *g, int vgo, size_t plane, size_t idx) {
-  float s = g[idx];
-  for (int v = 1; v < vgo; ++v) s += g[(size_t)v * plane + idx];
+// Sums planes v0, v0 + dv, ... (fewer than v1) at element idx in that order;
+// the loads go in batches of kPlaneBatch, all in flight before the adds.
+constexpr int kPlaneBatch = 8;
+__device__ __forceinline__ float planes_sum(const float *g, int v0, int v1, int dv, size_t plane,
+                                            size_t idx, float s) {
+  for (int v = v0; v < v1; v += kPlaneBatch * dv) {
+    float t[kPlaneBatch];
+#pragma unroll
+    for (int u = 0; u < kPlaneBatch; ++u) {
+      const int w = v + u * dv;
+      t[u] = w < v1 ? __ldg(g + (size_t)w * plane + idx) : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPlaneBatch; ++u)
+      if (v + u * dv < v1) s += t[u];
+  }
   return s;
+}
+
+__device__ __forceinline__ float g_sum(const float *g, int vgo, size_t plane, size_t idx) {
+  return planes_sum(g, 1, vgo, 1, plane, idx, __ldg(g + idx));
 }
 
 // Sum of the back-projector's npl partial planes for the cs x cs coarse pixels
@@ -702,9 +764,7 @@ __device__ void coarse_planes_sum(const float *g, int npl, int nl, int I0, int J
     for (int u = threadIdx.x; u < ncp * K; u += blockDim.x) {
       const int p = u % ncp, k = u / ncp;
       const size_t gi = (size_t)(I0 + p / cs) * nl + J0 + p % cs;
-      float sum = 0.0f;
-      for (int v = k; v < npl; v += K) sum += g[(size_t)v * plane + gi];
-      red[u] = sum;
+      red[u] = planes_sum(g, k, npl, K, plane, gi, 0.0f);
     }
   }
   __syncthreads();
@@ -714,7 +774,7 @@ __device__ void coarse_planes_sum(const float *g, int npl, int nl, int I0, int J
       for (int k = 0; k < K; ++k) sum += red[k * ncp + p];
     } else {
       const size_t gi = (size_t)(I0 + p / cs) * nl + J0 + p % cs;
-      for (int v = 0; v < npl; ++v) sum += g[(size_t)v * plane + gi];
+      sum = planes_sum(g, 0, npl, 1, plane, gi, 0.0f);
     }
     out[p] = sum;
   }
@@ -871,16 +931,39 @@ __global__ void __launch_bounds__(UPD_THREADS)
 // the next level.  phi_new = 4^-ell T^*(g) (ell >= 1, block-constant, kept on
 // the level grid) or S_r g (ell = 0); xi = phi_new - phi_ell + sum p phi;
 // x+ = prox(x - (sigma/mu) xi); the running mean and the table take phi_new.
-__global__ void __launch_bounds__(UPD_THREADS)
-    k_update(DevPlan P, LevelSel sel, PrimalArgs A, int write_sketch, PadSet pads) {
+__device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &sel,
+                                            const PrimalArgs &A, int write_sketch,
+                                            const PadSet &pads, int bid) {
   extern __shared__ __align__(16) float upd_smem[];
   const int ts = P.upd_tile, ntx = P.n / ts;
   float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
   float *dc = pyr + ts * ts / 2 + 4;
-  const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
+  const int ti0 = (bid / ntx) * ts, tj0 = (bid % ntx) * ts;
   const int n = P.n;
   const int ell = sel_level_x(P, sel);
   const float pl = P.probs[ell];
+
+  // A thread's pixels go in groups of kUpdPix: every load of a group is
+  // issued before its first store (a store to one pixel could alias the next
+  // pixel's loads and would otherwise keep them waiting one by one).  When
+  // one group covers the tile (the usual case) its loads are issued first of
+  // all, so that they are in flight together with the partial-plane sums.
+  constexpr int kUpdPix = 4;
+  const bool one_group = ts * ts <= kUpdPix * (int)blockDim.x;
+  float pmv[kUpdPix], xov[kUpdPix], ph0[kUpdPix];
+  auto load_group = [&](int p0) {
+#pragma unroll
+    for (int u = 0; u < kUpdPix; ++u) {
+      const int p = p0 + u * (int)blockDim.x;
+      pmv[u] = xov[u] = ph0[u] = 0.0f;
+      if (p >= ts * ts) continue;
+      const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
+      pmv[u] = A.phi_mean[gp];
+      xov[u] = A.x[gp];
+      if (ell < 1) ph0[u] = A.phi0[gp];
+    }
+  };
+  if (one_group) load_group(threadIdx.x);
 
   int cs = 0;
   if (ell >= 1) {
@@ -898,29 +981,44 @@ __global__ void __launch_bounds__(UPD_THREADS)
     }
     __syncthreads();
   } else {
+    // the partial planes of kUpdPix pixels per thread, kPlaneBatch planes of
+    // each in flight at once, added per pixel in plane order
     const int vgo0 = 2 * P.lg[1].bp_vgo;
-    for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-      aux[p] = g_sum(A.g, vgo0, (size_t)n * n, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
+    const size_t plane = (size_t)n * n;
+    for (int p0 = threadIdx.x; p0 < ts * ts; p0 += kUpdPix * blockDim.x) {
+      size_t gi[kUpdPix];
+      float sum[kUpdPix];
+#pragma unroll
+      for (int u = 0; u < kUpdPix; ++u) {
+        const int p = p0 + u * (int)blockDim.x;
+        gi[u] = p < ts * ts ? (size_t)(ti0 + p / ts) * n + tj0 + p % ts : 0;
+        sum[u] = p < ts * ts ? __ldg(A.g + gi[u]) : 0.0f;
+      }
+      for (int v = 1; v < vgo0; v += kPlaneBatch) {
+        float t[kUpdPix][kPlaneBatch];
+#pragma unroll
+        for (int u = 0; u < kUpdPix; ++u)
+#pragma unroll
+          for (int w = 0; w < kPlaneBatch; ++w)
+            t[u][w] = v + w < vgo0 ? __ldg(A.g + (size_t)(v + w) * plane + gi[u]) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < kUpdPix; ++u)
+#pragma unroll
+          for (int w = 0; w < kPlaneBatch; ++w)
+            if (v + w < vgo0) sum[u] += t[u][w];
+      }
+#pragma unroll
+      for (int u = 0; u < kUpdPix; ++u) {
+        const int p = p0 + u * (int)blockDim.x;
+        if (p < ts * ts) aux[p] = sum[u];
+      }
+    }
     __syncthreads();
     if (P.levels > 1) tile_pyramid(aux, pyr, ts, P.levels);
   }
 
-  // A thread's pixels go in groups of kUpdPix: every load of a group is
-  // issued before its first store (a store to one pixel could alias the next
-  // pixel's loads and would otherwise keep them waiting one by one).
-  constexpr int kUpdPix = 4;
   for (int p0 = threadIdx.x; p0 < ts * ts; p0 += kUpdPix * blockDim.x) {
-    float pmv[kUpdPix], xov[kUpdPix], ph0[kUpdPix];
-#pragma unroll
-    for (int u = 0; u < kUpdPix; ++u) {
-      const int p = p0 + u * (int)blockDim.x;
-      pmv[u] = xov[u] = ph0[u] = 0.0f;
-      if (p >= ts * ts) continue;
-      const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
-      pmv[u] = A.phi_mean[gp];
-      xov[u] = A.x[gp];
-      if (ell < 1) ph0[u] = A.phi0[gp];
-    }
+    if (!one_group) load_group(p0);
 #pragma unroll
     for (int u = 0; u < kUpdPix; ++u) {
       const int p = p0 + u * (int)blockDim.x;
@@ -952,6 +1050,98 @@ __global__ void __launch_bounds__(UPD_THREADS)
   const int elln = draw_level(P, sel.seed, sel_k(sel) + 1);
   float *S = A.snap.snap ? A.snap.snap + A.snap.snap_off[elln] : nullptr;
   sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0, S);
+}
+
+__global__ void __launch_bounds__(UPD_THREADS)
+    k_update(DevPlan P, LevelSel sel, PrimalArgs A, int write_sketch, PadSet pads) {
+  update_body(P, sel, A, write_sketch, pads, (int)blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------------
+// Fused batches: one launch of each kernel runs one iteration of every solve.
+// The projector and update grids are the solves' own grids one after the other
+// (their sizes do not depend on the drawn level).  The back-projector's work
+// depends on each solve's level, so its CTAs stay resident and take items
+// (one (role, tile, view group) each, heaviest first within a solve, the
+// solves largest first) from a device counter until the iteration's items
+// run out; no CTA ever waits for another.
+// ---------------------------------------------------------------------------------
+// Index s with start[s] <= b < start[s + 1] (start ascending, start[0] = 0).
+__device__ __forceinline__ int slice_of(const int *start, int n, int b) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (start[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(FP_THREADS, 2)
+    k_fp_multi(const FusedSlice *__restrict__ recs, const int *__restrict__ fp_start, int n) {
+  const int b = (int)blockIdx.x;
+  const int s = slice_of(fp_start, n, b);
+  const FusedSlice &R = recs[s];
+  fp_body(R.P, R.sel, R.pads_fp, nullptr, R.D, R.n_cta_x, R.err, 0, b - fp_start[s]);
+}
+
+__global__ void __launch_bounds__(UPD_THREADS, 3)
+    k_update_multi(const FusedSlice *__restrict__ recs, const int *__restrict__ upd_start, int n) {
+  const int b = (int)blockIdx.x;
+  const int s = slice_of(upd_start, n, b);
+  const FusedSlice &R = recs[s];
+  update_body(R.P, R.sel, R.A, 1, R.pads_upd, b - upd_start[s]);
+}
+
+// Items of every solve's back-projection at its drawn level, as offsets into
+// one list (start[n] = total), and the work counter reset for the launch that
+// follows.  One CTA.
+__global__ void __launch_bounds__(BP_THREADS)
+    k_bp_plan(const FusedSlice *__restrict__ recs, int n, int *__restrict__ start, int *counter) {
+  __shared__ int cnt[IMASK_MAX_FUSED + 1];
+  for (int s = threadIdx.x; s < n; s += BP_THREADS) {
+    const FusedSlice &R = recs[s];
+    const int ell = sel_level_x(R.P, R.sel);
+    const LevelGeom &G = R.P.lg[ell + 1];
+    cnt[s] = 2 * G.bp_nm * G.bp_nc * G.bp_vgo;
+  }
+  __syncthreads();
+  scan_counts(cnt, n);   // ends with a barrier
+  for (int s = threadIdx.x; s <= n; s += BP_THREADS) start[s] = cnt[s];
+  if (threadIdx.x == 0) *counter = 0;
+}
+
+__global__ void __launch_bounds__(BP_THREADS, 4)
+    k_bp_multi(const FusedSlice *__restrict__ recs, int n, const int *__restrict__ start,
+               int *counter, int nv_cap) {
+  __shared__ int item;
+  const int total = start[n];
+  // thread 0 asks for the next item while the current one runs, so that the
+  // counter's round trip is hidden behind the work
+  int next = 0;
+  if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      item = next;
+      if (next < total) next = atomicAdd(counter, 1);
+    }
+    __syncthreads();
+    const int it = item;
+    if (it >= total) break;
+    const int s = slice_of(start, n, it);
+    const FusedSlice &R = recs[s];
+    bp_body(R.P, R.sel, R.y_bp, R.g, R.err, nv_cap, it - start[s]);
+    // every thread is done with the item's shared memory (and with `item`)
+    // before the next item is published
+    __syncthreads();
+  }
+}
+
+__global__ void k_counter_multi(const FusedSlice *__restrict__ recs, int n, long long delta) {
+  for (int s = (int)(blockIdx.x * blockDim.x + threadIdx.x); s < n; s += gridDim.x * blockDim.x)
+    *const_cast<long long *>(recs[s].sel.k_dev) += delta;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1370,6 +1560,59 @@ cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int wri
   if (e != cudaSuccess) return e;
   count_launch();
   k_update<<<nt * nt, UPD_THREADS, sm, st>>>(P, sel, pa, write_sketch, pads);
+  return cudaGetLastError();
+}
+
+int upd_smem_bytes_of(const DevPlan &P) { return upd_smem_bytes(P); }
+
+cudaError_t launch_fp_multi(const FusedSlice *recs, const int *fp_start, int n_slices,
+                            int total_ctas, cudaStream_t st) {
+  const int sm = (int)fp_smem_bytes();
+  cudaError_t e = set_smem((const void *)k_fp_multi, sm);
+  if (e != cudaSuccess) return e;
+  if (total_ctas <= 0) return cudaSuccess;
+  count_launch();
+  k_fp_multi<<<total_ctas, FP_THREADS, sm, st>>>(recs, fp_start, n_slices);
+  return cudaGetLastError();
+}
+
+int bp_multi_blocks_per_sm(long long dyn_smem) {
+  if (set_smem((const void *)k_bp_multi, (int)dyn_smem) != cudaSuccess) return 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bp_multi, BP_THREADS,
+                                                    (size_t)dyn_smem) != cudaSuccess ||
+      n < 1)
+    return 1;
+  return n;
+}
+
+cudaError_t launch_bp_multi(const FusedSlice *recs, int n_slices, int *bp_start, int *bp_counter,
+                            int nv_cap, long long smem, int grid, cudaStream_t st) {
+  if (n_slices < 1 || n_slices > IMASK_MAX_FUSED) return cudaErrorInvalidValue;
+  cudaError_t e = set_smem((const void *)k_bp_multi, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  k_bp_plan<<<1, BP_THREADS, 0, st>>>(recs, n_slices, bp_start, bp_counter);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  count_launch();
+  k_bp_multi<<<grid, BP_THREADS, smem, st>>>(recs, n_slices, bp_start, bp_counter, nv_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_multi(const FusedSlice *recs, const int *upd_start, int n_slices,
+                                int total_ctas, int smem, cudaStream_t st) {
+  cudaError_t e = set_smem((const void *)k_update_multi, smem);
+  if (e != cudaSuccess) return e;
+  if (total_ctas <= 0) return cudaSuccess;
+  count_launch();
+  k_update_multi<<<total_ctas, UPD_THREADS, smem, st>>>(recs, upd_start, n_slices);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counter_multi(const FusedSlice *recs, int n_slices, long long delta,
+                                 cudaStream_t st) {
+  count_launch();
+  k_counter_multi<<<(n_slices + 255) / 256, 256, 0, st>>>(recs, n_slices, delta);
   return cudaGetLastError();
 }
 

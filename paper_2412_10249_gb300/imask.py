@@ -59,6 +59,7 @@ class PlanInfo(ctypes.Structure):
         ("n_xmajor_rays", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
         ("plan_bytes", ctypes.c_int64), ("autotuned", ctypes.c_int32),
         ("bp_view_groups", ctypes.c_int32 * 8),
+        ("fp_strip_lines", ctypes.c_int32 * 8),
     ]
 
 
@@ -101,6 +102,7 @@ SIGNATURES = {
     "imask_probe_smem": (_I32, [_DP, _VP]),
     "imask_selftest_projector_timeout": (_I32, [_VP, _VP]),
     "imask_batch_create": (_I32, [_VP, _I32, _VP]),
+    "imask_batch_create_fused": (_I32, [_VP, _I32, _VP]),
     "imask_batch_step": (_I32, [_VP, _I32, _VP]),
     "imask_batch_destroy": (_I32, [_VP]),
     "imask_pdhg": (_I32, [_VP, _VP, _I32, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -211,6 +213,7 @@ def imask_plan_get_info(plan) -> dict:
     _check(lib().imask_plan_get_info(plan, ctypes.byref(info)))
     out = {k: getattr(info, k) for k, _ in PlanInfo._fields_}
     out["bp_view_groups"] = list(info.bp_view_groups)
+    out["fp_strip_lines"] = list(info.fp_strip_lines)
     return out
 
 
@@ -453,13 +456,17 @@ class State:
 
 
 class Batch:
-    """Independent states advanced together through captured CUDA graphs."""
+    """Independent states advanced together through captured CUDA graphs:
+    one graph branch per state (default), or, with ``fused=True``, one
+    launch of each kernel per iteration for all states."""
 
-    def __init__(self, states):
+    def __init__(self, states, fused: bool = False):
         self.states = list(states)
+        self.fused = bool(fused)
         arr = (ctypes.c_void_p * len(self.states))(*[st.handle.value for st in self.states])
         h = ctypes.c_void_p()
-        _check(lib().imask_batch_create(arr, len(self.states), ctypes.byref(h)))
+        create = lib().imask_batch_create_fused if self.fused else lib().imask_batch_create
+        _check(create(arr, len(self.states), ctypes.byref(h)))
         self.handle = h
 
     def step(self, n_iters: int, stream=None):

@@ -1,6 +1,7 @@
-"""Plan-time autotuning of the back-projector split: the tuned plan keeps
-parity with the oracle (the split only changes the order of the partial-image
-sum) and reports what it chose."""
+"""Plan-time autotuning of the back-projector split and the projector's strip
+height: the tuned plan keeps parity with the oracle (the split only changes
+the order of the partial-image sum, the strip height only how the image
+streams through shared memory) and reports what it chose."""
 import math
 
 import numpy as np
@@ -33,20 +34,26 @@ def rel(a, b):
     inputs.Problem(n=64, n_angles=90, n_det=96, geometry=1, angle_span=2 * math.pi, levels=4),
     inputs.Problem(n=48, n_angles=37, n_det=75, geometry=1, angle_span=2 * math.pi,
                    angle_start=0.3, levels=4, probs=[0.3, 0.3, 0.2, 0.2]),
-], ids=["fan64_r4", "fan48_p3322"])
+    inputs.Problem(n=80, n_angles=45, n_det=117, geometry=0, angle_span=math.pi, levels=3),
+], ids=["fan64_r4", "fan48_p3322", "par80_r3"])
 def test_autotuned_plan_keeps_parity(imask, prob):
     params = dict(prob.params(), mu=0.1, sigma=0.04)
     plan = imask.Plan(dict(params, autotune=1))
     info = plan.info
     assert info["autotuned"] == 1
     assert all(v >= 1 for v in info["bp_view_groups"][:prob.levels])
+    assert all(t >= 4 and t % 4 == 0 for t in info["fp_strip_lines"][:prob.levels])
     o = Oracle(**params)
     rng = np.random.default_rng(0)
     y = rng.standard_normal(o.m)
     yt = torch.as_tensor(y.astype(np.float32), device="cuda")
+    x = rng.standard_normal(prob.n * prob.n)
+    xt = torch.as_tensor(x.astype(np.float32), device="cuda")
     for ell in range(prob.levels):
         got = plan.backproject(ell, yt).double().cpu().numpy()
         assert rel(got, o.KT(ell, y)) <= 1e-5, ell
+        got = plan.project(ell, xt).double().cpu().numpy()
+        assert rel(got, o.K(ell, x)) <= 1e-5, ell
     _, b, _ = inputs.measurements(prob, seed=1, noise="none")
     st, _ = o.run(b.ravel(), 3, 30)
     s = plan.state(torch.as_tensor(b.ravel().astype(np.float32), device="cuda"), 3)

@@ -186,3 +186,99 @@ def test_overlapped_streams_equal_serial_order(imask, extra):
         imask.imask_profile_enable(0)
         imask.imask_profile_read(reset=True)
     assert torch.equal(x_fast, x_serial)
+
+
+# ---- fused batches: one launch of each kernel per iteration for all states ----
+def _mixed_setups(imask):
+    """Quadratic solves of different sizes, geometries, level counts and
+    iteration forms (the fused batch takes reg = 0 only)."""
+    probs = (
+        (FAN64, {}),
+        (PAR40, dict(variant=1, theta=1.0, dual_tables=1)),
+        (inputs.Problem(n=48, n_angles=37, n_det=75, geometry=1, angle_span=2 * math.pi,
+                        angle_start=0.3, levels=4), dict(draws=1)),
+        (inputs.Problem(n=96, n_angles=60, n_det=144, geometry=1, angle_span=2 * math.pi,
+                        levels=2), dict(storage=1)),
+        (FAN64, dict(dual_tables=1)),
+    )
+    out = []
+    for prob, extra in probs:
+        plan = imask.Plan(dict(prob.params(), mu=0.1, sigma=0.04, **extra))
+        _, b, _ = inputs.measurements(prob, seed=len(out), noise="none")
+        out.append((prob, extra, plan, cuda(b)))
+    return out
+
+
+def test_fused_batch_equals_plain_steps(imask):
+    setups = _mixed_setups(imask)
+    ref = []
+    for i, (_, _, plan, b) in enumerate(setups):
+        s = plan.state(b, 40 + i)
+        s.step(23)
+        ref.append((s.get(s.X), s.get(s.Y), s.get(s.PSI_MEAN)))
+    states = [plan.state(b, 40 + i) for i, (_, _, plan, b) in enumerate(setups)]
+    states[2].step(1)                 # one state starts at the other parity
+    batch = imask.Batch(states, fused=True)
+    batch.step(12)                    # three replays
+    batch.step(10)                    # two replays and two plain iterations each
+    states[0].step(1)
+    states[1].step(1)
+    for s in states[3:]:
+        s.step(1)
+    torch.cuda.synchronize()
+    for s, (rx, ry, rp) in zip(states, ref):
+        assert s.k == 23
+        assert torch.equal(s.get(s.X), rx)
+        assert torch.equal(s.get(s.Y), ry)
+        assert torch.equal(s.get(s.PSI_MEAN), rp)
+    batch.close()
+    for (_, _, plan, _) in setups:
+        plan.check()
+
+
+def test_fused_batch_matches_oracle(imask):
+    # three solves of different sizes and geometries in one fused batch, each
+    # against the FP64 oracle on the same seed
+    setups = _mixed_setups(imask)[:3]
+    states = [plan.state(b, 9 + i) for i, (_, _, plan, b) in enumerate(setups)]
+    batch = imask.Batch(states, fused=True)
+    batch.step(24)
+    torch.cuda.synchronize()
+    for i, ((prob, extra, _, _), s) in enumerate(zip(setups, states)):
+        _, b, _ = inputs.measurements(prob, seed=i, noise="none")
+        o = Oracle(**dict(prob.params(), mu=0.1, sigma=0.04))
+        if extra.get("variant") == 1 or extra.get("dual_tables") or extra.get("draws"):
+            st, _, _ = o.run_variant(b.ravel(), 9 + i, 24,
+                                     sequential=extra.get("variant") == 1,
+                                     snapshots=bool(extra.get("dual_tables")),
+                                     independent=bool(extra.get("draws")))
+        else:
+            st, _ = o.run(b.ravel(), 9 + i, 24)
+        x = s.get(s.X).double().cpu().numpy()
+        err = np.linalg.norm(x - st["x"]) / np.linalg.norm(st["x"])
+        assert err <= 1e-4, (i, err)
+    batch.close()
+
+
+def test_fused_batch_launches_three_kernels_per_iteration(imask):
+    setups = _mixed_setups(imask)
+    states = [plan.state(b, i) for i, (_, _, plan, b) in enumerate(setups)]
+    batch = imask.Batch(states, fused=True)
+    batch.step(4)     # capture
+    torch.cuda.synchronize()
+    c0 = imask.imask_launch_count()
+    batch.step(8)
+    torch.cuda.synchronize()
+    # per iteration: projector, planner + back-projector, update; per replay
+    # one counter kernel
+    assert imask.imask_launch_count() - c0 == 2 * (4 * 4 + 1)
+    batch.close()
+
+
+def test_fused_batch_refuses_a_tv_state(imask):
+    plan = imask.Plan(dict(TV64.params(), mu=0.1, sigma=0.04, reg=1, tv_lambda=0.02))
+    _, b, _ = inputs.measurements(TV64, seed=0, noise="none")
+    s = plan.state(cuda(b), 1)
+    with pytest.raises(imask.ImaskError):
+        imask.Batch([s], fused=True)
+    s.close()

@@ -287,16 +287,24 @@ def test_fan512_iterates(imask, fan512):
 
 
 def test_fan512_autotuned_launch_configuration(imask, fan512):
-    # the benchmark's plan: back-projector splits measured at plan time
+    # the benchmark's plan: back-projector splits and projector strip heights
+    # measured at plan time; 12 iterations in one call run as graph replays of
+    # four iterations (the form the benchmark times), checked against the
+    # oracle at full size
     params, b, _, o = fan512
     plan = imask.Plan(dict(params, autotune=1))
     assert plan.info["autotuned"] == 1
     yv = np.random.default_rng(2).standard_normal(o.m)
     y = cuda(yv)
+    xv = np.random.default_rng(3).standard_normal(o.d)
+    x = cuda(xv)
     for ell in (1, 2):
         assert rel(host(plan.backproject(ell, y)), o.KT(ell, yv).ravel()) <= TOL_OP, ell
+        assert rel(host(plan.project(ell, x)), o.K(ell, xv).ravel()) <= TOL_OP, ell
     seed = 33
-    st, _ = o.run(b, seed, 6)
+    st, _ = o.run(b, seed, 12)
     s = plan.state(cuda(b), seed)
-    s.step(6)
+    s.step(12)
+    assert s.k == 12
     assert rel(host(s.get(s.X)), st["x"]) <= TOL_ITER
+    assert rel(host(s.get(s.Y)), st["y"]) <= TOL_ITER

@@ -112,3 +112,25 @@ def test_plan_bytes_estimate_bounds_the_plan(mods):
         plan = imask.Plan(dict(r.params, mu=0.3, sigma=0.03))
         assert serve.Server.plan_bytes_estimate(r.params) >= plan.info["plan_bytes"]
         plan.close()
+
+
+def test_served_results_match_the_oracle(mods):
+    # two requests served together (sharing the GPU in the loop), each against
+    # the FP64 oracle run with the plan's own mu and sigma on the same seed
+    from oracle import Oracle
+    imask, serve = mods
+    reqs = _requests(serve)[:2]
+    srv = serve.Server(budget_bytes=8 << 30, max_active=2, quantum=7)
+    st = srv.run(reqs)
+    srv.close()
+    assert st.completed == 2
+    for r in reqs:
+        plan = imask.Plan(dict(r.params, mu=0.0, sigma=serve.normalised_sigma(r.params["levels"]),
+                               power_iters=20))
+        info = plan.info
+        plan.close()
+        o = Oracle(**dict(r.params, mu=info["mu"], sigma=info["sigma"]))
+        ref, _ = o.run(r.b.astype(np.float64), r.seed, r.iters)
+        got = r.x.double().numpy()
+        err = np.linalg.norm(got - ref["x"]) / np.linalg.norm(ref["x"])
+        assert err <= 1e-4, (r.rid, err)
