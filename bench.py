@@ -769,6 +769,69 @@ def batch_oracle_check(imask, plans, probs, sinos, iters, n_check=3):
     return out
 
 
+def time_mixed_precision_fan512(imask, p, bt, info, iters, stream, x_plain, n_states=8,
+                                cpu_iters=8, with_oracle=True):
+    """The batched 16-bit form of the headline solve: n_states states whose
+    measurement-side tables are stored in binary16 / bfloat16 (fp32
+    arithmetic), advanced as one graph-captured batch, with the SM clocks of
+    the timed region; the first state's iterate after `iters` iterations
+    against the plain fp32 form (same seed), and, after cpu_iters
+    iterations, against the FP64 oracle with the same rounding and against
+    the oracle's exact (fp32-table-free) iteration."""
+    import torch
+    out = {}
+    exact = None
+    if with_oracle:
+        from oracle import Oracle
+        _, b, _ = inputs.measurements(p, seed=0)
+        o = Oracle(**dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
+        exact, _ = o.run(b.ravel(), 0, cpu_iters)
+    for name, fmt in (("fp16_tables", 2), ("bf16_tables", 1)):
+        plan = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"], storage=fmt))
+        warm = [plan.state(bt, 900 + i, stream=stream) for i in range(n_states)]
+        wb = imask.Batch(warm)
+        wb.step(4, stream=stream)
+        torch.cuda.synchronize()
+        wb.close()
+        for w in warm:
+            w.close()
+        states = [plan.state(bt, 950 + i, stream=stream) for i in range(n_states)]
+        batch = imask.Batch(states)
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            batch.step(iters, stream=stream)
+            e.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        t = a.elapsed_time(e) / 1e3
+        x0 = states[0].get(states[0].X, stream=stream)
+        torch.cuda.synchronize()
+        rel_plain = math.sqrt(imask.imask_rel_distance(x0, x_plain))
+        batch.close()
+        for s in states:
+            s.close()
+        rec = {"states": n_states, "storage": fmt, "solves_per_s": n_states / t, "seconds": t,
+               "rel_err_vs_plain_fp32": rel_plain, "clocks": clk,
+               "state_bytes": plan.info["state_bytes"],
+               "includes": "graph capture and instantiation"}
+        if with_oracle:
+            st_r, _, _ = o.run_variant(b.ravel(), 0, cpu_iters, storage=fmt)
+            st_e = exact
+            xg = plan.solve(bt, 0, cpu_iters, stream=stream)
+            torch.cuda.synchronize()
+            xg = xg.double().cpu().numpy()
+            rec["rel_err_vs_fp64_oracle"] = {
+                "iters": cpu_iters, "seed": 0,
+                "same_rounding": float(np.linalg.norm(xg - st_r["x"]) / np.linalg.norm(st_r["x"])),
+                "exact_iteration": float(np.linalg.norm(xg - st_e["x"]) / np.linalg.norm(st_e["x"]))}
+        plan.close()
+        out[name] = rec
+    return out
+
+
 def time_batch_fan512(imask, p, bt, info, iters, stream, n_states=8):
     """n_states copies of the headline solve advanced as one batch, with one
     graph branch per state and fused (one launch of each kernel per iteration
@@ -1101,8 +1164,19 @@ def run_ours(args):
     # ---- the other iteration variants on the same workload (short runs) ----
     variants = None
     if not args.no_variants:
+        plain_ref = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
         variants = time_variants(imask, p, bt, info, args.iters, stream, flush, x)
         variants["batch_fan512"] = time_batch_fan512(imask, p, bt, info, args.iters, stream)
+        # the spec comparison: the batched 16-bit form against the plain
+        # fp32 form (the headline value) at the same seed
+        with torch.cuda.stream(stream):
+            x_ref = plain_ref.solve(bt, 950, args.iters, stream=stream)
+        torch.cuda.synchronize()
+        mp = time_mixed_precision_fan512(imask, p, bt, info, args.iters, stream, x_ref,
+                                         with_oracle=rank == 0 and not args.no_cpu_baseline,
+                                         cpu_iters=args.cpu_iters)
+        mp["plain_fp32_solves_per_s"] = value
+        variants["mixed_precision_fan512"] = mp
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None

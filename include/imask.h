@@ -88,11 +88,16 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               last refresh (n^2 + sum_{l>=1} (n/2^l)^2 floats; the remark
  *               after Alg. 3), the projector then applies K_l to the
  *               difference.  Same iterates up to rounding.
- *  storage      format of the measurement-side tables psi_l (dual_tables 0),
- *               the largest arrays of a solve: 0 fp32, 1 bfloat16, 2 binary16
- *               (round to nearest even on store; all arithmetic in fp32; the
- *               running mean follows the stored values).  Rounded tables move
- *               the fixed point by about the format's precision;
+ *  storage      format of the SAGA tables of Alg. 1: the measurement-side
+ *               tables psi_l (dual_tables 0), the largest arrays of a solve,
+ *               and the image-side tables phi_l (level 0 on the full grid,
+ *               levels >= 1 on their own grids): 0 fp32, 1 bfloat16,
+ *               2 binary16 (round to nearest even on store; all arithmetic in
+ *               fp32, the projector and back-projector accumulating in fp32;
+ *               xi and zeta take the refreshed value, the running means move
+ *               by the stored value's change, so they stay the p-weighted
+ *               sums of the stored tables).  Rounded tables move the fixed
+ *               point by about the format's precision;
  *               imask_state_set_storage(state, 0, ...) switches a state to
  *               fp32 tables for a refinement sweep.
  *  draws        0: one level per iteration (Alg. 1); 1: the primal level
@@ -294,12 +299,12 @@ imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
 int64_t imask_state_checkpoint_bytes(imask_state_t state);
 imask_status imask_state_save(imask_state_t state, void *dst_dev, void *stream);
 imask_status imask_state_load(imask_state_t state, const void *src_dev, void *stream);
-/* Converts the state's measurement-side tables to another storage format
- * (0 fp32, 1 bf16, 2 fp16) and re-forms their running mean from the converted
- * tables; later iterations use the new format (widening to fp32 is exact: the
- * refinement sweep of a 16-bit solve).  Allocates the new tables with
- * cudaMallocAsync on stream.  INVALID for a state without such tables unless
- * storage is 0.  Graphs captured for the state (its own, or a batch's) are
+/* Converts the state's SAGA tables (measurement- and image-side) to another
+ * storage format (0 fp32, 1 bf16, 2 fp16) and re-forms their running means
+ * from the converted tables; later iterations use the new format (widening to
+ * fp32 is exact: the refinement sweep of a 16-bit solve).  Allocates the new
+ * tables with cudaMallocAsync on stream.  INVALID for a snapshot-form state
+ * (no measurement-side tables) unless storage is 0.  Graphs captured for the state (its own, or a batch's) are
  * captured again at their next step.  Not to be called while a batch holding
  * the state is being stepped from another thread. */
 imask_status imask_state_set_storage(imask_state_t state, int32_t storage, void *stream);

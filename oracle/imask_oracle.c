@@ -708,8 +708,9 @@ int32_t orc_imask_variant_run(const orc_desc *d, const orc_variant *var, const d
       for (int64_t p = 0; p < np; ++p) xbar[p] = xn[p] + var->theta * (xn[p] - x[p]);
     memcpy(x, xn, sizeof(double) * (size_t)np);
     memcpy(y, yn, sizeof(double) * (size_t)m);
-    /* table updates */
-    memcpy(phi + (int64_t)lp * np, phi_new, sizeof(double) * (size_t)np);
+    /* table updates (16-bit tables: the refreshed image-side entry is stored
+     * rounded too; xi above took the refreshed value itself) */
+    for (int64_t p = 0; p < np; ++p) phi[(int64_t)lp * np + p] = store_table(var, phi_new[p]);
     if (var->snapshots) {
       for (int64_t q = 0; q < m; ++q) psi_mean[q] += prob(d, ld) * delta[q];
       memcpy(snap + (int64_t)ld * np, u, sizeof(double) * (size_t)np);

@@ -96,7 +96,8 @@ typedef struct {
   double theta;        /* Alg. 7 extrapolation weight */
   int32_t snapshots;   /* 1: dual tables kept as projector-input snapshots */
   int32_t independent; /* 1: primal level drawn from the stream of orc_primal_seed(seed) */
-  int32_t storage;     /* measurement-side tables held as 0 FP64, 1 bfloat16, 2 binary16 */
+  int32_t storage;     /* SAGA tables (measurement- and image-side) held as 0 FP64,
+                          1 bfloat16, 2 binary16 */
 } orc_variant;
 
 /* Round-to-nearest-even of v to a binary format with `bits` significant bits

@@ -154,9 +154,14 @@ struct imask_state_s {
   void *psi = nullptr;        // measurement-side tables (format psi_fmt), or nullptr
   int psi_fmt = 0;            // 0 float, 1 bfloat16, 2 binary16
   void *psi_block = nullptr;  // separate table allocation after a storage change
+  void *phi_block = nullptr;  // idem for the image-side tables
+  int phi_fmt = 0;            // image-side tables: 0 float, 1 bfloat16, 2 binary16
   float *x = nullptr, *y[2] = {nullptr, nullptr}, *b = nullptr,
-        *psi_mean = nullptr, *phi0 = nullptr, *phic = nullptr, *phi_mean = nullptr, *g = nullptr,
+        *psi_mean = nullptr, *phi_mean = nullptr, *g = nullptr,
         *tv = nullptr, *x_prev = nullptr;
+  // image-side tables: level 0 at phi0 (n*n entries), level ell >= 1 on its
+  // own grid at entry phic_off[ell] of phic (phic == phi0: one region)
+  void *phi0 = nullptr, *phic = nullptr;
   long long phic_off[IMASK_MAX_LEVELS] = {0};
   SnapArgs snap{};   // dual_tables = 1: sketched projector inputs per level
   // padded sketch images: the projector of iteration k reads pads[k % 2], the
@@ -871,7 +876,10 @@ StateLayout state_layout(const imask_plan_s *p) {
   const size_t esize = p->desc.storage != 0 ? 2 : 4;   // bytes per table entry
   L.psi = snapshots ? 0 : cv.take((m * r * esize + 3) / 4);
   L.psim = cv.take(m);
-  L.phi0 = cv.take(d);
+  // image-side tables, level 0 and then the coarse levels, in one region
+  size_t phi_entries = d;
+  for (int l = 1; l < r; ++l) phi_entries += (size_t)p->dp.lg[l + 1].nl * p->dp.lg[l + 1].nl;
+  L.phi0 = cv.take((phi_entries * esize + 3) / 4);
   L.phim = cv.take(d);
   if (snapshots)
     for (int l = 0; l < r; ++l) {
@@ -882,10 +890,6 @@ StateLayout state_layout(const imask_plan_s *p) {
   L.kdev = cv.take(2);   // one 64-bit counter
   L.g = cv.take(p->gcap);
   L.g2 = seq ? 0 : cv.take(p->gcap);
-  for (int l = 1; l < r; ++l) {
-    const size_t nl = (size_t)p->dp.lg[l + 1].nl;
-    L.phic[l] = cv.take(nl * nl);
-  }
   L.tv = p->desc.reg != 0 ? cv.take(5 * d) : 0;
   for (int li = 1; li <= r; ++li) {
     L.T[li] = cv.take(pad_floats(p->dp.lg[li]));
@@ -1560,7 +1564,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   const size_t o_x = L.x, o_y0 = L.y0, o_y1 = L.y1, o_b = L.b, o_psi = L.psi, o_psim = L.psim,
                o_phi0 = L.phi0, o_phim = L.phim, o_xprev = L.xprev, o_kdev = L.kdev, o_g = L.g,
                o_tv = L.tv;
-  const size_t *o_snap = L.snap, *o_phic = L.phic, *o_T = L.T, *o_R = L.R;
+  const size_t *o_snap = L.snap, *o_T = L.T, *o_R = L.R;
   Carve cv;
   cv.off = L.total;
   void *mem = nullptr;
@@ -1585,12 +1589,19 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
   }
   s->x_prev = o_xprev ? B + o_xprev : nullptr;
   s->k_dev = (long long *)(B + o_kdev);
-  s->phi0 = B + o_phi0;
+  s->phi0 = (void *)(B + o_phi0);
+  s->phi_fmt = p->desc.storage;
   s->phi_mean = B + o_phim;
   s->g = B + o_g;
   s->g2 = L.g2 ? B + L.g2 : s->g;
-  s->phic = B;
-  for (int l = 1; l < r; ++l) s->phic_off[l] = (long long)o_phic[l];
+  s->phic = s->phi0;
+  {
+    long long off = (long long)p->dp.d;
+    for (int l = 1; l < r; ++l) {
+      s->phic_off[l] = off;
+      off += (long long)p->dp.lg[l + 1].nl * p->dp.lg[l + 1].nl;
+    }
+  }
   s->tv = p->desc.reg != 0 ? B + o_tv : nullptr;
   for (int li = 1; li <= r; ++li) {
     s->pads[0].T[li] = B + o_T[li];
@@ -1714,6 +1725,7 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   A.phi0 = s->phi0;
   A.phic = s->phic;
   for (int l = 0; l < IMASK_MAX_LEVELS; ++l) A.phic_off[l] = s->phic_off[l];
+  A.phi_fmt = s->phi_fmt;
   A.phi_mean = s->phi_mean;
   A.tau = tau;
   A.inv_1ps = inv_1ps;
@@ -1851,6 +1863,7 @@ std::vector<FusedSlice> fused_records(const imask_batch_s *b, int unroll) {
       R.A.phi0 = s->phi0;
       R.A.phic = s->phic;
       for (int l = 0; l < IMASK_MAX_LEVELS; ++l) R.A.phic_off[l] = s->phic_off[l];
+      R.A.phi_fmt = s->phi_fmt;
       R.A.phi_mean = s->phi_mean;
       R.A.tau = (float)(p->sigma / p->mu);
       R.A.inv_1ps = (float)(1.0 / (1.0 + p->sigma));
@@ -2217,7 +2230,7 @@ int64_t imask_state_checkpoint_bytes(imask_state_t s) {
 
 imask_status imask_state_save(imask_state_t s, void *dst, void *stream) {
   if (!s || !dst) return fail(IMASK_ERR_INVALID, "NULL argument");
-  if (s->psi_block)
+  if (s->psi_block || s->phi_block)
     return fail(IMASK_ERR_INVALID, "a state whose tables changed storage cannot be saved");
   cudaStream_t st = (cudaStream_t)stream;
   CheckpointHeader h{};
@@ -2243,7 +2256,7 @@ imask_status imask_state_save(imask_state_t s, void *dst, void *stream) {
 
 imask_status imask_state_load(imask_state_t s, const void *src, void *stream) {
   if (!s || !src) return fail(IMASK_ERR_INVALID, "NULL argument");
-  if (s->psi_block)
+  if (s->psi_block || s->phi_block)
     return fail(IMASK_ERR_INVALID, "a state whose tables changed storage cannot be loaded");
   cudaStream_t st = (cudaStream_t)stream;
   CheckpointHeader h{};
@@ -2274,34 +2287,53 @@ imask_status imask_state_load(imask_state_t s, const void *src, void *stream) {
 imask_status imask_state_set_storage(imask_state_t s, int32_t storage, void *stream) {
   if (!s) return fail(IMASK_ERR_INVALID, "NULL state");
   if (storage < 0 || storage > 2) return fail(IMASK_ERR_INVALID, "storage must be 0, 1 or 2");
-  if (!s->psi || storage == s->psi_fmt) {
-    if (!s->psi && storage != 0)
-      return fail(IMASK_ERR_INVALID, "the snapshot form keeps no measurement-side tables");
-    return IMASK_OK;
-  }
+  if (!s->psi && storage != 0)
+    return fail(IMASK_ERR_INVALID, "the snapshot form keeps no measurement-side tables");
+  const bool psi_change = s->psi && storage != s->psi_fmt;
+  const bool phi_change = storage != s->phi_fmt;
+  if (!psi_change && !phi_change) return IMASK_OK;
   cudaStream_t st = (cudaStream_t)stream;
   imask_status rc = state_use_stream(s, st);
   if (rc != IMASK_OK) return rc;
   const imask_plan_s *p = s->plan;
-  const long long n = (long long)p->dp.m * p->desc.levels;
-  void *mem = nullptr;
-  CK(cudaMallocAsync(&mem, (size_t)n * (storage != 0 ? 2 : 4), st), "cudaMallocAsync(tables)");
-  cudaError_t e = launch_convert(n, s->psi, s->psi_fmt, mem, storage, st);
+  const size_t esz = storage != 0 ? 2 : 4;
+  void *psi_mem = nullptr, *phi_mem = nullptr;
+  cudaError_t e = cudaSuccess;
+  // measurement-side tables, and their running mean re-formed from the
+  // converted tables so that it stays their p-weighted sum
+  if (psi_change) {
+    const long long n = (long long)p->dp.m * p->desc.levels;
+    if ((e = cudaMallocAsync(&psi_mem, (size_t)n * esz, st)) == cudaSuccess &&
+        (e = launch_convert(n, s->psi, s->psi_fmt, psi_mem, storage, st)) == cudaSuccess)
+      e = launch_table_mean(p->dp, psi_mem, storage, s->psi_mean, st);
+  }
+  // image-side tables (level 0 and the coarse levels, one region), likewise
+  if (e == cudaSuccess && phi_change) {
+    long long n = (long long)p->dp.d;
+    for (int l = 1; l < p->desc.levels; ++l)
+      n += (long long)p->dp.lg[l + 1].nl * p->dp.lg[l + 1].nl;
+    if ((e = cudaMallocAsync(&phi_mem, (size_t)n * esz, st)) == cudaSuccess &&
+        (e = launch_convert(n, s->phi0, s->phi_fmt, phi_mem, storage, st)) == cudaSuccess)
+      e = launch_phi_mean(p->dp, phi_mem, phi_mem, s->phic_off, storage, s->phi_mean, st);
+  }
   if (e != cudaSuccess) {
-    cudaFreeAsync(mem, st);
+    if (psi_mem) cudaFreeAsync(psi_mem, st);
+    if (phi_mem) cudaFreeAsync(phi_mem, st);
     return cuda_fail(e, "table conversion");
   }
-  // the running mean is re-formed from the converted tables so that it stays
-  // their p-weighted sum
-  e = launch_table_mean(p->dp, mem, storage, s->psi_mean, st);
-  if (e != cudaSuccess) {
-    cudaFreeAsync(mem, st);
-    return cuda_fail(e, "table mean");
+  if (psi_change) {
+    if (s->psi_block) cudaFreeAsync(s->psi_block, st);
+    s->psi_block = psi_mem;
+    s->psi = psi_mem;
+    s->psi_fmt = storage;
   }
-  if (s->psi_block) cudaFreeAsync(s->psi_block, st);
-  s->psi_block = mem;
-  s->psi = mem;
-  s->psi_fmt = storage;
+  if (phi_change) {
+    if (s->phi_block) cudaFreeAsync(s->phi_block, st);
+    s->phi_block = phi_mem;
+    s->phi0 = phi_mem;
+    s->phic = phi_mem;
+    s->phi_fmt = storage;
+  }
   s->stream = st;
   s->gen += 1;   // graphs captured with the old tables are captured again
   return IMASK_OK;
@@ -2318,6 +2350,7 @@ imask_status imask_state_destroy(imask_state_t s) {
                         s->ev_order})
     if (ev) cudaEventDestroy(ev);
   if (s->psi_block) cudaFreeAsync(s->psi_block, s->stream);
+  if (s->phi_block) cudaFreeAsync(s->phi_block, s->stream);
   if (s->block) cudaFreeAsync(s->block, s->stream);
   delete s;
   return IMASK_OK;

@@ -140,9 +140,10 @@ struct DualArgs {
 struct PrimalArgs {
   const float *g;    // R_ell^T y on the level grid as bp_vgo partial sums
   float *x;          // iterate, updated in place
-  float *phi0;       // table entry of level 0 (n*n)
-  float *phic;       // tables of levels >= 1, stored on their own grids
-  long long phic_off[IMASK_MAX_LEVELS];
+  void *phi0;        // table entry of level 0 (n*n)
+  void *phic;        // tables of levels >= 1, stored on their own grids, level
+  long long phic_off[IMASK_MAX_LEVELS];   // ell at entry phic_off[ell]
+  int phi_fmt;       // table entries: 0 float, 1 bfloat16, 2 binary16
   float *phi_mean;   // sum_l p_l phi_l (n*n)
   float tau;         // sigma / mu
   float inv_1ps;     // 1 / (1 + sigma)
@@ -230,6 +231,11 @@ cudaError_t launch_probe_smem(int blocks, int iters, int rmw, float *sink, cudaS
 // psi_mean = sum_l p_l psi_l over the level tables
 cudaError_t launch_table_mean(const DevPlan &P, const void *psi, int fmt, float *psi_mean,
                               cudaStream_t st);
+// phi_mean = sum_l p_l phi_l on the fine grid (level ell >= 1 replicated from
+// its grid), phi0 / phic as in PrimalArgs
+cudaError_t launch_phi_mean(const DevPlan &P, const void *phi0, const void *phic,
+                            const long long *phic_off, int fmt, float *phi_mean,
+                            cudaStream_t st);
 cudaError_t launch_scale(long long n, float alpha, float *x, cudaStream_t st);
 cudaError_t launch_fill(long long n, float v, float *x, cudaStream_t st);
 cudaError_t launch_copy(long long n, const float *x, float *y, cudaStream_t st);

@@ -163,6 +163,29 @@ __device__ __forceinline__ void block_origin(float a_hi, float a_lo, float t_hi,
   r = (S - Sr) + (e1 + E + fmaf(a_lo, s, fmaf(cc, t_lo, -0.5f)));
 }
 
+// Table entries in one of the storage formats (0 float, 1 bfloat16, 2 binary16):
+// read as float; a store rounds to nearest even and returns the stored value.
+__device__ __forceinline__ float tab_load(const void *t, size_t i, int fmt) {
+  if (fmt == 1) return __bfloat162float(((const __nv_bfloat16 *)t)[i]);
+  if (fmt == 2) return __half2float(((const __half *)t)[i]);
+  return ((const float *)t)[i];
+}
+
+__device__ __forceinline__ float tab_store(void *t, size_t i, float v, int fmt) {
+  if (fmt == 1) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    ((__nv_bfloat16 *)t)[i] = h;
+    return __bfloat162float(h);
+  }
+  if (fmt == 2) {
+    const __half h = __float2half_rn(v);
+    ((__half *)t)[i] = h;
+    return __half2float(h);
+  }
+  ((float *)t)[i] = v;
+  return v;
+}
+
 // ---------------------------------------------------------------------------------
 // Forward projector (Joseph) with the fused dual epilogue.
 //
@@ -938,10 +961,12 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
   const int ts = P.upd_tile, ntx = P.n / ts;
   float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
   float *dc = pyr + ts * ts / 2 + 4;
+  float *dm = dc + ts * ts / 4 + 4;
   const int ti0 = (bid / ntx) * ts, tj0 = (bid % ntx) * ts;
   const int n = P.n;
   const int ell = sel_level_x(P, sel);
   const float pl = P.probs[ell];
+  const int fmt = A.phi_fmt;
 
   // A thread's pixels go in groups of kUpdPix: every load of a group is
   // issued before its first store (a store to one pixel could alias the next
@@ -960,7 +985,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
       const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
       pmv[u] = A.phi_mean[gp];
       xov[u] = A.x[gp];
-      if (ell < 1) ph0[u] = A.phi0[gp];
+      if (ell < 1) ph0[u] = tab_load(A.phi0, gp, fmt);
     }
   };
   if (one_group) load_group(threadIdx.x);
@@ -970,14 +995,19 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
     const LevelGeom G = P.lg[ell + 1];
     cs = ts >> ell;
     const int I0 = ti0 >> ell, J0 = tj0 >> ell;
-    float *phic = A.phic + A.phic_off[ell];
+    const long long off = A.phic_off[ell];
     const float inv4l = G.inv2l * G.inv2l;
     coarse_planes_sum(A.g, 2 * G.bp_vgo, G.nl, I0, J0, cs, dc);
+    // xi takes the refreshed value's change, the running mean the stored
+    // (rounded, with 16-bit tables) value's change, so that the mean stays the
+    // p-weighted sum of the stored tables
     for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
-      const size_t gi = (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
+      const size_t gi = (size_t)off + (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
       const float cnew = dc[p] * inv4l;
-      dc[p] = cnew - phic[gi];
-      phic[gi] = cnew;
+      const float old = tab_load(A.phic, gi, fmt);
+      const float stored = tab_store(A.phic, gi, cnew, fmt);
+      dc[p] = cnew - old;
+      dm[p] = stored - old;
     }
     __syncthreads();
   } else {
@@ -1025,19 +1055,20 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
       if (p >= ts * ts) continue;
       const int li = p / ts, lj = p % ts;
       const size_t gp = (size_t)(ti0 + li) * n + tj0 + lj;
-      float delta;
+      float delta, dmean;
       if (ell >= 1) {
         delta = dc[(li >> ell) * cs + (lj >> ell)];
+        dmean = dm[(li >> ell) * cs + (lj >> ell)];
       } else {
         const float s0 = compensate_px(P, aux[p], pyr, ts, li, lj);
         delta = s0 - ph0[u];
-        A.phi0[gp] = s0;
+        dmean = tab_store(A.phi0, gp, s0, fmt) - ph0[u];
       }
       const float pm = pmv[u];
       const float xi = delta + pm;
       const float xo = xov[u];
       const float v = fmaf(-A.tau, xi, xo);
-      A.phi_mean[gp] = fmaf(pl, delta, pm);
+      A.phi_mean[gp] = fmaf(pl, dmean, pm);
       const float xn = A.prox_in_place ? v * A.inv_1ps : v;
       A.x[gp] = xn;
       if (A.x_prev) A.x_prev[gp] = xo;
@@ -1323,6 +1354,24 @@ __global__ void k_table_mean(DevPlan P, const void *psi, int fmt, float *psi_mea
   }
 }
 
+// phi_mean[p] = sum_l p_l phi_l[p], levels in order, level ell >= 1 read at
+// the block of p on its own grid
+__global__ void k_phi_mean(DevPlan P, const void *phi0, const void *phic, PrimalArgs offs,
+                           int fmt, float *phi_mean) {
+  const long long d = (long long)P.n * P.n;
+  for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < d;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(q / P.n), j = (int)(q % P.n);
+    float s = P.probs[0] * tab_load(phi0, (size_t)q, fmt);
+    for (int l = 1; l < P.levels; ++l) {
+      const int nl = P.n >> l;
+      const size_t gi = (size_t)offs.phic_off[l] + (size_t)(i >> l) * nl + (j >> l);
+      s = fmaf(P.probs[l], tab_load(phic, gi, fmt), s);
+    }
+    phi_mean[q] = s;
+  }
+}
+
 __global__ void k_counter(long long *k, long long delta, int set_value) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *k = set_value ? delta : *k + delta;
 }
@@ -1427,7 +1476,7 @@ inline int grid_for(long long n, int threads) {
 
 inline int upd_smem_bytes(const DevPlan &P) {
   const int ts = P.upd_tile;
-  return (int)sizeof(float) * (ts * ts * 2 + ts * ts / 2 + 4 + ts * ts / 4 + 4);
+  return (int)sizeof(float) * (ts * ts * 2 + ts * ts / 2 + 4 + 2 * (ts * ts / 4 + 4));
 }
 
 }  // namespace
@@ -1724,6 +1773,17 @@ cudaError_t launch_table_mean(const DevPlan &P, const void *psi, int fmt, float 
                               cudaStream_t st) {
   count_launch();
   k_table_mean<<<grid_for(P.m, 256), 256, 0, st>>>(P, psi, fmt, psi_mean);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi_mean(const DevPlan &P, const void *phi0, const void *phic,
+                            const long long *phic_off, int fmt, float *phi_mean,
+                            cudaStream_t st) {
+  PrimalArgs offs{};
+  for (int l = 0; l < IMASK_MAX_LEVELS; ++l) offs.phic_off[l] = phic_off[l];
+  count_launch();
+  k_phi_mean<<<grid_for((long long)P.n * P.n, 256), 256, 0, st>>>(P, phi0, phic, offs, fmt,
+                                                                 phi_mean);
   return cudaGetLastError();
 }
 

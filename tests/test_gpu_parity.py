@@ -296,7 +296,7 @@ def test_fan512_autotuned_launch_configuration(imask, fan512):
     assert plan.info["autotuned"] == 1
     yv = np.random.default_rng(2).standard_normal(o.m)
     y = cuda(yv)
-    xv = np.random.default_rng(3).standard_normal(o.d)
+    xv = np.random.default_rng(3).standard_normal(o.n * o.n)
     x = cuda(xv)
     for ell in (1, 2):
         assert rel(host(plan.backproject(ell, y)), o.KT(ell, yv).ravel()) <= TOL_OP, ell

@@ -1,5 +1,5 @@
-"""16-bit measurement-side tables (bfloat16 / binary16) against the oracle's
-rounded-table iteration, the refinement sweep to fp32 tables, and the memory
+"""16-bit SAGA tables (bfloat16 / binary16, measurement- and image-side)
+against the oracle's rounded-table iteration, the refinement sweep to fp32 tables, and the memory
 they save.
 
 Tolerances (relative L2 of the iterates): binary16 1e-4 as for fp32; bfloat16
@@ -80,6 +80,10 @@ def test_refinement_sweep(imask, fmt):
     m = o.m
     psi_mean = sum(pr[l] * st["psi"][l * m:(l + 1) * m] for l in range(o.r))
     assert rel(s.get(s.PSI_MEAN).double().cpu().numpy(), psi_mean) <= TOL[fmt]
+    # and so is the image-side running mean of the image-side tables
+    d = o.n * o.n
+    phi_mean = sum(pr[l] * st["phi"][l * d:(l + 1) * d] for l in range(o.r))
+    assert rel(s.get(s.PHI_MEAN).double().cpu().numpy(), phi_mean) <= TOL[fmt]
 
 
 def test_16bit_tables_save_memory(imask):
@@ -87,4 +91,7 @@ def test_16bit_tables_save_memory(imask):
     b32 = imask.Plan(base).info["state_bytes"]
     b16 = imask.Plan(dict(base, storage=1)).info["state_bytes"]
     m, r = FAN64.n_angles * FAN64.n_det, FAN64.levels
-    assert b32 - b16 >= 2 * m * r - 256
+    # both table families in half the bytes: r m measurement-side entries and
+    # n^2 + sum_{l>=1} (n / 2^l)^2 image-side entries
+    d_tab = sum((FAN64.n >> l) ** 2 for l in range(r))
+    assert b32 - b16 >= 2 * m * r + 2 * d_tab - 256
