@@ -976,16 +976,35 @@ def run_precision(args):
 # ---------------------------------------------------------------------------------
 # serving: Poisson arrivals, continuous batching under a device-memory budget
 # ---------------------------------------------------------------------------------
+def serving_mean_samples(n_draws: int = 20000, n_geometries: int = 0) -> float:
+    """Mean ray-samples per request of the serving mix (Monte Carlo over the
+    request generator; with a geometry fleet, over the fleet the timed run
+    draws)."""
+    if n_geometries > 0:
+        draws = inputs.serving_requests(n_draws / 10.0, 10.0, seed=0,
+                                        n_geometries=n_geometries)
+    else:
+        draws = inputs.serving_requests(n_draws / 10.0, 10.0, seed=12345)
+    return float(np.mean([expected_samples_per_solve(p, it) for _, p, it, _ in draws]))
+
+
 def run_serve(args):
     import torch
     from paper_2412_10249_gb300 import build as pkg_build
     pkg_build.build()
     from paper_2412_10249_gb300 import serve
+    rate = args.serve_rate
+    mean_samples = serving_mean_samples(n_geometries=args.serve_geometries)
+    if args.serve_load > 0:
+        # arrivals at a fraction of one GPU's capacity: the request mix's mean
+        # ray-samples per solve against the measured solve rate of the GPU
+        # (G ray-samples/s of the 512x512 fan workload)
+        rate = args.serve_load * args.serve_capacity_gsps * 1e9 / mean_samples
     reqs = []
     problems = {}
     offered = 0.0
-    for i, (t, p, iters, seed) in enumerate(inputs.serving_requests(args.serve_seconds,
-                                                                     args.serve_rate, seed=0)):
+    for i, (t, p, iters, seed) in enumerate(inputs.serving_requests(
+            args.serve_seconds, rate, seed=0, n_geometries=args.serve_geometries)):
         problems[i] = p
         def make_b(p=p, seed=seed):
             return inputs.poisson_log(inputs.disk_sinogram(p), 1e4, seed)
@@ -997,7 +1016,12 @@ def run_serve(args):
                        quantum=10, power_iters=20)
     clocks = ClockSampler(0)
     clocks.start()
-    st = srv.run(reqs, duration=args.serve_seconds, drain=False)
+    # at a load below capacity every admitted request is served to the end
+    # (latencies of all of them); at the overloaded rate the window closes
+    drain = args.serve_load > 0
+    t0 = time.perf_counter()
+    st = srv.run(reqs, duration=args.serve_seconds, drain=drain)
+    wall = time.perf_counter() - t0
     clk = clocks.stop()
     done = [r for r in reqs if r.status == "done"]
     achieved = sum(expected_samples_per_solve(problems[r.rid], r.iters) for r in done)
@@ -1008,11 +1032,15 @@ def run_serve(args):
                               for a in srv.active)
     lat = np.array(st.latencies) * 1e3
     wait = np.array(st.waits) * 1e3
-    T = args.serve_seconds
+    T = wall if drain else args.serve_seconds
     line = {"metric": "served ImaSk solves/s (Poisson arrivals, continuous batching)",
             "unit": "solves/s", "value": len(done) / T, "seconds": T,
-            "offered": {"requests": len(reqs), "rate_per_s": args.serve_rate,
-                        "gsamples_per_s": offered / T / 1e9},
+            "arrival_window_s": args.serve_seconds, "drained": drain,
+            "offered": {"requests": len(reqs), "rate_per_s": rate,
+                        "gsamples_per_s": offered / T / 1e9,
+                        "load": (rate * mean_samples / (args.serve_capacity_gsps * 1e9)),
+                        "mix_mean_gsamples_per_request": mean_samples / 1e9,
+                        "capacity_gsamples_per_s": args.serve_capacity_gsps},
             "achieved_gsamples_per_s": achieved / T / 1e9,
             "launched_gsamples_per_s": launched / T / 1e9,
             "p50_ms": float(np.percentile(lat, 50)) if lat.size else None,
@@ -1030,7 +1058,8 @@ def run_serve(args):
                                    "[128, 2048], views [180, 2048], bins 1.5 x side, fan beam, "
                                    "K in [100, 1000]; centred-disk sinograms with Poisson "
                                    "noise", "budget_gb": args.serve_budget_gb,
-                       "slots": args.serve_slots, "queue": args.serve_queue, "quantum": 10}}
+                       "slots": args.serve_slots, "queue": args.serve_queue, "quantum": 10,
+                       "geometries": args.serve_geometries or "one per request"}}
     srv.close()
     print(json.dumps(line))
     return 0
@@ -1283,6 +1312,12 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=64.0)
     ap.add_argument("--serve-slots", type=int, default=16)
     ap.add_argument("--serve-queue", type=int, default=64)
+    ap.add_argument("--serve-load", type=float, default=0.0,
+                    help="arrival rate as this fraction of one GPU's capacity (else --serve-rate)")
+    ap.add_argument("--serve-geometries", type=int, default=0,
+                    help="requests share this many geometries (0: every request its own)")
+    ap.add_argument("--serve-capacity-gsps", type=float, default=1500.0,
+                    help="G ray-samples/s one GPU sustains (the headline workload's rate)")
     ap.add_argument("--profile-period", type=int, default=32,
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)

@@ -19,7 +19,9 @@
  * (x_c, y_i) = (-W/2 + (c + 1/2) h, -W/2 + (i + 1/2) h) with h = W / n.
  * Sinograms are row-major float[n_angles][n_det].  The projector is Joseph's
  * method (linear interpolation along the major axis of every ray); the
- * back-projector is its exact transpose, computed pixel by pixel.
+ * back-projector is its exact transpose: every pixel's owner thread applies
+ * the rays crossing its tile into private shared-memory accumulators, no
+ * atomics, partial images added in a fixed order.
  *
  * Conventions.
  *  - Pointers named *_dev are device pointers owned by the caller; the library
@@ -191,7 +193,10 @@ imask_status imask_project(imask_plan_t plan, int32_t level, const float *x_dev,
                            float *sino_dev, void *stream);
 
 /* img_dev[n*n] = K_level^T y_dev: level >= 1: 4^-level T^*(R_level^T y);
- * level 0: S_r (K^T y); level -1: K^T y.  Pixel-driven gather (no atomics).
+ * level 0: S_r (K^T y); level -1: K^T y.  Owner-computes: each thread owns a
+ * line segment of a tile and applies the rays crossing the tile to it in
+ * private shared-memory accumulators (no atomics); the partial images of the
+ * view groups are added in a fixed order (deterministic).
  * Allocates its coarse temporary with cudaMallocAsync on stream. */
 imask_status imask_backproject(imask_plan_t plan, int32_t level, const float *y_dev,
                                float *img_dev, void *stream);
@@ -222,7 +227,11 @@ imask_status imask_levels(imask_plan_t plan, uint64_t seed, int64_t k0, int64_t 
                           int32_t *out_dev, void *stream);
 
 /* Creates the state of one solve (Alg. 1 defaults: x = y = 0, tables 0, k = 0)
- * and copies b_dev[n_angles*n_det].  Allocates with cudaMallocAsync on stream. */
+ * and copies b_dev[n_angles*n_det] (sinogram order, view-major).  Inside the
+ * state the measurement-space vectors (b, y, the tables psi_l and their mean)
+ * are kept in the plan's ray-list order, which the projector's epilogue
+ * reads and writes without an index; imask_state_get returns them in
+ * sinogram order.  Allocates with cudaMallocAsync on stream. */
 imask_status imask_state_create(imask_plan_t plan, const float *b_dev, uint64_t seed,
                                 imask_state_t *state_out, void *stream);
 /* Advances the state by n_iters iterations (Alg. 1, or the plan's variant) on
@@ -278,7 +287,8 @@ imask_status imask_batch_destroy(imask_batch_t batch);
 /* Iteration counter k of the state (host value, no synchronisation). */
 int64_t imask_state_iteration(imask_state_t state);
 /* Copies a part of the state into dst_dev (float): what = 0 x[n*n], 1 y[m],
- * 2 the running mean sum_l p_l phi_l [n*n], 3 the running mean sum_l p_l psi_l [m]. */
+ * 2 the running mean sum_l p_l phi_l [n*n], 3 the running mean sum_l p_l psi_l [m]
+ * (the measurement-space parts 1 and 3 in sinogram order). */
 imask_status imask_state_get(imask_state_t state, int32_t what, float *dst_dev, void *stream);
 imask_status imask_state_get_x(imask_state_t state, float *x_dev, void *stream);
 /* Checkpoints.  imask_state_save writes the whole state (iterates, tables,

@@ -206,6 +206,7 @@ struct imask_batch_s {
   int *d_bp_start = nullptr;           // [unroll][n + 1] back-projector item offsets
   int *d_bp_counter = nullptr;         // [unroll] back-projector work counters
   int fp_total = 0, upd_total = 0, upd_smem = 0, bp_grid = 0, nv_cap = 0;
+  int bp_max_items = 0;   // one back-projector CTA per item (0: resident CTAs)
   long long bp_smem = 0;
   bool any_seq = false;                // some state runs Alg. 7
   cudaStream_t f_fp = nullptr, f_bp = nullptr;   // capture branches of the fused launches
@@ -486,7 +487,7 @@ imask_status apply_KT(const imask_plan_s *p, int ell, const float *y, float *img
   const LevelSel sel = fixed_level(ell);
   {
     ProfScope ps(1, ell < 0 ? 0 : ell, st);
-    CK(launch_bp(p->dp, sel, y, s.g, p->d_err, st), "back-projector launch");
+    CK(launch_bp(p->dp, sel, y, 0, s.g, p->d_err, st), "back-projector launch");
   }
   CK(launch_adjsketch(p->dp, ell, s.g, img, st), "adjoint sketch launch");
   return IMASK_OK;
@@ -1610,8 +1611,7 @@ imask_status imask_state_create(imask_plan_t p, const float *b_dev, uint64_t see
     s->pads[1].R[li] = L.R2[li] ? B + L.R2[li] : s->pads[0].R[li];
   }
   if ((e = cudaMemsetAsync(mem, 0, cv.off * sizeof(float), st)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(s->b, b_dev, m * sizeof(float), cudaMemcpyDeviceToDevice, st)) !=
-          cudaSuccess) {
+      (e = launch_sino_order(p->dp, b_dev, s->b, 1, st)) != cudaSuccess) {
     cudaFreeAsync(mem, st);
     delete s;
     return cuda_fail(e, "state init");
@@ -1712,7 +1712,7 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
   // primal half: Alg. 1 back-projects y^k, Alg. 7 the new y^{k+1}
   {
     ProfScope ps(1, lvl_x, sbp, prof);
-    CK(launch_bp(P, sel, seq ? s->y[1 - cur] : s->y[cur], g, p->d_err, sbp),
+    CK(launch_bp(P, sel, seq ? s->y[1 - cur] : s->y[cur], 1, g, p->d_err, sbp),
        "back-projector launch");
   }
   if (fork) {
@@ -1924,7 +1924,8 @@ imask_status batch_capture_fused(imask_batch_s *b, int unroll) {
     }
     if (pos >= 2 && (e = cudaStreamWaitEvent(b->f_bp, ev_upd[pos - 2], 0)) != cudaSuccess) break;
     if ((e = launch_bp_multi(r, n, b->d_bp_start + (size_t)pos * (n + 1), b->d_bp_counter + pos,
-                             b->nv_cap, b->bp_smem, b->bp_grid, b->f_bp)) != cudaSuccess)
+                             b->nv_cap, b->bp_smem, b->bp_grid, b->bp_max_items, b->f_bp)) !=
+        cudaSuccess)
       break;
     if ((e = cudaEventRecord(ev_bp[pos], b->f_bp)) != cudaSuccess) break;
     if ((e = cudaStreamWaitEvent(origin, ev_bp[pos], 0)) != cudaSuccess) break;
@@ -2089,6 +2090,10 @@ imask_status imask_batch_create_fused(const imask_state_t *states, int32_t n_sta
     b->bp_smem = std::max(b->bp_smem, bp_smem_bytes(P));
     b->upd_smem = std::max(b->upd_smem, upd_smem_bytes_of(P));
     for (int li = 0; li <= P.levels; ++li) b->nv_cap = std::max(b->nv_cap, P.lg[li].bp_nv);
+    int most = 0;
+    for (int li = 1; li <= P.levels; ++li)
+      most = std::max(most, 2 * P.lg[li].bp_nm * P.lg[li].bp_nc * P.lg[li].bp_vgo);
+    b->bp_max_items += most;
   }
   b->fp_total = fp_start[n];
   b->upd_total = upd_start[n];
@@ -2195,8 +2200,14 @@ imask_status imask_state_get(imask_state_t s, int32_t what, float *dst, void *st
   }
   imask_status rc = state_use_stream(s, (cudaStream_t)stream);
   if (rc != IMASK_OK) return rc;
-  CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
-     "copy state");
+  if (what == 1 || what == 3) {
+    // measurement-space parts are kept in ray-list order: back to (view, bin)
+    CK(launch_sino_order(p->dp, src, dst, 0, (cudaStream_t)stream), "copy state");
+  } else {
+    CK(cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                       (cudaStream_t)stream),
+       "copy state");
+  }
   return IMASK_OK;
 }
 

@@ -31,7 +31,7 @@
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
 #endif
 
-// Per-view data for the pixel-driven back-projector (32 bytes).
+// Per-view data for the back-projector's ray windows (32 bytes).
 struct ViewInfo {
   float c, s;       // cos / sin of the view angle
   int xj0, xj1;     // x-major rays of the view: j in [xj0, xj1)
@@ -124,6 +124,8 @@ struct ExtrapArgs {
 };
 
 // Dual epilogue (Alg. 1, the zeta and y updates) fused into the projector.
+// A solve keeps its measurement-space vectors (y, b, the tables psi and their
+// mean) in ray-list order: entry i belongs to ray i of DevPlan::rays.
 struct DualArgs {
   int on;
   const float *y_in;
@@ -165,7 +167,7 @@ struct FusedSlice {
   PadSet pads_fp;      // sketch images the projector reads
   PadSet pads_upd;     // sketch images the update writes
   DualArgs D;          // projector epilogue
-  const float *y_bp;   // back-projector input
+  const float *y_bp;   // back-projector input (ray-list order)
   float *g;            // back-projector partial images
   PrimalArgs A;        // update
   unsigned int *err;
@@ -184,8 +186,13 @@ unsigned long long primal_seed(unsigned long long seed);
 cudaError_t launch_fp(const DevPlan &P, LevelSel sel, PadSet pads, float *sino, DualArgs dual,
                       int n_cta_x, int n_cta_y, unsigned int *err, cudaStream_t st,
                       int test_skip_first_strip = 0);
-cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
+// y_list: y in ray-list order (a state's dual iterate) rather than (view, bin)
+// order
+cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, int y_list, float *g,
                       unsigned int *err, cudaStream_t st);
+// dst = src moved from (view, bin) order to ray-list order (to_list = 1) or back
+cudaError_t launch_sino_order(const DevPlan &P, const float *src, float *dst, int to_list,
+                              cudaStream_t st);
 long long bp_smem_bytes(const DevPlan &P);
 int bp_blocks_per_sm(long long dyn_smem);
 cudaError_t launch_adjsketch(const DevPlan &P, int ell, const float *g, float *img,
@@ -201,8 +208,11 @@ cudaError_t launch_update(const DevPlan &P, LevelSel sel, PrimalArgs pa, int wri
 // largest over the solves.
 cudaError_t launch_fp_multi(const FusedSlice *recs, const int *fp_start, int n_slices,
                             int total_ctas, cudaStream_t st);
+// max_items > 0: one CTA per item over a grid of max_items CTAs (those past
+// the iteration's list return at once) instead of `grid` resident CTAs
 cudaError_t launch_bp_multi(const FusedSlice *recs, int n_slices, int *bp_start, int *bp_counter,
-                            int nv_cap, long long smem, int grid, cudaStream_t st);
+                            int nv_cap, long long smem, int grid, int max_items,
+                            cudaStream_t st);
 int bp_multi_blocks_per_sm(long long dyn_smem);
 cudaError_t launch_update_multi(const FusedSlice *recs, const int *upd_start, int n_slices,
                                 int total_ctas, int smem, cudaStream_t st);

@@ -4,8 +4,10 @@
 //   k_fp      forward projection K_ell x (Joseph, one ray per thread and slot)
 //             over image strips staged in shared memory by TMA bulk copies,
 //             with the dual SAGA update and dual prox fused into its epilogue;
-//   k_bp      pixel-driven back-projection R_ell^T y on the level grid (gather,
-//             no atomics), the exact transpose of k_fp's weights;
+//   k_bp      back-projection R_ell^T y on the level grid, owner-computes
+//             (each thread owns a line segment of a tile and applies the rays
+//             crossing the tile in private shared-memory accumulators; no
+//             atomics), the exact transpose of k_fp's weights;
 //   k_update  the image-side adjoint sketch (T_ell^T or S_r), the primal SAGA
 //             update and prox, and the image-side sketch T_ell' / S_r of the
 //             new iterate for the next drawn level (fused "sketch on load").
@@ -393,7 +395,15 @@ __device__ __forceinline__ void fp_body(const DevPlan &P, const LevelSel &sel, c
     const int idx = fp_ray(begin, r, tid);
     qv[r] = -1;
     gz[r] = 0.0f;
-    if (idx < end) {
+    if (idx >= end) continue;
+    if (D.on) {
+      // a solve's measurement-space vectors are kept in ray-list order: the
+      // ray's entry is its own index (coalesced, no index load), and only the
+      // ray's weight is read back
+      qv[r] = idx;
+      gz[r] = __ldg(&P.rays[idx].z) * G.scale2l;
+    } else {
+      // the bare operator writes the sinogram in (view, bin) order
       const float4 p = P.rays[idx];
       qv[r] = __float_as_int(p.w);
       gz[r] = p.z * G.scale2l;
@@ -564,9 +574,12 @@ __device__ int scan_counts(int *a, int n) {
 // One back-projector work item (block `bid` of the plan's grid at the drawn
 // level); returns with every shared-memory read done except the last
 // barrier's.
+// y_list: y is in ray-list order (a solve's dual iterate) rather than in
+// (view, bin) order (the bare operator's input).
 __device__ __forceinline__ void bp_body(const DevPlan &P, const LevelSel &sel,
-                                        const float *__restrict__ y, float *__restrict__ gout,
-                                        unsigned int *err, int nv_cap, int bid) {
+                                        const float *__restrict__ y, int y_list,
+                                        float *__restrict__ gout, unsigned int *err, int nv_cap,
+                                        int bid) {
   extern __shared__ __align__(16) float4 bp_raw[];
   // private accumulators: [slot][thread]; slots 0..BP_ACC-1 are cross lines
   // -2..BP_SEG+1 of the owner's segment
@@ -679,7 +692,7 @@ __device__ __forceinline__ void bp_body(const DevPlan &P, const LevelSel &sel,
         continue;
       rw[u] = __ldg(P.rays + vi.x + kk);
       rlo[u] = __ldg(P.rays_lo + vi.x + kk);
-      ry[u] = __ldg(y + vi.y + kk);
+      ry[u] = __ldg(y + (y_list ? vi.x : vi.y) + kk);
     }
   };
   auto put = [&](int k, int b) {
@@ -743,9 +756,9 @@ __device__ __forceinline__ void bp_body(const DevPlan &P, const LevelSel &sel,
 }
 
 __global__ void __launch_bounds__(BP_THREADS, 4)
-    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, float *__restrict__ gout,
-         unsigned int *err, int nv_cap) {
-  bp_body(P, sel, y, gout, err, nv_cap, (int)blockIdx.x);
+    k_bp(DevPlan P, LevelSel sel, const float *__restrict__ y, int y_list,
+         float *__restrict__ gout, unsigned int *err, int nv_cap) {
+  bp_body(P, sel, y, y_list, gout, err, nv_cap, (int)blockIdx.x);
 }
 
 // The back-projector leaves 2 bp_vgo partial images (x- and y-major rays, one
@@ -1144,6 +1157,19 @@ __global__ void __launch_bounds__(BP_THREADS)
   if (threadIdx.x == 0) *counter = 0;
 }
 
+// One item per CTA: the grid covers the most items the solves can have at
+// any level, CTAs past the iteration's list return at once.  Unlike resident
+// CTAs, these leave SMs to the projector's CTAs as they finish.
+__global__ void __launch_bounds__(BP_THREADS, 4)
+    k_bp_items(const FusedSlice *__restrict__ recs, int n, const int *__restrict__ start,
+               int nv_cap) {
+  const int it = (int)blockIdx.x;
+  if (it >= start[n]) return;
+  const int s = slice_of(start, n, it);
+  const FusedSlice &R = recs[s];
+  bp_body(R.P, R.sel, R.y_bp, 1, R.g, R.err, nv_cap, it - start[s]);
+}
+
 __global__ void __launch_bounds__(BP_THREADS, 4)
     k_bp_multi(const FusedSlice *__restrict__ recs, int n, const int *__restrict__ start,
                int *counter, int nv_cap) {
@@ -1163,7 +1189,7 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
     if (it >= total) break;
     const int s = slice_of(start, n, it);
     const FusedSlice &R = recs[s];
-    bp_body(R.P, R.sel, R.y_bp, R.g, R.err, nv_cap, it - start[s]);
+    bp_body(R.P, R.sel, R.y_bp, 1, R.g, R.err, nv_cap, it - start[s]);
     // every thread is done with the item's shared memory (and with `item`)
     // before the next item is published
     __syncthreads();
@@ -1372,6 +1398,20 @@ __global__ void k_phi_mean(DevPlan P, const void *phi0, const void *phic, Primal
   }
 }
 
+// Measurement-space vectors between (view, bin) order and ray-list order:
+// entry i of the list is sinogram entry rays[i].w.
+__global__ void k_sino_order(DevPlan P, const float *__restrict__ src, float *__restrict__ dst,
+                             int to_list) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P.m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int q = __float_as_int(__ldg(&P.rays[i].w));
+    if (to_list)
+      dst[i] = src[q];
+    else
+      dst[q] = src[i];
+  }
+}
+
 __global__ void k_counter(long long *k, long long delta, int set_value) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *k = set_value ? delta : *k + delta;
 }
@@ -1574,7 +1614,7 @@ long long bp_smem_bytes(const DevPlan &P) {   // dynamic part only
          (long long)(bp_nv_cap(P) + 1) * 4;
 }
 
-cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
+cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, int y_list, float *g,
                       unsigned int *err, cudaStream_t st) {
   // the grid covers the level with the most (tile, view group) pairs; extra
   // CTAs return at once
@@ -1586,7 +1626,7 @@ cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, float *g,
   cudaError_t e = set_smem((const void *)k_bp, sm);
   if (e != cudaSuccess) return e;
   count_launch();
-  k_bp<<<most, BP_THREADS, sm, st>>>(P, sel, y, g, err, bp_nv_cap(P));
+  k_bp<<<most, BP_THREADS, sm, st>>>(P, sel, y, y_list, g, err, bp_nv_cap(P));
   return cudaGetLastError();
 }
 
@@ -1636,15 +1676,20 @@ int bp_multi_blocks_per_sm(long long dyn_smem) {
 }
 
 cudaError_t launch_bp_multi(const FusedSlice *recs, int n_slices, int *bp_start, int *bp_counter,
-                            int nv_cap, long long smem, int grid, cudaStream_t st) {
+                            int nv_cap, long long smem, int grid, int max_items,
+                            cudaStream_t st) {
   if (n_slices < 1 || n_slices > IMASK_MAX_FUSED) return cudaErrorInvalidValue;
-  cudaError_t e = set_smem((const void *)k_bp_multi, (int)smem);
+  const void *fn = max_items > 0 ? (const void *)k_bp_items : (const void *)k_bp_multi;
+  cudaError_t e = set_smem(fn, (int)smem);
   if (e != cudaSuccess) return e;
   count_launch();
   k_bp_plan<<<1, BP_THREADS, 0, st>>>(recs, n_slices, bp_start, bp_counter);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   count_launch();
-  k_bp_multi<<<grid, BP_THREADS, smem, st>>>(recs, n_slices, bp_start, bp_counter, nv_cap);
+  if (max_items > 0)
+    k_bp_items<<<max_items, BP_THREADS, smem, st>>>(recs, n_slices, bp_start, nv_cap);
+  else
+    k_bp_multi<<<grid, BP_THREADS, smem, st>>>(recs, n_slices, bp_start, bp_counter, nv_cap);
   return cudaGetLastError();
 }
 
@@ -1784,6 +1829,13 @@ cudaError_t launch_phi_mean(const DevPlan &P, const void *phi0, const void *phic
   count_launch();
   k_phi_mean<<<grid_for((long long)P.n * P.n, 256), 256, 0, st>>>(P, phi0, phic, offs, fmt,
                                                                  phi_mean);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sino_order(const DevPlan &P, const float *src, float *dst, int to_list,
+                              cudaStream_t st) {
+  count_launch();
+  k_sino_order<<<grid_for(P.m, 256), 256, 0, st>>>(P, src, dst, to_list);
   return cudaGetLastError();
 }
 

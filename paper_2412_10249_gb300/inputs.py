@@ -243,26 +243,35 @@ def disk_sinogram(p: Problem, radius: float = 0.3, density: float = 1.0) -> np.n
         p.n_angles, p.n_det)
 
 
-def serving_requests(duration: float, rate: float, seed: int, max_side: int = 2048):
+def _serving_geometry(rng, max_side: int) -> Problem:
+    r = int(rng.integers(2, 7))
+    blk = 1 << (r - 1)
+    n = int(round(math.exp(rng.uniform(math.log(128), math.log(max_side))) / blk)) * blk
+    n = max(blk, min(n, max_side))
+    na = int(rng.integers(180, 2049))
+    return Problem(n=n, n_angles=na, n_det=3 * n // 2, geometry=1, angle_span=2 * math.pi,
+                   src_dist=2.0, det_dist=1.0, levels=r)
+
+
+def serving_requests(duration: float, rate: float, seed: int, max_side: int = 2048,
+                     n_geometries: int = 0):
     """Poisson arrivals (mean `rate` per second) over `duration` seconds; per
     request: levels r uniform in {2..6}, side N log-uniform in [128, max_side]
     rounded to a multiple of 2^(r-1), views uniform in [180, 2048], bins 1.5 N,
     fan beam as the 512x512 workload, iterations uniform in [100, 1000], a
-    seed.  Returns a list of (arrival, Problem, iters, seed)."""
+    seed.  With n_geometries > 0, that many geometries are drawn first (same
+    distribution) and every request takes one of them uniformly (a scanner
+    fleet with a few protocols); else every request draws its own.  Returns a
+    list of (arrival, Problem, iters, seed)."""
     rng = np.random.Generator(np.random.PCG64(seed))
+    fleet = [_serving_geometry(rng, max_side) for _ in range(n_geometries)]
     t = 0.0
     out = []
     while True:
         t += rng.exponential(1.0 / rate)
         if t >= duration:
             return out
-        r = int(rng.integers(2, 7))
-        blk = 1 << (r - 1)
-        n = int(round(math.exp(rng.uniform(math.log(128), math.log(max_side))) / blk)) * blk
-        n = max(blk, min(n, max_side))
-        na = int(rng.integers(180, 2049))
-        p = Problem(n=n, n_angles=na, n_det=3 * n // 2, geometry=1, angle_span=2 * math.pi,
-                    src_dist=2.0, det_dist=1.0, levels=r)
+        p = fleet[int(rng.integers(0, len(fleet)))] if fleet else _serving_geometry(rng, max_side)
         out.append((t, p, int(rng.integers(100, 1001)), int(rng.integers(0, 2 ** 31))))
 
 
