@@ -1762,7 +1762,11 @@ imask_status enqueue_iteration(const imask_state_s *s, cudaStream_t st, int cur,
 // its start).  Within a graph the back-projector of one iteration overlaps the
 // update of the previous one; replays are serialised, so longer graphs keep
 // that overlap for more of the iterations.
-constexpr int kGraphUnroll = 4;
+#ifndef IMASK_GRAPH_UNROLL
+#define IMASK_GRAPH_UNROLL 4
+#endif
+constexpr int kGraphUnroll = IMASK_GRAPH_UNROLL;
+static_assert(kGraphUnroll % 2 == 0, "graphs hold an even number of iterations");
 
 void batch_release_graph(imask_batch_s *b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
