@@ -989,9 +989,15 @@ def serving_mean_samples(n_draws: int = 20000, n_geometries: int = 0) -> float:
 
 
 def run_serve(args):
-    import torch
     from paper_2412_10249_gb300 import build as pkg_build
     pkg_build.build()
+    print(json.dumps(serving_line(args)))
+    return 0
+
+
+def serving_line(args) -> dict:
+    """One serving run (Poisson arrivals over args.serve_seconds, continuous
+    batching through serve.Server); returns the report."""
     from paper_2412_10249_gb300 import serve
     rate = args.serve_rate
     mean_samples = serving_mean_samples(n_geometries=args.serve_geometries)
@@ -1061,8 +1067,7 @@ def run_serve(args):
                        "slots": args.serve_slots, "queue": args.serve_queue, "quantum": 10,
                        "geometries": args.serve_geometries or "one per request"}}
     srv.close()
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 # ---------------------------------------------------------------------------------
@@ -1206,6 +1211,12 @@ def run_ours(args):
                                          cpu_iters=args.cpu_iters)
         mp["plain_fp32_solves_per_s"] = value
         variants["mixed_precision_fan512"] = mp
+        # serving: Poisson arrivals at 0.7 of this GPU's measured capacity, the
+        # requests sharing a fleet of four geometries, drained
+        sargs = argparse.Namespace(**vars(args))
+        sargs.serve_seconds, sargs.serve_load, sargs.serve_geometries = 15.0, 0.7, 4
+        sargs.serve_capacity_gsps = gs
+        variants["serving"] = serving_line(sargs)
 
     # ---- CPU baseline: the oracle on a bounded sample ----
     cpu = None
