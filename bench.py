@@ -357,6 +357,7 @@ def roofline_report(p, prof_ms, prof_cnt, dev, period=1, smem_probe=None, l2_gbs
            "gsamples_per_s": samples_launch / avg_s / 1e9,
            "traffic": traffic, "algorithmic_dram_bytes": alg_dram,
            "traffic_over_algorithmic": (traffic / alg_dram) if traffic else None,
+           "traffic_in_solve": _dram_traffic(KNAMES[kind], lvl, "dram_bytes_per_launch_in_solve"),
            "device": {"n_sm": n_sm, "max_sm_mhz": dev["max_mhz"]}}
     if kind in FLOPS_PER_SAMPLE:
         ach = samples_launch * SMEM_BYTES_PER_SAMPLE / avg_s / 1e9
@@ -411,15 +412,17 @@ def _kernels_sha() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def _dram_traffic(kname: str, level: int):
-    """DRAM bytes per launch from the committed ncu summary, if it still
-    describes the current kernel source (else None)."""
+def _dram_traffic(kname: str, level: int, field: str = "dram_bytes_per_launch"):
+    """DRAM bytes per launch from the committed ncu summary (cold caches, or
+    with field "dram_bytes_per_launch_in_solve" the same launch in a solve with
+    the caches as the solve left them), if it still describes the current
+    kernel source (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_counters.json")) as f:
             c = json.load(f)
         if c.get("kernels_cu_sha256_prefix") != _kernels_sha():
             return None
-        return c[kname][str(level)]["dram_bytes_per_launch"]
+        return c[kname][str(level)][field]
     except (OSError, KeyError, ValueError):
         return None
 

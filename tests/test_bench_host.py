@@ -45,7 +45,9 @@ DEV = {"n_sm": 152, "max_mhz": 2070.0}
 
 
 def test_roofline_report_arithmetic(monkeypatch):
-    monkeypatch.setattr(bench, "_dram_traffic", lambda kname, level: 1234)
+    monkeypatch.setattr(bench, "_dram_traffic",
+                        lambda kname, level, field="dram_bytes_per_launch":
+                        1234 if field == "dram_bytes_per_launch" else 99)
     p = inputs.fan512_problem()
     # back-projector level 0 dominates: 10 launches of 0.25 ms
     ms, cnt = _prof({(1, 0): (2.5, 10), (0, 0): (1.3, 10), (2, 1): (0.2, 12)})
@@ -64,6 +66,7 @@ def test_roofline_report_arithmetic(monkeypatch):
     alg = 4.0 * (720 * 768 + 512 * 512)          # y in, image out
     assert rep["algorithmic_dram_bytes"] == pytest.approx(alg)
     assert rep["traffic_over_algorithmic"] == pytest.approx(1234 / alg)
+    assert rep["traffic_in_solve"] == 99
     assert rep["gsamples_per_s"] == pytest.approx(samples / avg_s / 1e9)
     alu = rep["alu_view"]
     assert alu["achieved_tflops"] == pytest.approx(samples * 7.0 / avg_s / 1e12)
@@ -86,7 +89,7 @@ def test_roofline_report_arithmetic(monkeypatch):
 
 
 def test_roofline_report_projector_at_a_coarse_level(monkeypatch):
-    monkeypatch.setattr(bench, "_dram_traffic", lambda kname, level: None)
+    monkeypatch.setattr(bench, "_dram_traffic", lambda kname, level, field=None: None)
     p = inputs.fan512_problem()
     ms, cnt = _prof({(0, 2): (5.0, 100), (1, 0): (1.0, 4)})
     dev = {"n_sm": 148, "max_mhz": 1965.0}
