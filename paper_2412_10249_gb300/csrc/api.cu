@@ -383,12 +383,15 @@ LevelGeom level_geom(const imask_desc &d, int ell) {
 #define IMASK_UPD_TILE_CAP 32
 #endif
 
+// The largest power of two that divides n, is at least the coarsest block
+// (2^(levels-1), which divides n) and at most the cap: the kernels index tile
+// pixels with shifts and masks.  The tile size does not change any result
+// (block means are over aligned blocks inside one tile whatever its size).
 int update_tile(int n, int levels) {
   const int blk = 1 << (levels - 1);
   const int cap = std::max(IMASK_UPD_TILE_CAP, blk);
   int best = blk;
-  for (int k = 1; blk * k <= cap; ++k)
-    if (n % (blk * k) == 0) best = blk * k;
+  while (2 * best <= cap && n % (2 * best) == 0) best *= 2;
   return best;
 }
 

@@ -786,6 +786,10 @@ __device__ __forceinline__ float g_sum(const float *g, int vgo, size_t plane, si
   return planes_sum(g, 1, vgo, 1, plane, idx, __ldg(g + idx));
 }
 
+// log2 of a power of two (tile and block sides of the update-side kernels,
+// which index with shifts and masks instead of divisions)
+__device__ __forceinline__ int lg2i(int x) { return __ffs(x) - 1; }
+
 // Sum of the back-projector's npl partial planes for the cs x cs coarse pixels
 // starting at (I0, J0) of a level grid of side nl, into out[cs * cs]: K lanes
 // per pixel add planes k, k+K, ..., then the lanes are added in a fixed order.
@@ -796,10 +800,11 @@ __device__ void coarse_planes_sum(const float *g, int npl, int nl, int I0, int J
   const int ncp = cs * cs;
   const int K = max(1, min(UPD_THREADS / ncp, npl));   // K = 1 when ncp >= UPD_THREADS
   const size_t plane = (size_t)nl * nl;
+  const int lcs = lg2i(cs), lnp = 2 * lcs;
   if (K > 1) {
     for (int u = threadIdx.x; u < ncp * K; u += blockDim.x) {
-      const int p = u % ncp, k = u / ncp;
-      const size_t gi = (size_t)(I0 + p / cs) * nl + J0 + p % cs;
+      const int p = u & (ncp - 1), k = u >> lnp;
+      const size_t gi = (size_t)(I0 + (p >> lcs)) * nl + J0 + (p & (cs - 1));
       red[u] = planes_sum(g, k, npl, K, plane, gi, 0.0f);
     }
   }
@@ -809,7 +814,7 @@ __device__ void coarse_planes_sum(const float *g, int npl, int nl, int I0, int J
     if (K > 1) {
       for (int k = 0; k < K; ++k) sum += red[k * ncp + p];
     } else {
-      const size_t gi = (size_t)(I0 + p / cs) * nl + J0 + p % cs;
+      const size_t gi = (size_t)(I0 + (p >> lcs)) * nl + J0 + (p & (cs - 1));
       sum = planes_sum(g, 0, npl, 1, plane, gi, 0.0f);
     }
     out[p] = sum;
@@ -823,10 +828,10 @@ __device__ void tile_pyramid(const float *src, float *pyr, int ts, int r) {
   const float *prev = src;
   int ps = ts, off = 0;
   for (int l = 1; l < r; ++l) {
-    const int s = ps >> 1;
+    const int s = ps >> 1, ls = lg2i(s);
     float *cur = pyr + off;
     for (int p = threadIdx.x; p < s * s; p += blockDim.x) {
-      const int I = p / s, J = p % s;
+      const int I = p >> ls, J = p & (s - 1);
       const float *q = prev + (2 * I) * ps + 2 * J;
       cur[p] = 0.25f * ((q[0] + q[1]) + (q[ps] + q[ps + 1]));
     }
@@ -868,9 +873,10 @@ __device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, floa
   const int I0 = ti0 >> sh, J0 = tj0 >> sh;
   float *R = pads.R[li];
   float *T = pads.T[li];
+  const int lsd = lg2i(side), msd = side - 1;
   if (S) {
     for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
-      const size_t gi = (size_t)(I0 + p / side) * G.nl + J0 + p % side;
+      const size_t gi = (size_t)(I0 + (p >> lsd)) * G.nl + J0 + (p & msd);
       const float v = vals[p];
       vals[p] = v - S[gi];
       S[gi] = v;
@@ -878,12 +884,12 @@ __device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, floa
     __syncthreads();
   }
   for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
-    const int I = p / side, J = p % side;
+    const int I = p >> lsd, J = p & msd;
     if (!IMASK_INDEX_OK(I0 + I < G.nl && J0 + J < G.nl, 3)) continue;
     R[(size_t)(I0 + I) * G.ls + IMASK_PAD + J0 + J] = vals[I * side + J];
   }
   for (int p = threadIdx.x; p < side * side; p += blockDim.x) {
-    const int J = p / side, I = p % side;
+    const int J = p >> lsd, I = p & msd;
     T[(size_t)(J0 + J) * G.ls + IMASK_PAD + I0 + I] = vals[I * side + J];
   }
 }
@@ -899,7 +905,7 @@ __device__ void sketch_tile(const DevPlan &P, const PadSet &pads, int ell, float
   if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
   if (ell == 0) {
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-      aux[p] = compensate_px(P, xs[p], pyr, ts, p / ts, p % ts);
+      aux[p] = compensate_px(P, xs[p], pyr, ts, p >> lg2i(ts), p & (ts - 1));
     __syncthreads();
     write_padded(P, pads, 0, aux, ts, ti0, tj0, S);
   } else {
@@ -913,12 +919,12 @@ __global__ void __launch_bounds__(UPD_THREADS)
     k_sketch(DevPlan P, LevelSel sel, const float *__restrict__ x, PadSet pads, ExtrapArgs ex,
              SnapArgs sn) {
   extern __shared__ __align__(16) float upd_smem[];
-  const int ts = P.upd_tile, ntx = P.n / ts;
+  const int ts = P.upd_tile, ntx = P.n / ts, lts = lg2i(ts);
   float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
   const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
   const int ell = sel_level(P, sel);
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
-    const size_t gp = (size_t)(ti0 + p / ts) * P.n + tj0 + p % ts;
+    const size_t gp = (size_t)(ti0 + (p >> lts)) * P.n + tj0 + (p & (ts - 1));
     const float v = x[gp];
     xs[p] = ex.x_prev ? fmaf(ex.theta, v - ex.x_prev[gp], v) : v;
   }
@@ -932,7 +938,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
 __global__ void __launch_bounds__(UPD_THREADS)
     k_adjsketch(DevPlan P, int ell, const float *__restrict__ g, float *__restrict__ img) {
   extern __shared__ __align__(16) float upd_smem[];
-  const int ts = P.upd_tile, ntx = P.n / ts;
+  const int ts = P.upd_tile, ntx = P.n / ts, lts = lg2i(ts);
   float *xs = upd_smem, *pyr = xs + 2 * ts * ts;
   const int ti0 = (blockIdx.x / ntx) * ts, tj0 = (blockIdx.x % ntx) * ts;
   const int n = P.n;
@@ -940,7 +946,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
   const size_t plane = (size_t)G.nl * G.nl;
   if (ell < 0) {
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
-      const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
+      const size_t gp = (size_t)(ti0 + (p >> lts)) * n + tj0 + (p & (ts - 1));
       img[gp] = g_sum(g, 2 * G.bp_vgo, plane, gp);
     }
     return;
@@ -950,17 +956,18 @@ __global__ void __launch_bounds__(UPD_THREADS)
     const int cs = ts >> ell;
     coarse_planes_sum(g, 2 * G.bp_vgo, G.nl, ti0 >> ell, tj0 >> ell, cs, xs);
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x) {
-      const int li = p / ts, lj = p % ts;
+      const int li = p >> lts, lj = p & (ts - 1);
       img[(size_t)(ti0 + li) * n + tj0 + lj] = xs[(li >> ell) * cs + (lj >> ell)] * s;
     }
     return;
   }
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-    xs[p] = g_sum(g, 2 * G.bp_vgo, plane, (size_t)(ti0 + p / ts) * n + tj0 + p % ts);
+    xs[p] = g_sum(g, 2 * G.bp_vgo, plane, (size_t)(ti0 + (p >> lts)) * n + tj0 + (p & (ts - 1)));
   __syncthreads();
   if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-    img[(size_t)(ti0 + p / ts) * n + tj0 + p % ts] = compensate_px(P, xs[p], pyr, ts, p / ts, p % ts);
+    img[(size_t)(ti0 + (p >> lts)) * n + tj0 + (p & (ts - 1))] =
+        compensate_px(P, xs[p], pyr, ts, p >> lts, p & (ts - 1));
 }
 
 // Primal half of Alg. 1 on one tile, then the sketch of the new iterate for
@@ -971,7 +978,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
                                             const PrimalArgs &A, int write_sketch,
                                             const PadSet &pads, int bid) {
   extern __shared__ __align__(16) float upd_smem[];
-  const int ts = P.upd_tile, ntx = P.n / ts;
+  const int ts = P.upd_tile, ntx = P.n / ts, lts = lg2i(ts);
   float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
   float *dc = pyr + ts * ts / 2 + 4;
   float *dm = dc + ts * ts / 4 + 4;
@@ -995,7 +1002,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
       const int p = p0 + u * (int)blockDim.x;
       pmv[u] = xov[u] = ph0[u] = 0.0f;
       if (p >= ts * ts) continue;
-      const size_t gp = (size_t)(ti0 + p / ts) * n + tj0 + p % ts;
+      const size_t gp = (size_t)(ti0 + (p >> lts)) * n + tj0 + (p & (ts - 1));
       pmv[u] = A.phi_mean[gp];
       xov[u] = A.x[gp];
       if (ell < 1) ph0[u] = tab_load(A.phi0, gp, fmt);
@@ -1015,7 +1022,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
     // (rounded, with 16-bit tables) value's change, so that the mean stays the
     // p-weighted sum of the stored tables
     for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
-      const size_t gi = (size_t)off + (size_t)(I0 + p / cs) * G.nl + J0 + p % cs;
+      const size_t gi = (size_t)off + (size_t)(I0 + (p >> (lts - ell))) * G.nl + J0 + (p & (cs - 1));
       const float cnew = dc[p] * inv4l;
       const float old = tab_load(A.phic, gi, fmt);
       const float stored = tab_store(A.phic, gi, cnew, fmt);
@@ -1034,7 +1041,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
 #pragma unroll
       for (int u = 0; u < kUpdPix; ++u) {
         const int p = p0 + u * (int)blockDim.x;
-        gi[u] = p < ts * ts ? (size_t)(ti0 + p / ts) * n + tj0 + p % ts : 0;
+        gi[u] = p < ts * ts ? (size_t)(ti0 + (p >> lts)) * n + tj0 + (p & (ts - 1)) : 0;
         sum[u] = p < ts * ts ? __ldg(A.g + gi[u]) : 0.0f;
       }
       for (int v = 1; v < vgo0; v += kPlaneBatch) {
@@ -1066,7 +1073,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
     for (int u = 0; u < kUpdPix; ++u) {
       const int p = p0 + u * (int)blockDim.x;
       if (p >= ts * ts) continue;
-      const int li = p / ts, lj = p % ts;
+      const int li = p >> lts, lj = p & (ts - 1);
       const size_t gp = (size_t)(ti0 + li) * n + tj0 + lj;
       float delta, dmean;
       if (ell >= 1) {
