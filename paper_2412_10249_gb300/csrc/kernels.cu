@@ -528,7 +528,7 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) {
 
 #define BP_GROUPS (BP_THREADS / BP_W)   // ray residue classes per CTA
 #ifndef BP_UNROLL
-#define BP_UNROLL 2                      // unrolling of the scatter loop
+#define BP_UNROLL 8                      // unrolling of the scatter loop
 #endif
 #define IMASK_STR(x) #x
 #define IMASK_UNROLL(n) _Pragma(IMASK_STR(unroll n))
@@ -718,8 +718,7 @@ __device__ __forceinline__ void bp_body(const DevPlan &P, const LevelSel &sel,
     if (k + 1 < nch) fetch(k + 1);
     const float4 *win = bp_win(bp_raw, b);
     const int n = min(BP_SLOTS, NR - k * BP_SLOTS);
-    IMASK_UNROLL(BP_UNROLL)
-    for (int sl = g; sl < n; sl += BP_GROUPS) {
+    auto apply = [&](int sl) {
       const float4 e = win[sl];
       const float q = fmaf(dseg, e.y, e.x);
       const float tq = __fadd_rd(q, kMagic);
@@ -735,6 +734,15 @@ __device__ __forceinline__ void bp_body(const DevPlan &P, const LevelSel &sel,
       float *pa = acc + slot * BP_THREADS;
       pa[0] += e.z - w1;
       pa[BP_THREADS] += w1;
+    };
+    // a full chunk runs a fixed trip count (no per-entry bound test); the
+    // last, partial chunk tests the bound
+    if (n == BP_SLOTS) {
+      IMASK_UNROLL(BP_UNROLL)
+      for (int it = 0; it < BP_SLOTS / BP_GROUPS; ++it) apply(g + it * BP_GROUPS);
+    } else {
+      IMASK_UNROLL(BP_UNROLL)
+      for (int sl = g; sl < n; sl += BP_GROUPS) apply(sl);
     }
     // buffer b ^ 1 was last read by the scatter of chunk k - 1, which ended
     // before the previous barrier
