@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -289,88 +291,102 @@ __device__ __forceinline__ void fp_body(const DevPlan &P, const LevelSel &sel, c
   // it last refills it with the strip FP_STAGES further on.
   bool failed = false;
   unsigned act = 0u;   // ray slots with at least one on-grid ray in the warp (this block)
-  for (int s = 0; s < nstrips; ++s) {
-    const int st = s % FP_STAGES;
-    const uint32_t parity = (uint32_t)((s / FP_STAGES) & 1);
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[st]), parity, wait_limit));
-    if (!ok) {
-      failed = true;
-      break;
-    }
-    const float *buf = fp_smem + st * FP_STAGE_FLOATS;
-    float part[FP_RAYS];
-#pragma unroll
-    for (int r = 0; r < FP_RAYS; ++r) part[r] = 0.0f;
-    for (int cc = 0; cc < tc; cc += 4) {
-      const int c = s * tc + cc;
-      if ((c & (LBLOCK - 1)) == 0) {
-        const float ccm = (float)c - G.cmid;
-        act = 0u;
-#pragma unroll
-        for (int r = 0; r < FP_RAYS; ++r) {
-          int I;
-          block_origin(ahi[r], alo[r], thi[r], tlo[r], G.inv2l, ccm, I, rl[r]);
-          // rows of the block's first and last sample
-          const int f0 = __float_as_int(__fadd_rd(rl[r], kMagic)) - kMagicBits;
-          const int f1 =
-              __float_as_int(__fadd_rd(fmaf((float)(LBLOCK - 1), thi[r], rl[r]), kMagic)) -
-              kMagicBits;
-          const int lo = I + min(f0, f1), hi = I + max(f0, f1);
-          // off the grid (no row in [0, nl-1] is read): land in the leading zeros
-          const bool off = (hi + 1 < 0) || (lo > G.nl - 1);
-          boff[r] = off ? (IMASK_PAD / 2) - f0 : IMASK_PAD + I;
-          // a slot whose 32 rays all miss the grid in this block adds exactly
-          // zero: the warp skips its samples (the branch is warp-uniform)
-          act |= (__any_sync(0xffffffffu, !off) ? 1u : 0u) << r;
+  // The strip loop, compiled for the common strip heights (a fixed trip
+  // count through the strip, and block starts known at compile time when the
+  // height is a multiple of LBLOCK) and once for any other height.
+  auto strips = [&](auto tc_const) {
+    constexpr int TC = decltype(tc_const)::value;
+    const int tcv = TC > 0 ? TC : tc;
+    for (int s = 0; s < nstrips; ++s) {
+      const int st = s % FP_STAGES;
+      const uint32_t parity = (uint32_t)((s / FP_STAGES) & 1);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&full_bar[st]), parity, wait_limit));
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      const float *buf = fp_smem + st * FP_STAGE_FLOATS;
+      float part[FP_RAYS];
+  #pragma unroll
+      for (int r = 0; r < FP_RAYS; ++r) part[r] = 0.0f;
+  #pragma unroll
+      for (int cc = 0; cc < tcv; cc += 4) {
+        const int c = s * tcv + cc;
+        if ((c & (LBLOCK - 1)) == 0) {
+          const float ccm = (float)c - G.cmid;
+          act = 0u;
+  #pragma unroll
+          for (int r = 0; r < FP_RAYS; ++r) {
+            int I;
+            block_origin(ahi[r], alo[r], thi[r], tlo[r], G.inv2l, ccm, I, rl[r]);
+            // rows of the block's first and last sample
+            const int f0 = __float_as_int(__fadd_rd(rl[r], kMagic)) - kMagicBits;
+            const int f1 =
+                __float_as_int(__fadd_rd(fmaf((float)(LBLOCK - 1), thi[r], rl[r]), kMagic)) -
+                kMagicBits;
+            const int lo = I + min(f0, f1), hi = I + max(f0, f1);
+            // off the grid (no row in [0, nl-1] is read): land in the leading zeros
+            const bool off = (hi + 1 < 0) || (lo > G.nl - 1);
+            boff[r] = off ? (IMASK_PAD / 2) - f0 : IMASK_PAD + I;
+            // a slot whose 32 rays all miss the grid in this block adds exactly
+            // zero: the warp skips its samples (the branch is warp-uniform)
+            act |= (__any_sync(0xffffffffu, !off) ? 1u : 0u) << r;
+          }
+        }
+        const float d0 = (float)(c & (LBLOCK - 1));
+        // Rays go in pairs through the packed FP32x2 instructions of sm_100+
+        // (one issue slot for both rays; per component the rounding is that of
+        // the scalar operation, so the samples are bit for bit those of
+        // fmaf / __fadd_rd / subtraction).  A pair is skipped when neither of its
+        // slots has a ray on the grid in this block.
+  #pragma unroll
+        for (int r = 0; r < FP_RAYS; r += 2) {
+          if (!(act & (3u << r))) continue;
+          const float2 t2 = make_float2(thi[r], thi[r + 1]);
+          const float2 r2 = make_float2(rl[r], rl[r + 1]);
+          float2 a[4];
+  #pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float dcf = d0 + (float)u;
+            const float *line = buf + (cc + u) * ls;
+            const float2 q = __ffma2_rn(make_float2(dcf, dcf), t2, r2);
+            const float2 tq = __fadd2_rd(q, kMagic2);
+            int i0 = boff[r] + (__float_as_int(tq.x) - kMagicBits);
+            int i1 = boff[r + 1] + (__float_as_int(tq.y) - kMagicBits);
+            if (!IMASK_INDEX_OK(i0 >= 0 && i0 + 1 < ls, 1)) i0 = 0;
+            if (!IMASK_INDEX_OK(i1 >= 0 && i1 + 1 < ls, 1)) i1 = 0;
+            // f = q - (tq - magic), the subtraction as a fused multiply-add by -1
+            const float2 f = __ffma2_rn(__fadd2_rn(tq, kNegMagic2), kMinusOne2, q);
+            const float2 v0 = make_float2(line[i0], line[i1]);
+            const float2 v1 = make_float2(line[i0 + 1], line[i1 + 1]);
+            // independent samples, summed as a tree
+            a[u] = __ffma2_rn(f, __ffma2_rn(v0, kMinusOne2, v1), v0);
+          }
+          const float2 sum = __fadd2_rn(__fadd2_rn(a[0], a[1]), __fadd2_rn(a[2], a[3]));
+          part[r] += sum.x;
+          part[r + 1] += sum.y;
         }
       }
-      const float d0 = (float)(c & (LBLOCK - 1));
-      // Rays go in pairs through the packed FP32x2 instructions of sm_100+
-      // (one issue slot for both rays; per component the rounding is that of
-      // the scalar operation, so the samples are bit for bit those of
-      // fmaf / __fadd_rd / subtraction).  A pair is skipped when neither of its
-      // slots has a ray on the grid in this block.
-#pragma unroll
-      for (int r = 0; r < FP_RAYS; r += 2) {
-        if (!(act & (3u << r))) continue;
-        const float2 t2 = make_float2(thi[r], thi[r + 1]);
-        const float2 r2 = make_float2(rl[r], rl[r + 1]);
-        float2 a[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float dcf = d0 + (float)u;
-          const float *line = buf + (cc + u) * ls;
-          const float2 q = __ffma2_rn(make_float2(dcf, dcf), t2, r2);
-          const float2 tq = __fadd2_rd(q, kMagic2);
-          int i0 = boff[r] + (__float_as_int(tq.x) - kMagicBits);
-          int i1 = boff[r + 1] + (__float_as_int(tq.y) - kMagicBits);
-          if (!IMASK_INDEX_OK(i0 >= 0 && i0 + 1 < ls, 1)) i0 = 0;
-          if (!IMASK_INDEX_OK(i1 >= 0 && i1 + 1 < ls, 1)) i1 = 0;
-          // f = q - (tq - magic), the subtraction as a fused multiply-add by -1
-          const float2 f = __ffma2_rn(__fadd2_rn(tq, kNegMagic2), kMinusOne2, q);
-          const float2 v0 = make_float2(line[i0], line[i1]);
-          const float2 v1 = make_float2(line[i0 + 1], line[i1 + 1]);
-          // independent samples, summed as a tree
-          a[u] = __ffma2_rn(f, __ffma2_rn(v0, kMinusOne2, v1), v0);
+  #pragma unroll
+      for (int r = 0; r < FP_RAYS; ++r) acc[r] += part[r];
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();   // this warp's reads of the stage come first
+        const unsigned n = atomicAdd(&released[st], 1u) + 1u;
+        if (n % kWarps == 0u && s + FP_STAGES < nstrips) {
+          fence_proxy_async();
+          bulk_load(smem_u32(fp_smem + st * FP_STAGE_FLOATS),
+                    img + (size_t)(s + FP_STAGES) * tcv * ls, strip_bytes, smem_u32(&full_bar[st]));
+          issued[st] += 1u;   // only the last releaser of a stage issues its refill
         }
-        const float2 sum = __fadd2_rn(__fadd2_rn(a[0], a[1]), __fadd2_rn(a[2], a[3]));
-        part[r] += sum.x;
-        part[r + 1] += sum.y;
       }
     }
-#pragma unroll
-    for (int r = 0; r < FP_RAYS; ++r) acc[r] += part[r];
-    __syncwarp();
-    if (lane == 0) {
-      __threadfence_block();   // this warp's reads of the stage come first
-      const unsigned n = atomicAdd(&released[st], 1u) + 1u;
-      if (n % kWarps == 0u && s + FP_STAGES < nstrips) {
-        fence_proxy_async();
-        bulk_load(smem_u32(fp_smem + st * FP_STAGE_FLOATS),
-                  img + (size_t)(s + FP_STAGES) * tc * ls, strip_bytes, smem_u32(&full_bar[st]));
-        issued[st] += 1u;   // only the last releaser of a stage issues its refill
-      }
-    }
+  };
+  switch (tc) {
+    case 16: strips(std::integral_constant<int, 16>{}); break;
+    case 20: strips(std::integral_constant<int, 20>{}); break;
+    case 32: strips(std::integral_constant<int, 32>{}); break;
+    default: strips(std::integral_constant<int, 0>{}); break;
   }
   if (__syncthreads_or(failed)) {
     if (tid == 0) {
