@@ -848,7 +848,7 @@ __device__ void coarse_planes_sum(const float *g, int npl, int nl, int I0, int J
 
 // Block means of the tile `src` (side ts) at levels 1..r-1, level l at
 // pyr + pyr_off(l), side ts >> l.  Hierarchical 2x2 means.
-__device__ void tile_pyramid(const float *src, float *pyr, int ts, int r) {
+__device__ __forceinline__ void tile_pyramid(const float *src, float *pyr, int ts, int r) {
   const float *prev = src;
   int ps = ts, off = 0;
   for (int l = 1; l < r; ++l) {
@@ -872,12 +872,12 @@ __device__ __forceinline__ int pyr_off(int ts, int l) {
   return off;
 }
 
-// S_r v at tile pixel (li, lj): (v - sum_{l>=1} p_l mean_l) / p_0.
+// S_r v at tile pixel (li, lj): (v - sum_{l>=1} p_l mean_l) / p_0 (levels = r).
 __device__ __forceinline__ float compensate_px(const DevPlan &P, float v, const float *pyr, int ts,
-                                               int li, int lj) {
+                                               int li, int lj, int levels) {
   float s = v;
   int off = 0;
-  for (int l = 1; l < P.levels; ++l) {
+  for (int l = 1; l < levels; ++l) {
     const int side = ts >> l;
     s = fmaf(-P.probs[l], pyr[off + (li >> l) * side + (lj >> l)], s);
     off += side * side;
@@ -889,7 +889,8 @@ __device__ __forceinline__ float compensate_px(const DevPlan &P, float v, const 
 // (-1: plain grid).  `vals` holds the level values of the tile (side `side`).
 // With a snapshot array S of the level (ell >= 0) the images receive
 // vals - S, S takes vals, and vals is overwritten with the difference.
-__device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, float *vals,
+__device__ __forceinline__ void write_padded(const DevPlan &P, const PadSet &pads, int ell,
+                                             float *vals,
                              int side, int ti0, int tj0, float *S) {
   const int li = ell + 1;
   const LevelGeom G = P.lg[li];
@@ -919,17 +920,18 @@ __device__ void write_padded(const DevPlan &P, const PadSet &pads, int ell, floa
 }
 
 // Sketch of the tile held in xs (fine values) for level ell; uses aux and pyr.
-// S: the level's snapshot array (snapshot tables) or nullptr.
-__device__ void sketch_tile(const DevPlan &P, const PadSet &pads, int ell, float *xs, float *aux,
-                            float *pyr, int ts, int ti0, int tj0, float *S) {
+// S: the level's snapshot array (snapshot tables) or nullptr; levels = r.
+__device__ __forceinline__ void sketch_tile(const DevPlan &P, const PadSet &pads, int ell,
+                                            float *xs, float *aux, float *pyr, int ts, int ti0,
+                                            int tj0, float *S, int levels) {
   if (ell < 0) {
     write_padded(P, pads, -1, xs, ts, ti0, tj0, nullptr);
     return;
   }
-  if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
+  if (levels > 1) tile_pyramid(xs, pyr, ts, levels);
   if (ell == 0) {
     for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
-      aux[p] = compensate_px(P, xs[p], pyr, ts, p >> lg2i(ts), p & (ts - 1));
+      aux[p] = compensate_px(P, xs[p], pyr, ts, p >> lg2i(ts), p & (ts - 1), levels);
     __syncthreads();
     write_padded(P, pads, 0, aux, ts, ti0, tj0, S);
   } else {
@@ -954,7 +956,7 @@ __global__ void __launch_bounds__(UPD_THREADS)
   }
   __syncthreads();
   float *S = (sn.snap && ell >= 0) ? sn.snap + sn.snap_off[ell] : nullptr;
-  sketch_tile(P, pads, ell, xs, aux, pyr, ts, ti0, tj0, S);
+  sketch_tile(P, pads, ell, xs, aux, pyr, ts, ti0, tj0, S, P.levels);
 }
 
 // img = K_ell^T-side image map of g: ell >= 1: 4^-ell T^* g; ell = 0: S_r g;
@@ -991,18 +993,20 @@ __global__ void __launch_bounds__(UPD_THREADS)
   if (P.levels > 1) tile_pyramid(xs, pyr, ts, P.levels);
   for (int p = threadIdx.x; p < ts * ts; p += blockDim.x)
     img[(size_t)(ti0 + (p >> lts)) * n + tj0 + (p & (ts - 1))] =
-        compensate_px(P, xs[p], pyr, ts, p >> lts, p & (ts - 1));
+        compensate_px(P, xs[p], pyr, ts, p >> lts, p & (ts - 1), P.levels);
 }
 
 // Primal half of Alg. 1 on one tile, then the sketch of the new iterate for
 // the next level.  phi_new = 4^-ell T^*(g) (ell >= 1, block-constant, kept on
 // the level grid) or S_r g (ell = 0); xi = phi_new - phi_ell + sum p phi;
 // x+ = prox(x - (sigma/mu) xi); the running mean and the table take phi_new.
+// ts (the plan's update tile) and levels (r) come in as arguments, so that a
+// call with constants compiles the tile loops for that shape.
 __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &sel,
                                             const PrimalArgs &A, int write_sketch,
-                                            const PadSet &pads, int bid) {
+                                            const PadSet &pads, int bid, int ts, int levels) {
   extern __shared__ __align__(16) float upd_smem[];
-  const int ts = P.upd_tile, ntx = P.n / ts, lts = lg2i(ts);
+  const int ntx = P.n / ts, lts = lg2i(ts);
   float *xs = upd_smem, *aux = xs + ts * ts, *pyr = aux + ts * ts;
   float *dc = pyr + ts * ts / 2 + 4;
   float *dm = dc + ts * ts / 4 + 4;
@@ -1088,7 +1092,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
       }
     }
     __syncthreads();
-    if (P.levels > 1) tile_pyramid(aux, pyr, ts, P.levels);
+    if (levels > 1) tile_pyramid(aux, pyr, ts, levels);
   }
 
   for (int p0 = threadIdx.x; p0 < ts * ts; p0 += kUpdPix * blockDim.x) {
@@ -1104,7 +1108,7 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
         delta = dc[(li >> ell) * cs + (lj >> ell)];
         dmean = dm[(li >> ell) * cs + (lj >> ell)];
       } else {
-        const float s0 = compensate_px(P, aux[p], pyr, ts, li, lj);
+        const float s0 = compensate_px(P, aux[p], pyr, ts, li, lj, levels);
         delta = s0 - ph0[u];
         dmean = tab_store(A.phi0, gp, s0, fmt) - ph0[u];
       }
@@ -1124,12 +1128,17 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
   __syncthreads();
   const int elln = draw_level(P, sel.seed, sel_k(sel) + 1);
   float *S = A.snap.snap ? A.snap.snap + A.snap.snap_off[elln] : nullptr;
-  sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0, S);
+  sketch_tile(P, pads, elln, xs, aux, pyr, ts, ti0, tj0, S, levels);
 }
 
 __global__ void __launch_bounds__(UPD_THREADS)
     k_update(DevPlan P, LevelSel sel, PrimalArgs A, int write_sketch, PadSet pads) {
-  update_body(P, sel, A, write_sketch, pads, (int)blockIdx.x);
+  // the 32-pixel tile of a four-level plan compiled on its own, any other shape
+  // with runtime loops
+  if (P.upd_tile == 32 && P.levels == 4)
+    update_body(P, sel, A, write_sketch, pads, (int)blockIdx.x, 32, 4);
+  else
+    update_body(P, sel, A, write_sketch, pads, (int)blockIdx.x, P.upd_tile, P.levels);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1167,7 +1176,7 @@ __global__ void __launch_bounds__(UPD_THREADS, 3)
   const int b = (int)blockIdx.x;
   const int s = slice_of(upd_start, n, b);
   const FusedSlice &R = recs[s];
-  update_body(R.P, R.sel, R.A, 1, R.pads_upd, b - upd_start[s]);
+  update_body(R.P, R.sel, R.A, 1, R.pads_upd, b - upd_start[s], R.P.upd_tile, R.P.levels);
 }
 
 // Items of every solve's back-projection at its drawn level, as offsets into
