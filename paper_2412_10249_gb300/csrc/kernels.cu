@@ -1045,14 +1045,21 @@ __device__ __forceinline__ void update_body(const DevPlan &P, const LevelSel &se
     const int I0 = ti0 >> ell, J0 = tj0 >> ell;
     const long long off = A.phic_off[ell];
     const float inv4l = G.inv2l * G.inv2l;
+    auto table_index = [&](int p) {
+      return (size_t)off + (size_t)(I0 + (p >> (lts - ell))) * G.nl + J0 + (p & (cs - 1));
+    };
+    // the table entry of the thread's first coarse pixel is loaded before the
+    // plane sums, so that the two loads are in flight together
+    const int p_first = (int)threadIdx.x;
+    const float old_first = p_first < cs * cs ? tab_load(A.phic, table_index(p_first), fmt) : 0.0f;
     coarse_planes_sum(A.g, 2 * G.bp_vgo, G.nl, I0, J0, cs, dc);
     // xi takes the refreshed value's change, the running mean the stored
     // (rounded, with 16-bit tables) value's change, so that the mean stays the
     // p-weighted sum of the stored tables
     for (int p = threadIdx.x; p < cs * cs; p += blockDim.x) {
-      const size_t gi = (size_t)off + (size_t)(I0 + (p >> (lts - ell))) * G.nl + J0 + (p & (cs - 1));
+      const size_t gi = table_index(p);
       const float cnew = dc[p] * inv4l;
-      const float old = tab_load(A.phic, gi, fmt);
+      const float old = p == p_first ? old_first : tab_load(A.phic, gi, fmt);
       const float stored = tab_store(A.phic, gi, cnew, fmt);
       dc[p] = cnew - old;
       dm[p] = stored - old;
