@@ -69,3 +69,26 @@ def test_shared_memory_probe(imask):
     bound = n_sm * 128 * 2.2e9 / 1e9
     assert 0.2 * bound < load < 1.1 * bound
     assert 0.1 * bound < rmw < 1.1 * bound
+
+
+def test_strip_loop_variants_keep_parity(imask):
+    # The projector's strip loop is compiled separately for strip heights of
+    # 16, 20 and 32 lines and once for any other height.  Plans whose default
+    # heights hit every one of them (n = 80: 20 at level 0; n = 64: 32, 32,
+    # 16 and 8; n = 48: 24, 24, 12 and 8) project within the operator
+    # tolerance of the oracle at every level.
+    seen = set()
+    for n, lv in ((80, 3), (64, 4), (48, 4)):
+        prob = inputs.Problem(n=n, n_angles=30, n_det=int(1.5 * n) + 1, geometry=1,
+                              angle_span=2 * math.pi, levels=lv)
+        params = dict(prob.params(), mu=0.1, sigma=0.04)
+        plan = imask.Plan(params)
+        heights = plan.info["fp_strip_lines"][:lv]
+        seen.update(heights)
+        o = Oracle(**params)
+        x = np.random.default_rng(n).standard_normal(n * n)
+        xt = torch.as_tensor(x.astype(np.float32), device="cuda")
+        for ell in range(lv):
+            got = plan.project(ell, xt).double().cpu().numpy()
+            assert rel(got, o.K(ell, x)) <= 1e-5, (n, ell, heights[ell])
+    assert {16, 20, 32} <= seen and seen - {16, 20, 32}, seen
