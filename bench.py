@@ -268,7 +268,7 @@ def run_reference(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+        "config": workload_config(p, args, world),
         "gsamples_per_s": gs,
         "cpu_baseline": {"value": solves, "unit": "solves/s", "cores": pool.cores,
                          "kind": "oracle", "cpu_model": host["cpu_model"],
@@ -462,6 +462,21 @@ def l2_copy_gbs(torch, stream, mib: int = 32, reps: int = 20) -> float:
 def variant_params(variant: str, dual_tables: int, draws: int) -> dict:
     return {"variant": 1 if variant == "seq" else 0, "theta": 1.0,
             "dual_tables": int(dual_tables), "draws": int(draws)}
+
+
+L2_NOTE = ("GPU arm: L2 flushed between steps (512 MB write outside the step events); "
+           "CPU reference arm: no flush (FP64 oracle processes)")
+
+
+def workload_config(p, args, world: int) -> dict:
+    """The `config` object of the JSON line: what the workload is, the same for
+    the GPU arm and the reference arm (what a plan chooses on the device, its
+    step sizes and tuned splits, goes to the line's `plan` object)."""
+    return {"workload": WORKLOAD, "n": p.n, "views": p.n_angles, "bins": p.n_det,
+            "levels": p.levels, "iters_per_solve": args.iters,
+            "iteration": dict(variant_params(args.variant, args.dual_tables, args.draws),
+                              autotune=args.autotune),
+            "l2": L2_NOTE, "parallelism": f"replicas x{world}"}
 
 
 VARIANT_SET = {
@@ -1263,14 +1278,10 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded random-ellipse phantom, exact fan-beam line integrals, "
                     "Poisson I0=1e4)",
-            "config": {"workload": WORKLOAD, "n": p.n, "views": p.n_angles, "bins": p.n_det,
-                       "levels": p.levels, "iters_per_solve": args.iters,
-                       "iteration": vopts,
-                       "mu": info["mu"], "sigma": info["sigma"], "theta": info["theta"],
-                       "bp_view_groups": list(info["bp_view_groups"][:p.levels]),
-                       "fp_strip_lines": list(info["fp_strip_lines"][:p.levels]),
-                       "l2": "flushed between steps (512 MB write outside the step events)",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(p, args, world),
+            "plan": {"mu": info["mu"], "sigma": info["sigma"], "theta": info["theta"],
+                     "bp_view_groups": list(info["bp_view_groups"][:p.levels]),
+                     "fp_strip_lines": list(info["fp_strip_lines"][:p.levels])},
             "gsamples_per_s": gs,
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "rel_err_vs_plain_fp32": rel_err_plain,
@@ -1291,7 +1302,7 @@ def run_ours(args):
     return 0
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -1336,6 +1347,15 @@ def main():
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--sigma", type=float, default=0.0)
+    return ap
+
+
+def parse_args(argv=None):
+    return build_parser().parse_args(argv)
+
+
+def main():
+    ap = build_parser()
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -161,3 +161,14 @@ def test_oracle_pool_runs_independent_processes(oracle_lib):
                .sum() for s in (0, 1)]
     assert samples == pytest.approx(sum(per_run))
     assert wall > 0
+
+
+def test_both_arms_name_the_same_workload_config():
+    # the GPU arm and the reference arm print one `config` object built from
+    # the arguments alone (device-chosen values go to the GPU line's `plan`)
+    args = bench.parse_args([])
+    p = inputs.fan512_problem()
+    a, b = bench.workload_config(p, args, 1), bench.workload_config(p, args, 1)
+    assert a == b and a["workload"] == bench.WORKLOAD
+    assert not {"mu", "sigma", "theta", "bp_view_groups", "fp_strip_lines"} & set(a)
+    json.dumps(a)
