@@ -491,6 +491,61 @@ VARIANT_SET = {
 }
 
 
+def parallel512_problem():
+    """The paper's own geometry at the headline size: 512 x 512, parallel beam,
+    720 views over 180 degrees, ceil(sqrt(2) 512) = 725 bins at the pixel
+    pitch, r = 4 uniform levels."""
+    return inputs.Problem(n=512, n_angles=720, n_det=725, geometry=0, angle_span=math.pi,
+                          levels=4, reg=0, mu=1.0)
+
+
+def time_parallel_backprojectors(imask, iters, stream, flush, steps=3, period=16):
+    """Parallel-beam solves with the owner-computes and the pixel-driven
+    back-projector (bp_gather): solves/s, the back-projector's average launch
+    per level (CUDA events on every `period`-th iteration) and the distance
+    between the two results after `iters` iterations."""
+    import torch
+    p = parallel512_problem()
+    _, b, _ = inputs.measurements(p, seed=0)
+    bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
+    out, xs, mu, sigma = {}, {}, 0.0, 0.0
+    for name, gather in (("owner_scatter", 0), ("pixel_gather", 1)):
+        plan = imask.Plan(dict(p.params(), mu=mu, sigma=sigma, autotune=1, bp_gather=gather))
+        mu, sigma = plan.info["mu"], plan.info["sigma"]
+        x = torch.empty(p.d, device="cuda", dtype=torch.float32)
+        with torch.cuda.stream(stream):
+            plan.solve(bt, 777, iters, out=x, stream=stream)
+        stream.synchronize()
+        imask.imask_profile_read(reset=True)
+        imask.imask_profile_enable(period)
+        ms = []
+        for k in range(steps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+                a.record(stream)
+                plan.solve(bt, 5000 + k, iters, out=x, stream=stream)
+                e.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(e))
+        imask.imask_profile_enable(False)
+        pms, pcnt = imask.imask_profile_read(reset=True)
+        plan.check()
+        bp_us = {f"l{l}": round(1e3 * pms[8 + l] / pcnt[8 + l], 1)
+                 for l in range(p.levels) if pcnt[8 + l] > 0}
+        out[name] = {"solves_per_s": 1e3 * steps / float(sum(ms)),
+                     "back_projector_us_by_level": bp_us,
+                     "bp_view_groups": list(plan.info["bp_view_groups"][:p.levels])}
+        xs[name] = x.double().cpu().numpy()
+        plan.close()
+    out["rel_diff_x"] = float(np.linalg.norm(xs["pixel_gather"] - xs["owner_scatter"]) /
+                              np.linalg.norm(xs["owner_scatter"]))
+    out["speedup"] = out["pixel_gather"]["solves_per_s"] / out["owner_scatter"]["solves_per_s"]
+    out["config"] = {"workload": "par512: 512x512 parallel beam 720 views over 180 deg x 725 "
+                                 "bins, r=4 uniform, K=%d, quadratic R, autotuned" % iters}
+    return out
+
+
 def time_variants(imask, p, bt, info, iters, stream, flush, x, steps=3):
     """solves/s of each variant over `steps` solves (after one warm-up solve),
     same workload, mu and (Alg. 1) sigma; Alg. 7 takes sigma = 0.05; then the
@@ -1218,6 +1273,8 @@ def run_ours(args):
     if not args.no_variants:
         plain_ref = imask.Plan(dict(p.params(), mu=info["mu"], sigma=info["sigma"]))
         variants = time_variants(imask, p, bt, info, args.iters, stream, flush, x)
+        variants["parallel512_backprojectors"] = time_parallel_backprojectors(
+            imask, args.iters, stream, flush)
         variants["batch_fan512"] = time_batch_fan512(imask, p, bt, info, args.iters, stream)
         # the spec comparison: the batched 16-bit form against the plain
         # fp32 form (the headline value) at the same seed
@@ -1347,6 +1404,9 @@ def build_parser() -> argparse.ArgumentParser:
                     help="time the kernels of every N-th iteration with CUDA events")
     ap.add_argument("--mu", type=float, default=0.0)
     ap.add_argument("--sigma", type=float, default=0.0)
+    ap.add_argument("--parallel", action="store_true",
+                    help="only the parallel-beam line: owner-computes against pixel-driven "
+                         "back-projector")
     return ap
 
 
@@ -1368,6 +1428,16 @@ def main():
         return run_reference(args)
     if args.probe:
         return run_probe(args)
+    if args.parallel:
+        import torch
+        from paper_2412_10249_gb300 import build as pkg_build
+        pkg_build.build()
+        from paper_2412_10249_gb300 import imask
+        stream = torch.cuda.Stream()
+        flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda", dtype=torch.float32)
+        line = time_parallel_backprojectors(imask, args.iters, stream, flush)
+        print(json.dumps(line))
+        return 0
     if args.ablation:
         return run_ablation(args)
     if args.batch:

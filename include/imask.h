@@ -102,6 +102,17 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               point by about the format's precision;
  *               imask_state_set_storage(state, 0, ...) switches a state to
  *               fp32 tables for a refinement sweep.
+ *  bp_gather    parallel beam (geometry 0) only, else IMASK_ERR_INVALID:
+ *               the back-projector of every call and solve of the plan is
+ *               pixel-driven -- each pixel adds Lambda(q - i) g y over the
+ *               few bins of every view whose ray passes within one pixel of
+ *               it (Joseph's weights, the transpose of the projector up to
+ *               fp32 rounding of the pixel's local offsets, a few 1e-6 of a
+ *               weight) -- instead of owner-computes (exact to the last bit).
+ *               Fused batches (imask_batch_create_fused) refuse such plans;
+ *               IMASK_ERR_SHAPE when a level's ray window per 16-pixel tile
+ *               would exceed the kernel's staging (detector pitch far below
+ *               the pixel width at coarse levels).
  *  draws        0: one level per iteration (Alg. 1); 1: the primal level
  *               (back-projector, image-side tables) is drawn from a second
  *               SplitMix64 stream whose seed is the SplitMix64 finaliser of
@@ -127,6 +138,9 @@ typedef struct {
   int32_t autotune;                      /* 1: time, per level at plan time, the
                                             back-projector's view-group split and
                                             the projector's strip height */
+  int32_t bp_gather;                     /* parallel beam only: 1 computes K_l^T
+                                            pixel by pixel (see below), 0 by the
+                                            owners of tile segments */
 } imask_desc;
 
 /* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,

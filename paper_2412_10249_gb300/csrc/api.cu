@@ -127,6 +127,7 @@ struct imask_plan_s {
   float2 *d_rays_lo = nullptr;
   ViewInfo *d_views = nullptr;
   int *d_bp_order = nullptr;
+  float *d_view_da = nullptr;   // per view, a's step from one bin to the next (parallel)
   int *d_bp_views = nullptr;    // per role, the views holding rays of that role
   int *d_bp_vb = nullptr;       // per level and role, the view-group bounds
   std::vector<int> role_rays[2];   // rays of the role in each listed view
@@ -269,6 +270,11 @@ imask_status validate(const imask_desc *d) {
   if (d->step_rule < 0 || d->step_rule > 2)
     return fail(IMASK_ERR_INVALID, "step_rule must be 0, 1 or 2");
   if (d->autotune != 0 && d->autotune != 1) return fail(IMASK_ERR_INVALID, "autotune must be 0 or 1");
+  if (d->bp_gather != 0 && d->bp_gather != 1)
+    return fail(IMASK_ERR_INVALID, "bp_gather must be 0 or 1");
+  if (d->bp_gather == 1 && d->geometry != 0)
+    return fail(IMASK_ERR_INVALID, "the pixel-driven back-projector (bp_gather) is for parallel "
+                                   "beam only");
   if (d->power_iters < 0 || d->power_iters > 100000)
     return fail(IMASK_ERR_INVALID, "power_iters must be in [0, 100000]");
   if (d->geometry == 1) {
@@ -1135,6 +1141,9 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   std::vector<float4> rays((size_t)na * nd);
   std::vector<float2> rays_lo((size_t)na * nd);
   std::vector<ViewInfo> views(na);
+  std::vector<float> view_da(na, 0.0f);   // parallel beam: a's step per bin, per view
+  std::vector<float> view_t(na, 0.0f);    // parallel beam: the view's slope
+  std::vector<double> view_a0(na, 0.0);   // a of the view's first bin
   int m_x = 0;
   for (int a = 0; a < na; ++a) {
     const int sp = p->split[a];
@@ -1170,6 +1179,13 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
       // a = (cross coordinate at the centre line + W/2) / h, split into two
       // floats, and the slope t likewise (see block_origin in kernels.cu)
       const double av = (c0 + 0.5 * W) / h;
+      if (j == 0) {
+        view_t[a] = (float)t;
+        view_a0[a] = av;
+        view_da[a] = 1.0f;   // one bin: any step
+      } else if (j == 1) {
+        view_da[a] = (float)(av - view_a0[a]);
+      }
       float4 e;
       e.x = (float)av;
       e.y = (float)t;
@@ -1207,6 +1223,30 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.lg[0] = level_geom(*desc, -1);
   for (int l = 0; l < r; ++l) dp.lg[l + 1] = level_geom(*desc, l);
   dp.upd_tile = update_tile(desc->n, r);
+  // pixel-driven back-projector: per level, the most bins of one view that
+  // cross a GW_TILE x GW_TILE tile (the tile widened by one pixel across the
+  // rays' major axis, the slope's drift along it), and the views staged at once
+  dp.bp_gather = desc->bp_gather;
+  if (dp.bp_gather) {
+    for (int li = 0; li <= r; ++li) {
+      LevelGeom &g = dp.lg[li];
+      double wmax = 1.0;
+      for (int a = 0; a < na; ++a) {
+        const double D = fabs((double)view_da[a]) * (double)g.inv2l;
+        const double span = (GW_TILE + 1) + (GW_TILE - 1) * fabs((double)view_t[a]);
+        const double b = nd > 1 ? ceil(span / std::max(D, 1e-9)) + 3.0 : 1.0;
+        wmax = std::max(wmax, std::min(b, (double)nd));
+      }
+      if (wmax > GW_SLOTS - 18) {   // a window and its zero padding must fit
+        imask_plan_destroy(p);
+        return fail(IMASK_ERR_SHAPE,
+                    "pixel-driven back-projector: %d bins of one view cross a tile at level "
+                    "%d, more than the %d it stages", (int)wmax, li - 1, GW_SLOTS - 18);
+      }
+      g.gw_max = (int)wmax;
+      g.gw_vc = std::max(1, std::min(128, GW_SLOTS / (g.gw_max + 18)));
+    }
+  }
   // Grid sizes from the SM count: the projector runs exactly one wave of
   // 2 CTAs per SM (ray chunks shrink below FP_CHUNK to fill it); the
   // back-projector's view groups are chosen for the best last-wave fill at
@@ -1290,6 +1330,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
       (e = cudaMalloc(&p->d_views, views.size() * sizeof(ViewInfo))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_err, sizeof(unsigned int))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_bp_order, order.size() * sizeof(int))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_view_da, view_da.size() * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_bp_views, role_views.size() * sizeof(int))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_bp_vb, (size_t)(r + 1) * 2 * (na + 1) * sizeof(int))) !=
           cudaSuccess) {
@@ -1314,6 +1355,8 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(p->d_bp_order, order.data(), order.size() * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(p->d_view_da, view_da.data(), view_da.size() * sizeof(float),
+                           cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemcpyAsync(p->d_bp_views, role_views.data(), role_views.size() * sizeof(int),
                            cudaMemcpyHostToDevice, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(p->d_err, 0, sizeof(unsigned int), st)) != cudaSuccess ||
@@ -1327,6 +1370,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.rays_lo = p->d_rays_lo;
   dp.views = p->d_views;
   dp.bp_order = p->d_bp_order;
+  dp.view_da = p->d_view_da;
   dp.bp_views = p->d_bp_views;
   dp.bp_vb = p->d_bp_vb;
   for (int li = 0; li <= r && rc == IMASK_OK; ++li) rc = upload_bp_groups(p, li, st);
@@ -1354,6 +1398,7 @@ imask_status imask_plan_destroy(imask_plan_t p) {
   if (p->d_views) cudaFree(p->d_views);
   if (p->d_err) cudaFree(p->d_err);
   if (p->d_bp_order) cudaFree(p->d_bp_order);
+  if (p->d_view_da) cudaFree(p->d_view_da);
   if (p->d_bp_views) cudaFree(p->d_bp_views);
   if (p->d_bp_vb) cudaFree(p->d_bp_vb);
   delete p;
@@ -2070,10 +2115,15 @@ imask_status imask_batch_create_fused(const imask_state_t *states, int32_t n_sta
   if (!states || !batch_out || n_states < 1) return fail(IMASK_ERR_INVALID, "bad argument");
   if (n_states > IMASK_MAX_FUSED)
     return fail(IMASK_ERR_INVALID, "a fused batch holds at most %d states", IMASK_MAX_FUSED);
-  for (int i = 0; i < n_states; ++i)
+  for (int i = 0; i < n_states; ++i) {
     if (states[i] && states[i]->plan->desc.reg != 0)
       return fail(IMASK_ERR_INVALID,
                   "state %d: fused batches take the quadratic regulariser (reg = 0) only", i);
+    if (states[i] && states[i]->plan->desc.bp_gather != 0)
+      return fail(IMASK_ERR_INVALID,
+                  "state %d: fused batches run the owner-computes back-projector, not the "
+                  "pixel-driven one (bp_gather)", i);
+  }
   imask_status rc = imask_batch_create(states, n_states, batch_out);
   if (rc != IMASK_OK) return rc;
   imask_batch_s *b = *batch_out;

@@ -27,6 +27,8 @@
 #endif
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin);
                                // equal to BP_W so a back-projector tile is one block
+#define GW_TILE 16             // gather back-projector: tile side (pixels), one pixel per thread
+#define GW_SLOTS 4096          // gather back-projector: staged bins per chunk of views
 #ifndef UPD_THREADS
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
 #endif
@@ -56,6 +58,8 @@ struct LevelGeom {
   int bp_vgo;      // back-projector view groups per major axis (partial sums)
   int bp_nv;       // largest number of views handled by one CTA
   int bp_order_off;  // this level's entries in DevPlan::bp_order
+  int gw_max;      // gather back-projector: most bins of one view that cross a tile
+  int gw_vc;       // gather back-projector: views staged together (GW_SLOTS / gw_max)
 };
 
 // Everything the kernels need about a plan (passed by value).
@@ -68,6 +72,8 @@ struct DevPlan {
   unsigned long long thr[IMASK_MAX_LEVELS];   // level thresholds (r - 1 used)
   LevelGeom lg[IMASK_MAX_LEVELS + 1];
   int upd_tile;      // fine-pixel tile side of the sketch / update kernels
+  int bp_gather;     // 1: the pixel-driven back-projector (parallel beam), 0: owner scatter
+  const float *view_da;   // parallel beam: per view, the change of a from one bin to the next
   int fp_chunk_x;    // projector: x-major rays per CTA (<= FP_CHUNK)
   int fp_chunk_y;    // projector: y-major rays per CTA (<= FP_CHUNK)
   const float4 *rays;      // ray list: (a_hi, t_hi, g, sino index bits)

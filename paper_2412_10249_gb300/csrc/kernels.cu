@@ -785,6 +785,171 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
   bp_body(P, sel, y, y_list, gout, err, nv_cap, (int)blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------------
+// Pixel-driven back-projector for parallel beam (plans with bp_gather = 1):
+// g = R_ell^T y computed pixel by pixel, each pixel's sum in a register.
+//
+// Joseph's weight of ray j at pixel (i, c) is Lambda(q_j(c) - i) (x-major
+// rays; q_j(c) the ray's cross coordinate at line c, Lambda(u) = max(0,
+// 1 - |u|)), and Lambda(q_j(i) - c) for y-major rays -- the same weights the
+// projector applies.  In parallel beam the rays of a view share their slope
+// and their intercepts a_j step by a constant D per bin, so with the local
+// frame (I, r) of one reference ray j0 at the tile's first line (block_origin,
+// as in the projector) q_{j0+e}(m0 + d) = I + r + d t + e D 2^-ell, and a
+// pixel finds the few bins with weight (|q - i| < 1) from one division-free
+// estimate instead of visiting rays.
+//
+// CTA = a GW_TILE x GW_TILE tile of level pixels (one per thread) and one view
+// group vg; it covers that group's x-major views (partial image role 0) and
+// y-major views (role 1), so it writes the same 2 bp_vgo partial images as the
+// owner-computes back-projector and the consumer adds them the same way.
+// Views go in chunks of gw_vc; for each the bins crossing the tile (the ray
+// window of the scatter, from the bin map at the tile's corners) are staged
+// as g y in shared memory, at most gw_max per view (plan-time bound).
+// ---------------------------------------------------------------------------------
+__global__ void __launch_bounds__(GW_TILE * GW_TILE)
+    k_bp_gather(DevPlan P, LevelSel sel, const float *__restrict__ y, int y_list,
+                float *__restrict__ gout, unsigned int *err) {
+  constexpr int kThreads = GW_TILE * GW_TILE;
+  constexpr int kMaxVc = 128;
+  constexpr int kGwPad = 9;   // zeros staged on either side of a view's window
+  __shared__ float yg[GW_SLOTS];
+  __shared__ float4 vf[kMaxVc];   // per staged view: (r, t, D_ell, 1 / D_ell)
+  __shared__ int4 vi[kMaxVc];     // per staged view: (I, bins staged, candidates, y index)
+  __shared__ float vw[kMaxVc];    // per staged view: the rays' weight g
+  const int ell = sel_level_x(P, sel);
+  const LevelGeom G = P.lg[ell + 1];
+  const int nt = (G.nl + GW_TILE - 1) / GW_TILE;
+  const int vgo = G.bp_vgo;
+  const int tile = (int)blockIdx.x / vgo, vg = (int)blockIdx.x % vgo;
+  if (tile >= nt * nt) return;
+  const int i0 = (tile / nt) * GW_TILE, c0 = (tile % nt) * GW_TILE;
+  const int tid = threadIdx.x;
+  const int di = tid / GW_TILE, dc = tid % GW_TILE;
+  const int wmax = G.gw_max, wstr = wmax + 2 * kGwPad;   // window and its stride
+  const int vc = max(1, min(min(G.gw_vc, kMaxVc), GW_SLOTS / wstr));   // plan: wstr <= GW_SLOTS
+  const float hl = G.hl, W = P.fov;
+  float acc[2] = {0.0f, 0.0f};
+#pragma unroll
+  for (int role = 0; role < 2; ++role) {
+    const int *vb = P.bp_vb + ((ell + 1) * 2 + role) * (P.n_angles + 1);
+    const int a0 = vb[vg];
+    const int nv = vb[vg + 1] - a0;
+    const int *vlist = P.bp_views + role * P.n_angles + a0;
+    // march lines (columns for x-major rays) and cross lines of the tile
+    const int m0 = role == 0 ? c0 : i0, x0 = role == 0 ? i0 : c0;
+    const int m1 = min(m0 + GW_TILE, G.nl) - 1, x1 = min(x0 + GW_TILE, G.nl) - 1;
+    const float mlo = -0.5f * W + ((float)m0 + 0.5f) * hl, mhi = -0.5f * W + ((float)m1 + 0.5f) * hl;
+    const float clo = -0.5f * W + ((float)x0 + 0.5f) * hl - hl;
+    const float chi = -0.5f * W + ((float)x1 + 0.5f) * hl + hl;
+    const float cco = (float)m0 - G.cmid;
+    const float dm = (float)(role == 0 ? dc : di);   // own march offset in the tile
+    const int xo = role == 0 ? i0 + di : c0 + dc;    // own cross line
+    for (int v0 = 0; v0 < nv; v0 += vc) {
+      const int nvc = min(vc, nv - v0);
+      __syncthreads();   // the previous chunk's reads are done
+      if (tid < nvc) {
+        const int a = vlist[v0 + tid];
+        int len = 0, I = 0, nc = 0, ybase = 0;
+        float gw = 0.0f;
+        float4 f = make_float4(0.0f, 0.0f, 1.0f, 1.0f);
+        if (IMASK_INDEX_OK(a >= 0 && a < P.n_angles, 4)) {
+          const ViewInfo V = P.views[a];
+          float mn = 1.0e30f, mx = -1.0e30f;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float mcoord = (k & 1) ? mhi : mlo, ccoord = (k & 2) ? chi : clo;
+            const float j = role == 0 ? bin_of(P, V.c, V.s, mcoord, ccoord)
+                                      : bin_of(P, V.c, V.s, ccoord, mcoord);
+            mn = fminf(mn, j);
+            mx = fmaxf(mx, j);
+          }
+          const int j0 = role == 0 ? V.xj0 : V.yj0, j1 = role == 0 ? V.xj1 : V.yj1;
+          const int lo = max(ceil_i(clampf(mn - kBpEps, -1.0e6f, 1.0e6f)), j0);
+          const int hi = min(floor_i(clampf(mx + kBpEps, -1.0e6f, 1.0e6f)), j1 - 1);
+          len = max(hi - lo + 1, 0);
+          // (the plan's bound; a checked build records a window beyond it)
+          if (!IMASK_INDEX_OK(len <= wmax, 4)) len = wmax;
+          if (len > 0) {
+            const int list0 = (role == 0 ? V.xoff - V.xj0 : V.yoff - V.yj0) + lo;
+            const float4 pr = P.rays[list0];
+            const float2 pl = P.rays_lo[list0];
+            float r;
+            block_origin(pr.x, pl.x, pr.y, pl.y, G.inv2l, cco, I, r);
+            const float D = P.view_da[a] * G.inv2l;
+            const float inv = 1.0f / D;
+            // the bins e with |q - i| < 1 lie within 1 / |D| of the estimate
+            nc = (int)floorf(2.0f * fabsf(inv)) + 1;
+            f = make_float4(r, pr.y, D, inv);
+            ybase = y_list ? list0 : a * P.n_det + lo;
+            gw = pr.z;
+          }
+        }
+        vf[tid] = f;
+        vi[tid] = make_int4(I, len, nc, ybase);
+        vw[tid] = gw;
+      }
+      __syncthreads();
+      // stage g y of every view's window (a parallel view's rays share g),
+      // kGwPad zeros on either side of it
+      for (int k = tid; k < nvc * wstr; k += kThreads) {
+        const int v = k / wstr, e = k - v * wstr - kGwPad;
+        const int4 q = vi[v];
+        yg[k] = (e >= 0 && e < q.y) ? __ldg(y + q.w + e) * vw[v] : 0.0f;
+      }
+      __syncthreads();
+      for (int v = 0; v < nvc; ++v) {
+        const int4 q = vi[v];
+        if (q.y == 0) continue;   // uniform
+        const float4 f = vf[v];
+        // cross offset of the reference ray from this pixel at its line
+        const float ep = (float)(q.x - xo) + fmaf(dm, f.y, f.x);
+        const float u = -ep * f.w;                 // estimate of the bin with q = own line
+        const float rr = fabsf(f.w);
+        const int elo = ceil_i(u - rr);
+        const float *yv = yg + v * wstr + kGwPad;
+        // up to 3, 5 or 9 bins: a fixed, branch-free trip; the padding holds
+        // zeros for bins just outside the window, and a start clamped into
+        // the padding only skips bins of zero weight or outside the window
+        auto fixed_trip = [&](auto nc_const) {
+          constexpr int NC = decltype(nc_const)::value;
+          const int eb = min(max(elo, -kGwPad), q.y + kGwPad - NC);
+          const float d0 = fmaf((float)eb, f.z, ep);
+          float a = acc[role];
+#pragma unroll
+          for (int k = 0; k < NC; ++k) {
+            const float w = fmaxf(1.0f - fabsf(fmaf((float)k, f.z, d0)), 0.0f);
+            a = fmaf(w, yv[eb + k], a);
+          }
+          acc[role] = a;
+        };
+        if (q.z <= 3) {
+          fixed_trip(std::integral_constant<int, 3>{});
+        } else if (q.z <= 5) {
+          fixed_trip(std::integral_constant<int, 5>{});
+        } else if (q.z <= 9) {
+          fixed_trip(std::integral_constant<int, 9>{});
+        } else {
+          for (int k = 0; k < q.z; ++k) {
+            const int e = elo + k;
+            if ((unsigned)e < (unsigned)q.y) {
+              const float w = 1.0f - fabsf(fmaf((float)e, f.z, ep));
+              if (w > 0.0f) acc[role] = fmaf(w, yv[e], acc[role]);
+            }
+          }
+        }
+      }
+    }
+  }
+  const int i = i0 + di, c = c0 + dc;
+  if (i < G.nl && c < G.nl) {
+    const size_t plane = (size_t)G.nl * G.nl;
+#pragma unroll
+    for (int role = 0; role < 2; ++role)
+      gout[(size_t)(role * vgo + vg) * plane + (size_t)i * G.nl + c] = acc[role] * G.scale2l;
+  }
+}
+
 // The back-projector leaves 2 bp_vgo partial images (x- and y-major rays, one
 // per view group), each of side nl; their sum in a fixed order is R_ell^T y.
 // Sums planes v0, v0 + dv, ... (fewer than v1) at element idx in that order;
@@ -1665,6 +1830,19 @@ cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, int y_list
                       unsigned int *err, cudaStream_t st) {
   // the grid covers the level with the most (tile, view group) pairs; extra
   // CTAs return at once
+  if (P.bp_gather) {
+    // pixel-driven form: (tile, view group) CTAs of GW_TILE x GW_TILE pixels
+    auto gctas = [&](int li) {
+      const int nt = (P.lg[li].nl + GW_TILE - 1) / GW_TILE;
+      return nt * nt * P.lg[li].bp_vgo;
+    };
+    int most = 0;
+    for (int li = 0; li <= P.levels; ++li) most = max(most, gctas(li));
+    if (sel.fixed >= -1) most = gctas(sel.fixed + 1);
+    count_launch();
+    k_bp_gather<<<most, GW_TILE * GW_TILE, 0, st>>>(P, sel, y, y_list, g, err);
+    return cudaGetLastError();
+  }
   auto ctas = [&](int li) { return 2 * P.lg[li].bp_nm * P.lg[li].bp_nc * P.lg[li].bp_vgo; };
   int most = 0;
   for (int li = 0; li <= P.levels; ++li) most = max(most, ctas(li));

@@ -47,6 +47,7 @@ class Desc(ctypes.Structure):
         ("dual_tables", ctypes.c_int32), ("draws", ctypes.c_int32),
         ("step_rule", ctypes.c_int32), ("power_iters", ctypes.c_int32),
         ("autotune", ctypes.c_int32),
+        ("bp_gather", ctypes.c_int32),
     ]
 
 
@@ -191,6 +192,7 @@ def make_desc(params: dict):
     d.step_rule = int(params.get("step_rule", 0))
     d.power_iters = int(params.get("power_iters", 0))
     d.autotune = int(params.get("autotune", 0))
+    d.bp_gather = int(params.get("bp_gather", 0))
     return d, keep
 
 
