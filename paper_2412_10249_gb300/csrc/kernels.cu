@@ -42,7 +42,8 @@ constexpr int kWaitLimit = 1 << 20;      // bounded mbarrier polls before giving
 
 // Index checks of a checked build (-DIMASK_BOUNDS_CHECK): a computed index
 // outside its buffer sets a bit of this flag (1 projector image line, 2
-// back-projector staging, 3 sketch / update writes) and the access is skipped
+// back-projector staging, 3 sketch / update writes, 4 pixel-driven
+// back-projector views and windows) and the access is skipped
 // or redirected to element 0; the host reads the flag in imask_plan_check.
 // In the normal build the checks compile to nothing.
 __device__ unsigned int g_index_check_flag = 0u;
@@ -805,7 +806,8 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
 // owner-computes back-projector and the consumer adds them the same way.
 // Views go in chunks of gw_vc; for each the bins crossing the tile (the ray
 // window of the scatter, from the bin map at the tile's corners) are staged
-// as g y in shared memory, at most gw_max per view (plan-time bound).
+// as g y in shared memory, at most gw_max per view (plan-time bound), with
+// kGwPad zeros on either side so that a fixed trip of bins needs no test.
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(GW_TILE * GW_TILE)
     k_bp_gather(DevPlan P, LevelSel sel, const float *__restrict__ y, int y_list,

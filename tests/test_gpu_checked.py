@@ -39,8 +39,11 @@ CHILD = textwrap.dedent(r"""
     for prob in cases:
         params = dict(prob.params(), mu=0.1, sigma=0.04)
         o = Oracle(**params)
-        for extra in ({}, dict(variant=1, theta=1.0), dict(dual_tables=1, draws=1),
-                      dict(reg=2, tv_lambda=0.01, tv_inner=5), dict(storage=2), dict(autotune=1)):
+        extras = [{}, dict(variant=1, theta=1.0), dict(dual_tables=1, draws=1),
+                  dict(reg=2, tv_lambda=0.01, tv_inner=5), dict(storage=2), dict(autotune=1)]
+        if prob.geometry == 0:
+            extras.append(dict(bp_gather=1))   # the pixel-driven back-projector
+        for extra in extras:
             plan = imask.Plan(dict(params, **extra))
             img = rng.random((prob.n, prob.n))
             y = rng.standard_normal(o.m)
