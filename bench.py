@@ -337,8 +337,8 @@ def roofline_report(p, prof_ms, prof_cnt, dev, period=1, smem_probe=None, l2_gbs
     / average launch time against the measured shared-memory load ceiling.
     The FP32-ALU view is kept beside it, and every (kernel, level) is also
     put against the measured L2 copy and HBM bandwidth on its algorithmic
-    DRAM bytes (the memory view, where the fused epilogues and the coarse
-    levels are judged)."""
+    DRAM bytes (the memory view, the measure for the fused epilogues and the
+    coarse levels)."""
     best = int(np.argmax(prof_ms))
     kind, lvl = best // 8, best % 8
     cnt = max(1, prof_cnt[best])
@@ -1276,8 +1276,8 @@ def run_ours(args):
         variants["parallel512_backprojectors"] = time_parallel_backprojectors(
             imask, args.iters, stream, flush)
         variants["batch_fan512"] = time_batch_fan512(imask, p, bt, info, args.iters, stream)
-        # the spec comparison: the batched 16-bit form against the plain
-        # fp32 form (the headline value) at the same seed
+        # the mixed-precision comparison: the batched 16-bit form against the
+        # plain fp32 form (the headline value) at the same seed
         with torch.cuda.stream(stream):
             x_ref = plain_ref.solve(bt, 950, args.iters, stream=stream)
         torch.cuda.synchronize()
