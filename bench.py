@@ -1450,15 +1450,17 @@ def main():
 
 
 def run_probe(args):
-    """Bare K_ell / K_ell^T launches on the fan512 geometry (a small, fixed
-    workload for profilers): three of each per level, timed with CUDA events;
-    then four iterations of one solve."""
+    """Bare K_ell / K_ell^T launches on the fan512 geometry (with --parallel:
+    the 512 x 512 parallel-beam geometry and its pixel-driven back-projector),
+    a small, fixed workload for profilers: three of each per level, timed with
+    CUDA events; then four iterations of one solve."""
     import torch
     from paper_2412_10249_gb300 import build as pkg_build
     pkg_build.build()
     from paper_2412_10249_gb300 import imask
-    p = inputs.fan512_problem()
-    plan = imask.Plan(dict(p.params(), mu=0.25, sigma=0.03))
+    p = parallel512_problem() if args.parallel else inputs.fan512_problem()
+    extra = dict(bp_gather=1) if args.parallel else {}
+    plan = imask.Plan(dict(p.params(), mu=0.25, sigma=0.03, **extra))
     _, img = inputs.phantom(0, p.n)
     x = torch.as_tensor(img.ravel().astype(np.float32), device="cuda")
     y = torch.rand(p.m, device="cuda")

@@ -110,7 +110,7 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               fp32 rounding of the pixel's local offsets, a few 1e-6 of a
  *               weight) -- instead of owner-computes (exact to the last bit).
  *               Fused batches (imask_batch_create_fused) refuse such plans;
- *               IMASK_ERR_SHAPE when a level's ray window per 16-pixel tile
+ *               IMASK_ERR_SHAPE when a level's ray window per 16 x 32-pixel tile
  *               would exceed the kernel's staging (detector pitch far below
  *               the pixel width at coarse levels).
  *  draws        0: one level per iteration (Alg. 1); 1: the primal level

@@ -1224,16 +1224,24 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   for (int l = 0; l < r; ++l) dp.lg[l + 1] = level_geom(*desc, l);
   dp.upd_tile = update_tile(desc->n, r);
   // pixel-driven back-projector: per level, the most bins of one view that
-  // cross a GW_TILE x GW_TILE tile (the tile widened by one pixel across the
+  // cross a GW_TY x GW_TX tile (the tile widened by one pixel across the
   // rays' major axis, the slope's drift along it), and the views staged at once
   dp.bp_gather = desc->bp_gather;
   if (dp.bp_gather) {
     for (int li = 0; li <= r; ++li) {
       LevelGeom &g = dp.lg[li];
       double wmax = 1.0;
+      int ncmax = 1;
       for (int a = 0; a < na; ++a) {
+        // the kernel's count, in the same float operations
+        const float Df = view_da[a] * g.inv2l;
+        const float inv = 1.0f / Df;
+        ncmax = std::max(ncmax, (int)floorf(2.0f * fabsf(inv)) + 1);
         const double D = fabs((double)view_da[a]) * (double)g.inv2l;
-        const double span = (GW_TILE + 1) + (GW_TILE - 1) * fabs((double)view_t[a]);
+        // cross extent (lines + 1) plus the march extent's drift, for either
+        // orientation of the tile
+        const double at = fabs((double)view_t[a]);
+        const double span = std::max((GW_TY + 1) + (GW_TX - 1) * at, (GW_TX + 1) + (GW_TY - 1) * at);
         const double b = nd > 1 ? ceil(span / std::max(D, 1e-9)) + 3.0 : 1.0;
         wmax = std::max(wmax, std::min(b, (double)nd));
       }
@@ -1244,6 +1252,7 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
                     "%d, more than the %d it stages", (int)wmax, li - 1, GW_SLOTS - 18);
       }
       g.gw_max = (int)wmax;
+      g.gw_nc = ncmax;
       g.gw_vc = std::max(1, std::min(128, GW_SLOTS / (g.gw_max + 18)));
     }
   }

@@ -27,7 +27,9 @@
 #endif
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin);
                                // equal to BP_W so a back-projector tile is one block
-#define GW_TILE 16             // gather back-projector: tile side (pixels), one pixel per thread
+#define GW_TY 16               // gather back-projector: tile rows
+#define GW_TX 32               // gather back-projector: tile columns (two pixels per thread)
+#define GW_THREADS 256         // gather back-projector: threads per CTA
 #define GW_SLOTS 4096          // gather back-projector: staged bins per chunk of views
 #ifndef UPD_THREADS
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA
@@ -60,6 +62,7 @@ struct LevelGeom {
   int bp_order_off;  // this level's entries in DevPlan::bp_order
   int gw_max;      // gather back-projector: most bins of one view that cross a tile
   int gw_vc;       // gather back-projector: views staged together (GW_SLOTS / gw_max)
+  int gw_nc;       // gather back-projector: most bins with weight per pixel and view
 };
 
 // Everything the kernels need about a plan (passed by value).

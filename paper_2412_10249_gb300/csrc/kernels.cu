@@ -800,8 +800,8 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
 // pixel finds the few bins with weight (|q - i| < 1) from one division-free
 // estimate instead of visiting rays.
 //
-// CTA = a GW_TILE x GW_TILE tile of level pixels (one per thread) and one view
-// group vg; it covers that group's x-major views (partial image role 0) and
+// CTA = a GW_TY x GW_TX tile of level pixels (two per thread, GW_TX / 2
+// apart in a row, sharing the view parameters) and one view group vg; it covers that group's x-major views (partial image role 0) and
 // y-major views (role 1), so it writes the same 2 bp_vgo partial images as the
 // owner-computes back-projector and the consumer adds them the same way.
 // Views go in chunks of gw_vc; for each the bins crossing the tile (the ray
@@ -809,10 +809,11 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
 // as g y in shared memory, at most gw_max per view (plan-time bound), with
 // kGwPad zeros on either side so that a fixed trip of bins needs no test.
 // ---------------------------------------------------------------------------------
-__global__ void __launch_bounds__(GW_TILE * GW_TILE)
+__global__ void __launch_bounds__(GW_THREADS)
     k_bp_gather(DevPlan P, LevelSel sel, const float *__restrict__ y, int y_list,
                 float *__restrict__ gout, unsigned int *err) {
-  constexpr int kThreads = GW_TILE * GW_TILE;
+  constexpr int kThreads = GW_THREADS;
+  static_assert(GW_TX == 2 * (GW_THREADS / GW_TY), "two pixels per thread, GW_TX / 2 apart");
   constexpr int kMaxVc = 128;
   constexpr int kGwPad = 9;   // zeros staged on either side of a view's window
   __shared__ float yg[GW_SLOTS];
@@ -821,17 +822,19 @@ __global__ void __launch_bounds__(GW_TILE * GW_TILE)
   __shared__ float vw[kMaxVc];    // per staged view: the rays' weight g
   const int ell = sel_level_x(P, sel);
   const LevelGeom G = P.lg[ell + 1];
-  const int nt = (G.nl + GW_TILE - 1) / GW_TILE;
+  const int ntx = (G.nl + GW_TX - 1) / GW_TX, nty = (G.nl + GW_TY - 1) / GW_TY;
   const int vgo = G.bp_vgo;
   const int tile = (int)blockIdx.x / vgo, vg = (int)blockIdx.x % vgo;
-  if (tile >= nt * nt) return;
-  const int i0 = (tile / nt) * GW_TILE, c0 = (tile % nt) * GW_TILE;
+  if (tile >= ntx * nty) return;
+  const int i0 = (tile / ntx) * GW_TY, c0 = (tile % ntx) * GW_TX;
   const int tid = threadIdx.x;
-  const int di = tid / GW_TILE, dc = tid % GW_TILE;
+  // this thread's pixels: row i0 + di, columns c0 + dc and c0 + dc + GW_TX / 2
+  constexpr int kHalf = GW_TX / 2;
+  const int di = tid / kHalf, dc = tid % kHalf;
   const int wmax = G.gw_max, wstr = wmax + 2 * kGwPad;   // window and its stride
   const int vc = max(1, min(min(G.gw_vc, kMaxVc), GW_SLOTS / wstr));   // plan: wstr <= GW_SLOTS
   const float hl = G.hl, W = P.fov;
-  float acc[2] = {0.0f, 0.0f};
+  float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};   // [role][pixel]
 #pragma unroll
   for (int role = 0; role < 2; ++role) {
     const int *vb = P.bp_vb + ((ell + 1) * 2 + role) * (P.n_angles + 1);
@@ -840,13 +843,16 @@ __global__ void __launch_bounds__(GW_TILE * GW_TILE)
     const int *vlist = P.bp_views + role * P.n_angles + a0;
     // march lines (columns for x-major rays) and cross lines of the tile
     const int m0 = role == 0 ? c0 : i0, x0 = role == 0 ? i0 : c0;
-    const int m1 = min(m0 + GW_TILE, G.nl) - 1, x1 = min(x0 + GW_TILE, G.nl) - 1;
+    const int m1 = min(m0 + (role == 0 ? GW_TX : GW_TY), G.nl) - 1;
+    const int x1 = min(x0 + (role == 0 ? GW_TY : GW_TX), G.nl) - 1;
     const float mlo = -0.5f * W + ((float)m0 + 0.5f) * hl, mhi = -0.5f * W + ((float)m1 + 0.5f) * hl;
     const float clo = -0.5f * W + ((float)x0 + 0.5f) * hl - hl;
     const float chi = -0.5f * W + ((float)x1 + 0.5f) * hl + hl;
     const float cco = (float)m0 - G.cmid;
-    const float dm = (float)(role == 0 ? dc : di);   // own march offset in the tile
-    const int xo = role == 0 ? i0 + di : c0 + dc;    // own cross line
+    // own march offsets and cross lines in the tile (x-major rays march along
+    // the row, so the two pixels differ in march offset; y-major rays cross it)
+    const float dm0 = (float)(role == 0 ? dc : di), dm1 = (float)(role == 0 ? dc + kHalf : di);
+    const int xo0 = role == 0 ? i0 + di : c0 + dc, xo1 = role == 0 ? i0 + di : c0 + dc + kHalf;
     for (int v0 = 0; v0 < nv; v0 += vc) {
       const int nvc = min(vc, nv - v0);
       __syncthreads();   // the previous chunk's reads are done
@@ -882,6 +888,8 @@ __global__ void __launch_bounds__(GW_TILE * GW_TILE)
             const float inv = 1.0f / D;
             // the bins e with |q - i| < 1 lie within 1 / |D| of the estimate
             nc = (int)floorf(2.0f * fabsf(inv)) + 1;
+            // (the plan's per-level bound; a checked build records a view beyond it)
+            if (!IMASK_INDEX_OK(nc <= G.gw_nc, 4)) nc = G.gw_nc;
             f = make_float4(r, pr.y, D, inv);
             ybase = y_list ? list0 : a * P.n_det + lo;
             gw = pr.z;
@@ -900,55 +908,70 @@ __global__ void __launch_bounds__(GW_TILE * GW_TILE)
         yg[k] = (e >= 0 && e < q.y) ? __ldg(y + q.w + e) * vw[v] : 0.0f;
       }
       __syncthreads();
-      for (int v = 0; v < nvc; ++v) {
-        const int4 q = vi[v];
-        if (q.y == 0) continue;   // uniform
-        const float4 f = vf[v];
-        // cross offset of the reference ray from this pixel at its line
-        const float ep = (float)(q.x - xo) + fmaf(dm, f.y, f.x);
-        const float u = -ep * f.w;                 // estimate of the bin with q = own line
-        const float rr = fabsf(f.w);
-        const int elo = ceil_i(u - rr);
-        const float *yv = yg + v * wstr + kGwPad;
-        // up to 3, 5 or 9 bins: a fixed, branch-free trip; the padding holds
-        // zeros for bins just outside the window, and a start clamped into
-        // the padding only skips bins of zero weight or outside the window
-        auto fixed_trip = [&](auto nc_const) {
-          constexpr int NC = decltype(nc_const)::value;
-          const int eb = min(max(elo, -kGwPad), q.y + kGwPad - NC);
-          const float d0 = fmaf((float)eb, f.z, ep);
-          float a = acc[role];
+      // The level's largest bin count per pixel-view (plan time, the same
+      // float arithmetic as nc above) picks a fixed, branch-free trip of 3, 5
+      // or 9 bins for the whole chunk, else a bounded loop.  The padding
+      // holds zeros for bins just outside a window (empty windows included),
+      // and a start clamped into the padding only skips bins of zero weight
+      // or outside the window.
+      auto views = [&](auto nc_const) {
+        constexpr int NC = decltype(nc_const)::value;   // 0: the bounded loop
+        float a0 = acc[role][0], a1 = acc[role][1];
+#pragma unroll 2
+        for (int v = 0; v < nvc; ++v) {
+          const int4 q = vi[v];
+          const float4 f = vf[v];
+          const float *yv = yg + v * wstr + kGwPad;
+          // cross offset of the reference ray from the pixel at its line, the
+          // estimate of the bin that passes through the pixel, and its bins
+          auto pixel = [&](float dm, int xo, float &a) {
+            const float ep = (float)(q.x - xo) + fmaf(dm, f.y, f.x);
+            const int elo = ceil_i(fmaf(-ep, f.w, -fabsf(f.w)));
+            if constexpr (NC > 0) {
+              const int eb = min(max(elo, -kGwPad), q.y + kGwPad - NC);
+              const float d0 = fmaf((float)eb, f.z, ep);
 #pragma unroll
-          for (int k = 0; k < NC; ++k) {
-            const float w = fmaxf(1.0f - fabsf(fmaf((float)k, f.z, d0)), 0.0f);
-            a = fmaf(w, yv[eb + k], a);
-          }
-          acc[role] = a;
-        };
-        if (q.z <= 3) {
-          fixed_trip(std::integral_constant<int, 3>{});
-        } else if (q.z <= 5) {
-          fixed_trip(std::integral_constant<int, 5>{});
-        } else if (q.z <= 9) {
-          fixed_trip(std::integral_constant<int, 9>{});
-        } else {
-          for (int k = 0; k < q.z; ++k) {
-            const int e = elo + k;
-            if ((unsigned)e < (unsigned)q.y) {
-              const float w = 1.0f - fabsf(fmaf((float)e, f.z, ep));
-              if (w > 0.0f) acc[role] = fmaf(w, yv[e], acc[role]);
+              for (int k = 0; k < NC; ++k) {
+                const float w = fmaxf(1.0f - fabsf(fmaf((float)k, f.z, d0)), 0.0f);
+                a = fmaf(w, yv[eb + k], a);
+              }
+            } else {
+              for (int k = 0; k < q.z; ++k) {
+                const int e = elo + k;
+                if ((unsigned)e < (unsigned)q.y) {
+                  const float w = 1.0f - fabsf(fmaf((float)e, f.z, ep));
+                  if (w > 0.0f) a = fmaf(w, yv[e], a);
+                }
+              }
             }
-          }
+          };
+          pixel(dm0, xo0, a0);
+          pixel(dm1, xo1, a1);
         }
+        acc[role][0] = a0;
+        acc[role][1] = a1;
+      };
+      if (G.gw_nc <= 3) {
+        views(std::integral_constant<int, 3>{});
+      } else if (G.gw_nc <= 5) {
+        views(std::integral_constant<int, 5>{});
+      } else if (G.gw_nc <= 9) {
+        views(std::integral_constant<int, 9>{});
+      } else {
+        views(std::integral_constant<int, 0>{});
       }
     }
   }
-  const int i = i0 + di, c = c0 + dc;
-  if (i < G.nl && c < G.nl) {
-    const size_t plane = (size_t)G.nl * G.nl;
+  const int i = i0 + di;
+  const size_t plane = (size_t)G.nl * G.nl;
 #pragma unroll
-    for (int role = 0; role < 2; ++role)
-      gout[(size_t)(role * vgo + vg) * plane + (size_t)i * G.nl + c] = acc[role] * G.scale2l;
+  for (int k = 0; k < 2; ++k) {
+    const int c = c0 + dc + k * kHalf;
+    if (i < G.nl && c < G.nl) {
+#pragma unroll
+      for (int role = 0; role < 2; ++role)
+        gout[(size_t)(role * vgo + vg) * plane + (size_t)i * G.nl + c] = acc[role][k] * G.scale2l;
+    }
   }
 }
 
@@ -1833,16 +1856,16 @@ cudaError_t launch_bp(const DevPlan &P, LevelSel sel, const float *y, int y_list
   // the grid covers the level with the most (tile, view group) pairs; extra
   // CTAs return at once
   if (P.bp_gather) {
-    // pixel-driven form: (tile, view group) CTAs of GW_TILE x GW_TILE pixels
+    // pixel-driven form: (tile, view group) CTAs of GW_TY x GW_TX pixels
     auto gctas = [&](int li) {
-      const int nt = (P.lg[li].nl + GW_TILE - 1) / GW_TILE;
-      return nt * nt * P.lg[li].bp_vgo;
+      const int nl = P.lg[li].nl;
+      return ((nl + GW_TX - 1) / GW_TX) * ((nl + GW_TY - 1) / GW_TY) * P.lg[li].bp_vgo;
     };
     int most = 0;
     for (int li = 0; li <= P.levels; ++li) most = max(most, gctas(li));
     if (sel.fixed >= -1) most = gctas(sel.fixed + 1);
     count_launch();
-    k_bp_gather<<<most, GW_TILE * GW_TILE, 0, st>>>(P, sel, y, y_list, g, err);
+    k_bp_gather<<<most, GW_THREADS, 0, st>>>(P, sel, y, y_list, g, err);
     return cudaGetLastError();
   }
   auto ctas = [&](int li) { return 2 * P.lg[li].bp_nm * P.lg[li].bp_nc * P.lg[li].bp_vgo; };
