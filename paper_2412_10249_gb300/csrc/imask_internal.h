@@ -28,8 +28,14 @@
 #define LBLOCK 16              // lines per local interpolation frame (see block_origin);
                                // equal to BP_W so a back-projector tile is one block
 #define GW_TY 16               // gather back-projector: tile rows
-#define GW_TX 32               // gather back-projector: tile columns (two pixels per thread)
-#define GW_THREADS 256         // gather back-projector: threads per CTA
+#define GW_TX 32               // gather back-projector: tile columns
+#ifndef GW_PR
+#define GW_PR 1                // gather back-projector: pixel rows per thread
+#endif
+#ifndef GW_PC
+#define GW_PC 2                // gather back-projector: pixel columns per thread
+#endif
+#define GW_THREADS ((GW_TY / GW_PR) * (GW_TX / GW_PC))
 #define GW_SLOTS 4096          // gather back-projector: staged bins per chunk of views
 #ifndef UPD_THREADS
 #define UPD_THREADS 256        // sketch / update kernels: threads per CTA

@@ -800,8 +800,8 @@ __global__ void __launch_bounds__(BP_THREADS, 4)
 // pixel finds the few bins with weight (|q - i| < 1) from one division-free
 // estimate instead of visiting rays.
 //
-// CTA = a GW_TY x GW_TX tile of level pixels (two per thread, GW_TX / 2
-// apart in a row, sharing the view parameters) and one view group vg; it covers that group's x-major views (partial image role 0) and
+// CTA = a GW_TY x GW_TX tile of level pixels (GW_PR x GW_PC per thread,
+// sharing the view parameters) and one view group vg; it covers that group's x-major views (partial image role 0) and
 // y-major views (role 1), so it writes the same 2 bp_vgo partial images as the
 // owner-computes back-projector and the consumer adds them the same way.
 // Views go in chunks of gw_vc; for each the bins crossing the tile (the ray
@@ -813,7 +813,10 @@ __global__ void __launch_bounds__(GW_THREADS)
     k_bp_gather(DevPlan P, LevelSel sel, const float *__restrict__ y, int y_list,
                 float *__restrict__ gout, unsigned int *err) {
   constexpr int kThreads = GW_THREADS;
-  static_assert(GW_TX == 2 * (GW_THREADS / GW_TY), "two pixels per thread, GW_TX / 2 apart");
+  // a thread's pixels: GW_PR rows GW_TY / GW_PR apart times GW_PC columns
+  // GW_TX / GW_PC apart
+  constexpr int kRs = GW_TY / GW_PR, kCs = GW_TX / GW_PC, kPix = GW_PR * GW_PC;
+  static_assert(kRs * kCs == GW_THREADS, "the pixels of a tile fill the CTA");
   constexpr int kMaxVc = 128;
   constexpr int kGwPad = 9;   // zeros staged on either side of a view's window
   __shared__ float yg[GW_SLOTS];
@@ -828,13 +831,15 @@ __global__ void __launch_bounds__(GW_THREADS)
   if (tile >= ntx * nty) return;
   const int i0 = (tile / ntx) * GW_TY, c0 = (tile % ntx) * GW_TX;
   const int tid = threadIdx.x;
-  // this thread's pixels: row i0 + di, columns c0 + dc and c0 + dc + GW_TX / 2
-  constexpr int kHalf = GW_TX / 2;
-  const int di = tid / kHalf, dc = tid % kHalf;
+  const int di = tid / kCs, dc = tid % kCs;
   const int wmax = G.gw_max, wstr = wmax + 2 * kGwPad;   // window and its stride
-  const int vc = max(1, min(min(G.gw_vc, kMaxVc), GW_SLOTS / wstr));   // plan: wstr <= GW_SLOTS
+  // views staged together: the plan's count, at most one per thread (each
+  // thread sets up one view) and what the staging buffer holds
+  const int vc = max(1, min(min(min(G.gw_vc, kMaxVc), kThreads), GW_SLOTS / wstr));
   const float hl = G.hl, W = P.fov;
-  float acc[2][2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};   // [role][pixel]
+  float acc[2][kPix];   // [role][pixel]
+#pragma unroll
+  for (int k = 0; k < kPix; ++k) acc[0][k] = acc[1][k] = 0.0f;
 #pragma unroll
   for (int role = 0; role < 2; ++role) {
     const int *vb = P.bp_vb + ((ell + 1) * 2 + role) * (P.n_angles + 1);
@@ -850,9 +855,15 @@ __global__ void __launch_bounds__(GW_THREADS)
     const float chi = -0.5f * W + ((float)x1 + 0.5f) * hl + hl;
     const float cco = (float)m0 - G.cmid;
     // own march offsets and cross lines in the tile (x-major rays march along
-    // the row, so the two pixels differ in march offset; y-major rays cross it)
-    const float dm0 = (float)(role == 0 ? dc : di), dm1 = (float)(role == 0 ? dc + kHalf : di);
-    const int xo0 = role == 0 ? i0 + di : c0 + dc, xo1 = role == 0 ? i0 + di : c0 + dc + kHalf;
+    // a row, across the columns; y-major rays down a column)
+    float dmk[kPix];
+    int xok[kPix];
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+      const int ri = di + (k / GW_PC) * kRs, ci = dc + (k % GW_PC) * kCs;
+      dmk[k] = (float)(role == 0 ? ci : ri);
+      xok[k] = role == 0 ? i0 + ri : c0 + ci;
+    }
     for (int v0 = 0; v0 < nv; v0 += vc) {
       const int nvc = min(vc, nv - v0);
       __syncthreads();   // the previous chunk's reads are done
@@ -916,7 +927,9 @@ __global__ void __launch_bounds__(GW_THREADS)
       // or outside the window.
       auto views = [&](auto nc_const) {
         constexpr int NC = decltype(nc_const)::value;   // 0: the bounded loop
-        float a0 = acc[role][0], a1 = acc[role][1];
+        float av[kPix];
+#pragma unroll
+        for (int k = 0; k < kPix; ++k) av[k] = acc[role][k];
 #pragma unroll 2
         for (int v = 0; v < nvc; ++v) {
           const int4 q = vi[v];
@@ -945,11 +958,11 @@ __global__ void __launch_bounds__(GW_THREADS)
               }
             }
           };
-          pixel(dm0, xo0, a0);
-          pixel(dm1, xo1, a1);
+#pragma unroll
+          for (int k = 0; k < kPix; ++k) pixel(dmk[k], xok[k], av[k]);
         }
-        acc[role][0] = a0;
-        acc[role][1] = a1;
+#pragma unroll
+        for (int k = 0; k < kPix; ++k) acc[role][k] = av[k];
       };
       if (G.gw_nc <= 3) {
         views(std::integral_constant<int, 3>{});
@@ -962,11 +975,10 @@ __global__ void __launch_bounds__(GW_THREADS)
       }
     }
   }
-  const int i = i0 + di;
   const size_t plane = (size_t)G.nl * G.nl;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int c = c0 + dc + k * kHalf;
+  for (int k = 0; k < kPix; ++k) {
+    const int i = i0 + di + (k / GW_PC) * kRs, c = c0 + dc + (k % GW_PC) * kCs;
     if (i < G.nl && c < G.nl) {
 #pragma unroll
       for (int role = 0; role < 2; ++role)
