@@ -501,15 +501,16 @@ def parallel512_problem():
 
 def time_parallel_backprojectors(imask, iters, stream, flush, steps=3, period=16):
     """Parallel-beam solves with the owner-computes and the pixel-driven
-    back-projector (bp_gather): solves/s, the back-projector's average launch
-    per level (CUDA events on every `period`-th iteration) and the distance
-    between the two results after `iters` iterations."""
+    back-projector (bp_gather), and with the form the plan picks by timing
+    both (bp_gather = -1): solves/s, the back-projector's average launch per
+    level (CUDA events on every `period`-th iteration) and the distance
+    between the two forms' results after `iters` iterations."""
     import torch
     p = parallel512_problem()
     _, b, _ = inputs.measurements(p, seed=0)
     bt = torch.as_tensor(b.ravel().astype(np.float32), device="cuda")
     out, xs, mu, sigma = {}, {}, 0.0, 0.0
-    for name, gather in (("owner_scatter", 0), ("pixel_gather", 1)):
+    for name, gather in (("owner_scatter", 0), ("pixel_gather", 1), ("chosen_at_plan_time", -1)):
         plan = imask.Plan(dict(p.params(), mu=mu, sigma=sigma, autotune=1, bp_gather=gather))
         mu, sigma = plan.info["mu"], plan.info["sigma"]
         x = torch.empty(p.d, device="cuda", dtype=torch.float32)
@@ -535,7 +536,8 @@ def time_parallel_backprojectors(imask, iters, stream, flush, steps=3, period=16
                  for l in range(p.levels) if pcnt[8 + l] > 0}
         out[name] = {"solves_per_s": 1e3 * steps / float(sum(ms)),
                      "back_projector_us_by_level": bp_us,
-                     "bp_view_groups": list(plan.info["bp_view_groups"][:p.levels])}
+                     "bp_view_groups": list(plan.info["bp_view_groups"][:p.levels]),
+                     "form": "pixel_gather" if plan.info["bp_gather"] else "owner_scatter"}
         xs[name] = x.double().cpu().numpy()
         plan.close()
     out["rel_diff_x"] = float(np.linalg.norm(xs["pixel_gather"] - xs["owner_scatter"]) /

@@ -102,7 +102,7 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               point by about the format's precision;
  *               imask_state_set_storage(state, 0, ...) switches a state to
  *               fp32 tables for a refinement sweep.
- *  bp_gather    parallel beam (geometry 0) only, else IMASK_ERR_INVALID:
+ *  bp_gather    1 (parallel beam, geometry 0, only; else IMASK_ERR_INVALID):
  *               the back-projector of every call and solve of the plan is
  *               pixel-driven -- each pixel adds Lambda(q - i) g y over the
  *               few bins of every view whose ray passes within one pixel of
@@ -112,7 +112,12 @@ typedef struct imask_batch_s *imask_batch_t; /* states advanced together by CUDA
  *               Fused batches (imask_batch_create_fused) refuse such plans;
  *               IMASK_ERR_SHAPE when a level's ray window per 16 x 32-pixel tile
  *               would exceed the kernel's staging (detector pitch far below
- *               the pixel width at coarse levels).
+ *               the pixel width at coarse levels).  -1: for parallel beam the
+ *               faster of the two forms -- with autotune = 1 both are timed
+ *               at plan time (each with its own tuned splits, weighted by the
+ *               level probabilities), else the pixel-driven one -- falling
+ *               back to the owners where the windows do not fit; for fan beam
+ *               the owners.  imask_plan_info.bp_gather reports the form.
  *  draws        0: one level per iteration (Alg. 1); 1: the primal level
  *               (back-projector, image-side tables) is drawn from a second
  *               SplitMix64 stream whose seed is the SplitMix64 finaliser of
@@ -140,7 +145,7 @@ typedef struct {
                                             the projector's strip height */
   int32_t bp_gather;                     /* parallel beam only: 1 computes K_l^T
                                             pixel by pixel (see below), 0 by the
-                                            owners of tile segments */
+                                            owners of tile segments, -1 picks */
 } imask_desc;
 
 /* Constants of a plan (Sec. 3.4-3.6): L = |sum p K_l| / sqrt(mu), Lbar,
@@ -156,6 +161,7 @@ typedef struct {
   int32_t autotuned;                    /* 1 when the choices below were measured */
   int32_t bp_view_groups[8];            /* back-projector view groups per level */
   int32_t fp_strip_lines[8];            /* projector strip height (lines) per level */
+  int32_t bp_gather;                    /* back-projector form in use: 1 pixel-driven, 0 owners */
 } imask_plan_info;
 
 /* Creates a plan: validates the descriptor, builds the per-ray geometry tables

@@ -270,8 +270,8 @@ imask_status validate(const imask_desc *d) {
   if (d->step_rule < 0 || d->step_rule > 2)
     return fail(IMASK_ERR_INVALID, "step_rule must be 0, 1 or 2");
   if (d->autotune != 0 && d->autotune != 1) return fail(IMASK_ERR_INVALID, "autotune must be 0 or 1");
-  if (d->bp_gather != 0 && d->bp_gather != 1)
-    return fail(IMASK_ERR_INVALID, "bp_gather must be 0 or 1");
+  if (d->bp_gather < -1 || d->bp_gather > 1)
+    return fail(IMASK_ERR_INVALID, "bp_gather must be -1, 0 or 1");
   if (d->bp_gather == 1 && d->geometry != 0)
     return fail(IMASK_ERR_INVALID, "the pixel-driven back-projector (bp_gather) is for parallel "
                                    "beam only");
@@ -577,8 +577,10 @@ imask_status upload_bp_groups(imask_plan_s *p, int li, cudaStream_t st) {
 // output) is timed with CUDA events for split counts around the occupancy
 // heuristic's choice, and the fastest is kept.
 // ---------------------------------------------------------------------------------
-imask_status autotune_bp(imask_plan_s *p, cudaStream_t st) {
+imask_status autotune_bp(imask_plan_s *p, cudaStream_t st,
+                         std::vector<float> *best_ms_out = nullptr) {
   DevPlan &dp = p->dp;
+  if (best_ms_out) best_ms_out->assign(IMASK_MAX_LEVELS + 1, 0.0f);
   const int r = p->desc.levels, na = p->desc.n_angles;
   std::vector<int> cand[IMASK_MAX_LEVELS + 1];
   size_t gmax = p->gcap;
@@ -631,6 +633,7 @@ imask_status autotune_bp(imask_plan_s *p, cudaStream_t st) {
       }
     }
     dp.lg[li].bp_vgo = best_v;
+    if (best_ms_out) (*best_ms_out)[li] = best_ms;
     if (rc == IMASK_OK) rc = upload_bp_groups(p, li, st);
   }
   if (e0) cudaEventDestroy(e0);
@@ -1226,9 +1229,12 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   // pixel-driven back-projector: per level, the most bins of one view that
   // cross a GW_TY x GW_TX tile (the tile widened by one pixel across the
   // rays' major axis, the slope's drift along it), and the views staged at once
-  dp.bp_gather = desc->bp_gather;
-  if (dp.bp_gather) {
-    for (int li = 0; li <= r; ++li) {
+  // (bp_gather = -1, parallel beam: the form is chosen below; the bounds are
+  // needed in case the pixel-driven one is)
+  dp.bp_gather = desc->bp_gather == 1 ? 1 : 0;
+  bool gather_possible = desc->geometry == 0 && desc->bp_gather != 0;
+  if (gather_possible) {
+    for (int li = 0; li <= r && gather_possible; ++li) {
       LevelGeom &g = dp.lg[li];
       double wmax = 1.0;
       int ncmax = 1;
@@ -1246,6 +1252,10 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
         wmax = std::max(wmax, std::min(b, (double)nd));
       }
       if (wmax > GW_SLOTS - 18) {   // a window and its zero padding must fit
+        if (desc->bp_gather == -1) {   // chosen automatically: keep the owner-computes form
+          gather_possible = false;
+          break;
+        }
         imask_plan_destroy(p);
         return fail(IMASK_ERR_SHAPE,
                     "pixel-driven back-projector: %d bins of one view cross a tile at level "
@@ -1384,7 +1394,39 @@ imask_status imask_plan(const imask_desc *desc, imask_plan_t *plan_out) {
   dp.bp_vb = p->d_bp_vb;
   for (int li = 0; li <= r && rc == IMASK_OK; ++li) rc = upload_bp_groups(p, li, st);
 
-  if (rc == IMASK_OK && p->desc.autotune) rc = autotune_bp(p, st);
+  if (rc == IMASK_OK && p->desc.autotune) {
+    if (gather_possible && p->desc.bp_gather == -1) {
+      // both back-projector forms, each with its own tuned splits; the one
+      // with the smaller expected time per iteration (sum of p_l times the
+      // level's time) is kept
+      double t_form[2] = {0.0, 0.0};
+      int vgo_form[2][IMASK_MAX_LEVELS + 1];
+      int vgo0[IMASK_MAX_LEVELS + 1];
+      for (int li = 0; li <= r; ++li) vgo0[li] = dp.lg[li].bp_vgo;
+      for (int form = 0; form < 2 && rc == IMASK_OK; ++form) {
+        dp.bp_gather = form;
+        for (int li = 0; li <= r; ++li) dp.lg[li].bp_vgo = vgo0[li];
+        std::vector<float> ms;
+        rc = autotune_bp(p, st, &ms);
+        for (int li = 1; li <= r && rc == IMASK_OK; ++li)
+          t_form[form] += p->probs[li - 1] * (double)ms[li];
+        for (int li = 0; li <= r; ++li) vgo_form[form][li] = dp.lg[li].bp_vgo;
+      }
+      if (rc == IMASK_OK) {
+        dp.bp_gather = t_form[1] < t_form[0] ? 1 : 0;
+        p->gcap = 0;
+        for (int li = 0; li <= r && rc == IMASK_OK; ++li) {
+          dp.lg[li].bp_vgo = vgo_form[dp.bp_gather][li];
+          p->gcap = std::max(p->gcap, (size_t)2 * dp.lg[li].bp_vgo * dp.lg[li].nl * dp.lg[li].nl);
+          rc = upload_bp_groups(p, li, st);
+        }
+      }
+    } else {
+      rc = autotune_bp(p, st);
+    }
+  } else if (rc == IMASK_OK && gather_possible && p->desc.bp_gather == -1) {
+    dp.bp_gather = 1;   // not timed: the pixel-driven form (the faster one measured)
+  }
   if (rc == IMASK_OK && p->desc.autotune) rc = autotune_fp(p, st);
   if (rc == IMASK_OK) rc = plan_constants(p, st);
   e = cudaStreamSynchronize(st);
@@ -1431,6 +1473,7 @@ imask_status imask_plan_get_info(imask_plan_t p, imask_plan_info *info) {
   info->n_xmajor_rays = p->dp.m_x;
   info->state_bytes = (int64_t)(state_layout(p).total * sizeof(float));
   info->autotuned = p->autotuned ? 1 : 0;
+  info->bp_gather = p->dp.bp_gather;
   for (int l = 0; l < IMASK_MAX_LEVELS; ++l)
     info->bp_view_groups[l] = l < p->desc.levels ? p->dp.lg[l + 1].bp_vgo : 0;
   for (int l = 0; l < 8; ++l)
@@ -2128,7 +2171,7 @@ imask_status imask_batch_create_fused(const imask_state_t *states, int32_t n_sta
     if (states[i] && states[i]->plan->desc.reg != 0)
       return fail(IMASK_ERR_INVALID,
                   "state %d: fused batches take the quadratic regulariser (reg = 0) only", i);
-    if (states[i] && states[i]->plan->desc.bp_gather != 0)
+    if (states[i] && states[i]->plan->dp.bp_gather != 0)
       return fail(IMASK_ERR_INVALID,
                   "state %d: fused batches run the owner-computes back-projector, not the "
                   "pixel-driven one (bp_gather)", i);

@@ -61,6 +61,7 @@ class PlanInfo(ctypes.Structure):
         ("plan_bytes", ctypes.c_int64), ("autotuned", ctypes.c_int32),
         ("bp_view_groups", ctypes.c_int32 * 8),
         ("fp_strip_lines", ctypes.c_int32 * 8),
+        ("bp_gather", ctypes.c_int32),
     ]
 
 

@@ -1,5 +1,6 @@
-"""The pixel-driven back-projector of parallel-beam plans (bp_gather = 1)
-against the FP64 oracle and against the owner-computes back-projector: every
+"""The pixel-driven back-projector of parallel-beam plans (bp_gather = 1, or
+-1 when the plan picks the faster form) against the FP64 oracle and against
+the owner-computes back-projector: every
 pixel adds Joseph's weight Lambda(q - i) g y over the bins of each view whose
 ray passes within one pixel of it.
 
@@ -125,3 +126,23 @@ def test_fused_batches_refuse_gather_plans(imask):
         imask.Batch([s], fused=True)
     batch = imask.Batch([s])   # graph branches run any back-projector
     batch.close()
+
+
+def test_form_chosen_at_plan_time(imask):
+    # bp_gather = -1: for parallel beam the faster form (timed when autotune
+    # = 1, else the pixel-driven one), for fan beam the owners; either way the
+    # plan reports the form and keeps parity
+    name = "par64_r4"
+    params = dict(CASES[name], mu=1.0, sigma=0.1)
+    o = Oracle(**params)
+    yv = np.random.default_rng(5).standard_normal(o.m)
+    for autotune in (0, 1):
+        plan = imask.Plan(dict(params, bp_gather=-1, autotune=autotune))
+        form = plan.info["bp_gather"]
+        assert form in (0, 1) and (autotune == 1 or form == 1)
+        for ell in range(params["levels"]):
+            assert rel(host(plan.backproject(ell, cuda(yv))), o.KT(ell, yv).ravel()) <= TOL_OP
+    fan = inputs.Problem(n=32, n_angles=20, n_det=48, geometry=1, angle_span=2 * math.pi,
+                         levels=2).params()
+    plan = imask.Plan(dict(fan, mu=1.0, sigma=0.1, bp_gather=-1, autotune=1))
+    assert plan.info["bp_gather"] == 0
