@@ -945,7 +945,8 @@ __global__ void __launch_bounds__(GW_THREADS)
               const float d0 = fmaf((float)eb, f.z, ep);
 #pragma unroll
               for (int k = 0; k < NC; ++k) {
-                const float w = fmaxf(1.0f - fabsf(fmaf((float)k, f.z, d0)), 0.0f);
+                // 1 - |d| never exceeds 1, so clamping to [0, 1] is max(., 0)
+                const float w = __saturatef(1.0f - fabsf(fmaf((float)k, f.z, d0)));
                 a = fmaf(w, yv[eb + k], a);
               }
             } else {
