@@ -823,6 +823,7 @@ __global__ void __launch_bounds__(GW_THREADS)
   __shared__ float4 vf[kMaxVc];   // per staged view: (r, t, D_ell, 1 / D_ell)
   __shared__ int4 vi[kMaxVc];     // per staged view: (I, bins staged, candidates, y index)
   __shared__ float vw[kMaxVc];    // per staged view: the rays' weight g
+  __shared__ float vx[kMaxVc];    // per staged view: I as a float (exact)
   const int ell = sel_level_x(P, sel);
   const LevelGeom G = P.lg[ell + 1];
   const int ntx = (G.nl + GW_TX - 1) / GW_TX, nty = (G.nl + GW_TY - 1) / GW_TY;
@@ -856,13 +857,12 @@ __global__ void __launch_bounds__(GW_THREADS)
     const float cco = (float)m0 - G.cmid;
     // own march offsets and cross lines in the tile (x-major rays march along
     // a row, across the columns; y-major rays down a column)
-    float dmk[kPix];
-    int xok[kPix];
+    float dmk[kPix], xok[kPix];   // (the cross lines as floats, exact)
 #pragma unroll
     for (int k = 0; k < kPix; ++k) {
       const int ri = di + (k / GW_PC) * kRs, ci = dc + (k % GW_PC) * kCs;
       dmk[k] = (float)(role == 0 ? ci : ri);
-      xok[k] = role == 0 ? i0 + ri : c0 + ci;
+      xok[k] = (float)(role == 0 ? i0 + ri : c0 + ci);
     }
     for (int v0 = 0; v0 < nv; v0 += vc) {
       const int nvc = min(vc, nv - v0);
@@ -909,6 +909,7 @@ __global__ void __launch_bounds__(GW_THREADS)
         vf[tid] = f;
         vi[tid] = make_int4(I, len, nc, ybase);
         vw[tid] = gw;
+        vx[tid] = (float)I;
       }
       __syncthreads();
       // stage g y of every view's window (a parallel view's rays share g),
@@ -934,11 +935,13 @@ __global__ void __launch_bounds__(GW_THREADS)
         for (int v = 0; v < nvc; ++v) {
           const int4 q = vi[v];
           const float4 f = vf[v];
+          const float fx = vx[v];
           const float *yv = yg + v * wstr + kGwPad;
           // cross offset of the reference ray from the pixel at its line, the
           // estimate of the bin that passes through the pixel, and its bins
-          auto pixel = [&](float dm, int xo, float &a) {
-            const float ep = (float)(q.x - xo) + fmaf(dm, f.y, f.x);
+          auto pixel = [&](float dm, float xo, float &a) {
+            // (fx - xo is a difference of small integers: exact)
+            const float ep = (fx - xo) + fmaf(dm, f.y, f.x);
             const int elo = ceil_i(fmaf(-ep, f.w, -fabsf(f.w)));
             if constexpr (NC > 0) {
               const int eb = min(max(elo, -kGwPad), q.y + kGwPad - NC);
