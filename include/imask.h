@@ -21,7 +21,8 @@
  * method (linear interpolation along the major axis of every ray); the
  * back-projector is its exact transpose: every pixel's owner thread applies
  * the rays crossing its tile into private shared-memory accumulators, no
- * atomics, partial images added in a fixed order.
+ * atomics, partial images added in a fixed order (parallel-beam plans may
+ * instead gather over bins pixel by pixel: imask_desc.bp_gather).
  *
  * Conventions.
  *  - Pointers named *_dev are device pointers owned by the caller; the library
