@@ -165,3 +165,38 @@ def test_null_handles_are_refused_without_device(imask):
     assert lib.imask_state_destroy(None) == 0     # destroying nothing is fine
     assert lib.imask_plan_destroy(None) == 0
     assert lib.imask_last_error()                  # the message of the last failure
+
+
+def test_null_plans_and_outputs_are_refused_without_device(imask):
+    # the plan-level entry points check their handles and output pointers
+    # before any device work: INVALID (1), with a message naming the argument
+    lib = imask.lib()
+    arr = (ctypes.c_int32 * 4)()
+    buf = ctypes.cast(ctypes.create_string_buffer(64), ctypes.c_void_p)
+    info = imask.PlanInfo()
+    checks = {
+        "imask_plan_axis_split": lambda: lib.imask_plan_axis_split(None, arr, arr),
+        "imask_plan_get_info": lambda: lib.imask_plan_get_info(None, ctypes.byref(info)),
+        "imask_plan_check": lambda: lib.imask_plan_check(None),
+        "imask_project": lambda: lib.imask_project(None, 0, buf, buf, None),
+        "imask_backproject": lambda: lib.imask_backproject(None, 0, buf, buf, None),
+        "imask_backproject_noalloc": lambda: lib.imask_backproject_noalloc(None, 0, buf, buf,
+                                                                           None),
+        "imask_levels": lambda: lib.imask_levels(None, 0, 0, 4, buf, None),
+        "imask_state_create": lambda: lib.imask_state_create(
+            None, buf, 0, ctypes.byref(ctypes.c_void_p()), None),
+        "imask_state_set_storage": lambda: lib.imask_state_set_storage(None, 1, None),
+        "imask_batch_create": lambda: lib.imask_batch_create(None, 1, buf),
+        "imask_batch_create_fused": lambda: lib.imask_batch_create_fused(None, 1, buf),
+        "imask_profile_enable": lambda: lib.imask_profile_enable(-1),
+    }
+    for name, call in checks.items():
+        assert call() == 1, name
+        assert lib.imask_last_error(), name
+    # a batch of one missing state
+    states = (ctypes.c_void_p * 1)(None)
+    out = ctypes.c_void_p()
+    assert lib.imask_batch_create(ctypes.cast(states, ctypes.c_void_p), 1,
+                                  ctypes.cast(ctypes.byref(out), ctypes.c_void_p)) == 1
+    assert b"NULL" in lib.imask_last_error()
+    assert out.value is None
