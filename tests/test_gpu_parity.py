@@ -66,6 +66,8 @@ def _image(n, seed=0):
 def test_projector_parity_all_levels(imask, name):
     params = dict(CASES[name], mu=1.0, sigma=0.1)
     plan = imask.Plan(params)
+    # the plan's major-axis tables are the host geometry's (and so the oracle's)
+    assert plan.axis_split() == imask.imask_geometry_axis_split(params), name
     o = Oracle(**params)
     img = _image(params["n"], 1)
     x = cuda(img)
